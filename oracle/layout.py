@@ -1,0 +1,79 @@
+"""Brute-force sparse block tables (oracle).
+
+Reading of the sparse layout (Sec. 4 and Sec. 6.2; the paper names a
+block-sparse grid "commonly managed by space-filling curves" and the
+boundary / non-boundary block split, but gives no ordering):
+
+* the virtual box is cut into cubic blocks of edge B (8 by default);
+* a block is active iff it holds at least one updated voxel (type fluid,
+  regularized velocity or regularized pressure);
+* a block is a boundary block iff it holds at least one regularized voxel
+  (Sec. 6.2: bounce-back voxels do not make a block "boundary");
+* numbering (memory-based grouping, Sec. 4): boundary blocks first, then
+  non-boundary blocks; inside each group ascending Morton code of the block
+  coordinate with x in the lowest bit (bit 3k = x_k, 3k+1 = y_k, 3k+2 = z_k);
+* nbr[b][k], k = (dx+1) + 3(dy+1) + 9(dz+1), is the id of the block at
+  (bx+dx, by+dy, bz+dz) (wrapped on periodic axes) or -1.
+
+Everything here is computed by the most direct loops over block
+coordinates; it is compared byte for byte with the library's tables.
+"""
+import numpy as np
+
+UPDATED_TYPES = (0, 2, 3)
+REGULARIZED_TYPES = (2, 3)
+
+
+def morton_code(bx, by, bz, bits=10):
+    """Interleave the bits of (bx, by, bz), x in the lowest position."""
+    code = 0
+    for k in range(bits):
+        code |= ((bx >> k) & 1) << (3 * k)
+        code |= ((by >> k) & 1) << (3 * k + 1)
+        code |= ((bz >> k) & 1) << (3 * k + 2)
+    return code
+
+
+def block_tables(flags, block_edge=8, periodic=(False, False, False)):
+    """Return dict(coords (n,3) int32, n_boundary, nbr (n,27) int32, map dict).
+
+    ``flags`` has shape (nz, ny, nx); the box is padded with type 7 (not in
+    domain) up to a whole number of blocks.
+    """
+    nz, ny, nx = flags.shape
+    B = block_edge
+    nbz, nby, nbx = -(-nz // B), -(-ny // B), -(-nx // B)
+    types = flags & 7
+    active, boundary = [], []
+    for bz in range(nbz):
+        for by in range(nby):
+            for bx in range(nbx):
+                t = types[bz * B:(bz + 1) * B, by * B:(by + 1) * B, bx * B:(bx + 1) * B]
+                if np.isin(t, UPDATED_TYPES).any():
+                    is_b = bool(np.isin(t, REGULARIZED_TYPES).any())
+                    active.append((bx, by, bz))
+                    boundary.append(is_b)
+    keys = [(0 if isb else 1, morton_code(*c)) for c, isb in zip(active, boundary)]
+    order = sorted(range(len(active)), key=lambda i: keys[i])
+    coords = np.array([active[i] for i in order], dtype=np.int32).reshape(-1, 3)
+    n_boundary = int(sum(boundary))
+    index = {tuple(int(v) for v in c): b for b, c in enumerate(coords)}
+    nbr = np.full((len(coords), 27), -1, dtype=np.int32)
+    dims_b = (nbx, nby, nbz)
+    for b, c in enumerate(coords):
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    k = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+                    q = [int(c[0]) + dx, int(c[1]) + dy, int(c[2]) + dz]
+                    ok = True
+                    for a in range(3):
+                        if q[a] < 0 or q[a] >= dims_b[a]:
+                            if periodic[a]:
+                                q[a] %= dims_b[a]
+                            else:
+                                ok = False
+                    if ok:
+                        nbr[b, k] = index.get(tuple(q), -1)
+    return {"coords": coords, "n_boundary": n_boundary, "nbr": nbr,
+            "dims_blocks": dims_b}

@@ -1,0 +1,117 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds input generators only (flag fields, boundary values,
+initial density and velocity fields).  It contains none of the
+lattice-Boltzmann arithmetic: the equilibrium, streaming, boundaries and
+collision live in the CUDA library (and, for testing, in the independent
+oracle).  Both sides receive the same arrays from here.
+
+Flag byte: bits 0-2 type (0 fluid, 1 solid, 2 regularized velocity,
+3 regularized pressure, 7 not in domain); bits 3-5 outward normal index
+(0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z).  Arrays are (nz, ny, nx), x fastest.
+"""
+import numpy as np
+
+FLUID, SOLID, VELOCITY, PRESSURE, OUTSIDE = 0, 1, 2, 3, 7
+NX_P, NX_M, NY_P, NY_M, NZ_P, NZ_M = 0, 1, 2, 3, 4, 5
+
+
+def flag(kind, normal=0):
+    return np.uint8((kind & 7) | ((normal & 7) << 3))
+
+
+def cavity(n, u_lid=0.05, dims=None):
+    """Lid-driven cavity (Sec. 6.1): closed box, top plane z = nz-1 is a
+    regularized velocity node with outward normal +z moving at u_lid along x;
+    the other five sides are halfway bounce-back walls (box edges).
+
+    Returns (flags, bc) with bc of shape (4, nz, ny, nx) = (ux, uy, uz, rho).
+    """
+    nx, ny, nz = dims if dims is not None else (n, n, n)
+    flags = np.zeros((nz, ny, nx), dtype=np.uint8)
+    flags[nz - 1] = flag(VELOCITY, NZ_P)
+    bc = np.zeros((4, nz, ny, nx), dtype=np.float64)
+    bc[0, nz - 1] = u_lid
+    bc[3] = 1.0
+    return flags, bc
+
+
+def sphere_channel(dims=(512, 256, 256), radius_channel=81, sphere_center_x=128,
+                   sphere_radius=32, u_in=0.04, rho_out=1.0):
+    """Flow past a sphere in a circular channel (Sec. 6.2 wind-tunnel setup).
+
+    Fluid iff (y-cy)^2 + (z-cz)^2 < Rc^2 and the voxel is outside the sphere;
+    voxels outside the channel are 'not in domain', the sphere is solid.
+    x = 0 is a regularized velocity inlet (normal -x, u = (u_in, 0, 0)),
+    x = nx-1 a regularized pressure outlet (normal +x, rho = rho_out).
+    """
+    nx, ny, nz = dims
+    cy, cz = ny // 2, nz // 2
+    z = np.arange(nz)[:, None, None]
+    y = np.arange(ny)[None, :, None]
+    x = np.arange(nx)[None, None, :]
+    in_channel = ((y - cy) ** 2 + (z - cz) ** 2) < radius_channel ** 2
+    in_sphere = ((x - sphere_center_x) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) < sphere_radius ** 2
+    in_channel = np.broadcast_to(in_channel, (nz, ny, nx))
+    flags = np.full((nz, ny, nx), OUTSIDE, dtype=np.uint8)
+    flags[in_channel] = FLUID
+    flags[in_channel & in_sphere] = SOLID
+    inlet = in_channel[:, :, 0]
+    outlet = in_channel[:, :, nx - 1] & ~in_sphere[:, :, nx - 1]
+    flags[:, :, 0][inlet & ~in_sphere[:, :, 0]] = flag(VELOCITY, NX_M)
+    flags[:, :, nx - 1][outlet] = flag(PRESSURE, NX_P)
+    bc = np.zeros((4, nz, ny, nx), dtype=np.float64)
+    bc[0, :, :, 0] = u_in
+    bc[3] = rho_out
+    return flags, bc
+
+
+def taylor_green_2d(n, u0=0.02, dims=None):
+    """2D Taylor-Green vortex in a periodic box (x, y), uniform along z.
+
+    u = -u0 cos(kx) sin(ky), v = u0 sin(kx) cos(ky), w = 0, k = 2 pi / n,
+    rho = 1 - 3/4 u0^2 (cos 2kx + cos 2ky) (pressure of the exact solution,
+    rho' = 3 p').  Voxel centres at integer coordinates.
+    """
+    nx, ny, nz = dims if dims is not None else (n, n, n)
+    kx = 2.0 * np.pi / nx
+    ky = 2.0 * np.pi / ny
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    y = np.arange(ny, dtype=np.float64)[None, :, None]
+    shape = (nz, ny, nx)
+    u = np.zeros((3,) + shape, dtype=np.float64)
+    u[0] = np.broadcast_to(-u0 * np.cos(kx * x) * np.sin(ky * y), shape)
+    u[1] = np.broadcast_to(u0 * np.sin(kx * x) * np.cos(ky * y), shape)
+    rho = np.broadcast_to(1.0 - 0.75 * u0 * u0 * (np.cos(2 * kx * x) + np.cos(2 * ky * y)),
+                          shape).copy()
+    return rho, u
+
+
+def random_fields(shape_zyx, seed, rho_amp=0.01, u_amp=0.03):
+    """Seeded random density / velocity fields (uniform noise around rest)."""
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + rho_amp * (2.0 * rng.random(shape_zyx) - 1.0)
+    u = u_amp * (2.0 * rng.random((3,) + tuple(shape_zyx)) - 1.0)
+    return rho, u
+
+
+def random_obstacles(shape_zyx, seed, solid_fraction=0.1, kind="spheres"):
+    """Random solid spheres (or boxes) until ~solid_fraction of voxels are solid."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape_zyx
+    flags = np.zeros(shape_zyx, dtype=np.uint8)
+    z = np.arange(nz)[:, None, None]
+    y = np.arange(ny)[None, :, None]
+    x = np.arange(nx)[None, None, :]
+    target = solid_fraction * flags.size
+    tries = 0
+    while (flags == SOLID).sum() < target and tries < 10000:
+        tries += 1
+        r = rng.integers(2, max(3, min(nx, ny, nz) // 6) + 1)
+        c = [rng.integers(0, nx), rng.integers(0, ny), rng.integers(0, nz)]
+        if kind == "spheres":
+            m = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 < r * r
+        else:
+            m = (abs(x - c[0]) < r) & (abs(y - c[1]) < r) & (abs(z - c[2]) < r)
+        flags[np.broadcast_to(m, shape_zyx)] = SOLID
+    return flags
