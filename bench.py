@@ -1,0 +1,323 @@
+"""Benchmark: D3Q19 GLUPS and fraction of the HBM roofline on one GB300.
+
+Default workload (the lid-driven cavity the metric is quoted on): dense
+256^3 D3Q19, FP32 storage, BGK tau = 0.515, regularized lid u = 0.05 on the
+top plane, bounce-back on the other walls, disaggregated schedule (lean
+interior kernel + regularized lid kernel).  One bench step = one lattice
+time step over the whole grid.  The 2.55 GB population state is ~20x the
+L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the FP64 oracle (the plain
+numpy program the CUDA path is checked against) on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}   # 19 loads + 19 stores
+METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated error"
+
+# DRAM traffic of the dominant kernel from an ncu capture (profiles/), valid
+# only while the kernel sources hash to the recorded value.
+NCU_TRAFFIC = {}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("d3q19.cuh", "dense.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2503_07898_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[3 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_cavity_glups(n, steps, tau=0.515, u_lid=0.05):
+    """The FP64 oracle as it stands on an n^3 cavity (same physics as the
+    GPU workload); returns (GLUPS, seconds)."""
+    from oracle import lbm as olbm
+    from paper_2503_07898_gb300 import workloads as wl
+    flags, bc = wl.cavity(n, u_lid=u_lid)
+    f = olbm.init_equilibrium(np.ones((n, n, n)), np.zeros((3, n, n, n)))
+    f = olbm.step(f, flags, tau, bc=bc)          # warm-up
+    c0 = time.process_time()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = olbm.step(f, flags, tau, bc=bc)
+    dt = time.perf_counter() - t0
+    cores = (time.process_time() - c0) / dt      # threads numpy/BLAS actually kept busy
+    return n ** 3 * steps / dt / 1e9, dt, round(cores, 1)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = 48 if args.steps <= 1000 else 32
+    from oracle import lbm as olbm  # noqa: F401
+    oracle_cavity_glups(n, max(1, args.warmup))
+    value, dt, cores = oracle_cavity_glups(n, args.steps)
+    sample = f"{n}^3 cavity window of the 256^3 workload, tau 0.515, lid 0.05, numpy FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cavity256 (sampled)", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2503_07898_gb300 import binding as lbm
+    from paper_2503_07898_gb300 import build as lbm_build
+    from paper_2503_07898_gb300 import workloads as wl
+    lbm_build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    n = args.n
+    dims = (n, n, n)
+    flags, bc = wl.cavity(n)
+    tau = 0.515
+    stream = torch.cuda.Stream()
+    g = lbm.lbm_grid_create_dense(dims, lbm.physics(tau, storage=args.storage,
+                                                    schedule=args.schedule), stream=stream)
+    lbm.lbm_set_boundary(g, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
+    info = lbm.lbm_get_info(g)
+    n_upd = info["n_updated"][0]
+    lbm.lbm_init_equilibrium(g, 0, None, None)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    lbm.lbm_step(g, args.warmup, stream)
+    barrier()
+    # timed region (A): K steps, events on the launching stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        barrier()
+        e0.record(stream)
+        lbm.lbm_step(g, args.steps, stream)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_upd * args.steps / (ms * 1e-3) / 1e9
+
+    # pass (B): per-kernel CUDA events for the roofline of the dominant kernel
+    kb = min(args.steps, 200)
+    lbm.lbm_profile(g, 1)
+    lbm.lbm_step(g, kb, stream)
+    stats = lbm.lbm_profile_read(g)
+    lbm.lbm_profile(g, 0)
+    launches_per_step = sum(s["launches"] for s in stats.values()) / kb
+    top = max(stats, key=lambda k: stats[k]["total_ms"])
+    st = stats[top]
+    bpu = BYTES_PER_UPDATE[args.storage]
+    avg_ms = st["total_ms"] / st["launches"]
+    units = st["units"] / st["launches"]
+    achieved = bpu * units / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    tr = NCU_TRAFFIC.get(top)
+    traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == src_hash() else None
+    shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in stats.values()), 4)
+              for k, v in stats.items()}
+
+    # schedule / storage variants on the same workload (context lines)
+    variants = {}
+    if not args.no_variants:
+        for name, kw in (("monolithic_f32", dict(storage="f32", schedule="monolithic")),
+                         ("disaggregated_f16", dict(storage="f16", schedule="disaggregated")),
+                         ("disaggregated_bf16", dict(storage="bf16", schedule="disaggregated"))):
+            if kw["storage"] == args.storage and kw["schedule"] == args.schedule:
+                continue
+            gv = lbm.lbm_grid_create_dense(dims, lbm.physics(tau, **kw), stream=stream)
+            lbm.lbm_set_boundary(gv, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
+            lbm.lbm_init_equilibrium(gv, 0, None, None)
+            lbm.lbm_step(gv, 20, stream)
+            torch.cuda.synchronize()
+            kv = min(args.steps, 200)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            lbm.lbm_step(gv, kv, stream)
+            a1.record(stream)
+            a1.synchronize()
+            vms = a0.elapsed_time(a1)
+            variants[name] = {"GLUPS": round(n_upd * kv / (vms * 1e-3) / 1e9, 3),
+                              "roofline_frac": round(n_upd * kv * BYTES_PER_UPDATE[kw["storage"]]
+                                                     / (vms * 1e-3) / 1e9 / peak, 4)}
+            lbm.lbm_grid_destroy(gv)
+
+    # end to end through the C ABI with pinned host buffers: init from host
+    # (rho, u), K steps, moments back to host
+    nv = n ** 3
+    rho_h = torch.ones(nv, dtype=torch.float64).pin_memory()
+    u_h = torch.zeros(3 * nv, dtype=torch.float64).pin_memory()
+    rho_o = torch.empty(nv, dtype=torch.float64).pin_memory()
+    u_o = torch.empty(3 * nv, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    lbm.lbm_init_equilibrium(g, 0, rho_h, u_h)
+    lbm.lbm_step(g, args.steps, stream)
+    lbm.lbm_get_moments(g, 0, rho_o, u_o)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n_upd * args.steps / e2e_s / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": 4 * nv * 8, "d2h_bytes_per_step": 4 * nv * 8,
+           "lbm_steps_per_step": args.steps,
+           "what": "one call sequence: lbm_init_equilibrium(host rho,u) + lbm_step(K) + "
+                   "lbm_get_moments(host) from/to pinned memory"}
+    assert np.isfinite(rho_o.numpy()).all()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cn, csteps = 48, 60
+            cv, cdt, ccores = oracle_cavity_glups(cn, csteps)
+            cpu = {"value": cv, "unit": "GLUPS", "cores": ccores, "kind": "oracle",
+                   "sample": f"{cn}^3 cavity (tau 0.515, lid 0.05), {csteps} steps, numpy FP64, "
+                             f"{cdt:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"cavity{n} dense D3Q19 lid-driven cavity", "dims": list(dims),
+                       "tau": tau, "lid_u": 0.05, "collision": "bgk", "storage": args.storage,
+                       "schedule": args.schedule, "updated_voxels": n_upd,
+                       "l2": "inputs larger than L2 (population state "
+                             f"{2 * info['population_bytes'][0] / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                         "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "bytes_per_update": bpu, "units_per_launch": units,
+                         "avg_launch_ms": avg_ms, "kernel_time_share": shares},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clk.summary(),
+            "variants": variants,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    lbm.lbm_grid_destroy(g)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--schedule", default="disaggregated", choices=["disaggregated", "monolithic"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

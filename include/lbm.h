@@ -1,0 +1,217 @@
+/*
+ * lbm.h - C ABI of the GB300-native disaggregated D3Q19 lattice-Boltzmann
+ * library (liblbm.so).
+ *
+ * The library implements the fused stream-and-collide D3Q19 update of the
+ * paper "Disaggregated Design for GPU-Based Volumetric Data Structures"
+ * (Sec. 6: LBM with BGK collision, D3Q19; Sec. 6.2: bounce-back and
+ * regularized inflow/outflow boundaries) over the paper's disaggregated
+ * layouts: voxels are first grouped by a trait (Sec. 2, Definition:
+ * definition / classification / mapping / operations) and then laid out
+ * for locality inside each group:
+ *   - dense grids (Sec. 3): boundary-trait voxels form their own contiguous
+ *     SoA group, processed by their own kernel;
+ *   - block-sparse grids (Sec. 4, Table 2 "Disag - Mem"): boundary blocks are
+ *     stored first, non-boundary blocks after, one lean kernel per group;
+ *   - multi-resolution grids (Sec. 5, Sec. 6.3): per level, blocks next to a
+ *     resolution jump (G_c) are separated from uniform blocks (G_i), which
+ *     run fused at every level.
+ *
+ * Conventions shared by every call
+ *   - All functions return lbm_status; they never abort or trap.  On error,
+ *     lbm_last_error() returns a thread-local message.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Host arrays passed in are only read during the call and stay owned by
+ *     the caller.  Device memory of a grid is owned by the library and is
+ *     obtained through the lbm_allocator given at creation (NULL allocator:
+ *     cudaMalloc / cudaFree).  Output buffers belong to the caller.
+ *   - Virtual-box arrays are indexed x fastest: v = x + nx*(y + ny*z).
+ *   - Flag byte per voxel: bits 0-2 type (0 fluid, 1 solid / bounce-back,
+ *     2 regularized velocity node, 3 regularized pressure node, 7 not in
+ *     domain); bits 3-5 outward normal index of a regularized node
+ *     (0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z).
+ *   - Lattice: D3Q19, velocities ordered rest, +x, -x, +y, -y, +z, -z,
+ *     (+1,+1,0), (-1,-1,0), (+1,-1,0), (-1,+1,0), (+1,0,+1), (-1,0,-1),
+ *     (+1,0,-1), (-1,0,+1), (0,+1,+1), (0,-1,-1), (0,+1,-1), (0,-1,+1).
+ *   - Stored state: post-collision populations f* (pull scheme).
+ *   - Asynchronous device errors are latched in a per-grid status word and
+ *     reported by the next lbm_sync / lbm_get_* call.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_grid lbm_grid;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID = 1,     /* bad argument or descriptor                      */
+  LBM_ERR_OOM = 2,         /* allocation failed (nothing leaked)              */
+  LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
+  LBM_ERR_TIMEOUT = 4,     /* a bounded device wait ran out                   */
+  LBM_ERR_DIVERGED = 5,    /* non-finite mass / momentum                      */
+  LBM_ERR_UNSUPPORTED = 6, /* valid request this build does not implement     */
+  LBM_ERR_INTERNAL = 7     /* library invariant broken (device-side check)    */
+} lbm_status;
+
+enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_REG = 1 };
+enum { LBM_STORAGE_F32 = 0, LBM_STORAGE_F16 = 1, LBM_STORAGE_BF16 = 2 };
+/* Kernel schedule.  DISAGGREGATED: one lean kernel per voxel group (the
+ * paper's design).  MONOLITHIC: one kernel with per-voxel branches over every
+ * voxel (the paper's "naive" kernel, Sec. 4 and Table 2); for multi-resolution
+ * grids it selects the unfused collide / stream pair on every block (the
+ * baseline of Sec. 6.3). */
+enum { LBM_SCHEDULE_DISAGGREGATED = 0, LBM_SCHEDULE_MONOLITHIC = 1 };
+
+typedef struct {
+  double tau;        /* BGK relaxation time of the finest level, > 0.5        */
+  int collision;     /* LBM_COLLISION_*                                       */
+  int storage;       /* LBM_STORAGE_*; F16 / BF16 store f_i - w_i (RN-even)   */
+  int closure;       /* 0 none, 1 learned tau correction (multi-res levels)   */
+  int periodic[3];   /* per axis: 1 periodic, 0 bounce-back walls at the box  */
+  int schedule;      /* LBM_SCHEDULE_*                                        */
+} lbm_physics;
+
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes, void* stream); /* NULL on failure */
+  void (*free)(void* ctx, void* p, void* stream);
+} lbm_allocator;
+
+typedef struct {
+  int kind;                 /* 0 dense, 1 sparse, 2 multi-resolution          */
+  int n_levels;
+  int dims[3];              /* virtual box of level 0                         */
+  int block_edge;           /* sparse / multi-res block edge (0 for dense)    */
+  int64_t n_updated[4];     /* updated voxels per level (fluid + regularized) */
+  int64_t n_blocks[4];      /* active blocks per level                        */
+  int64_t n_group_b[4];     /* boundary blocks (sparse) / G_c blocks (multi)  */
+  int64_t n_regularized;    /* regularized voxels (all levels)                */
+  size_t population_bytes[4]; /* bytes of one population buffer per level     */
+  int64_t steps_done;
+} lbm_info;
+
+/* ---------------------------------------------------------------- grids */
+
+/* Dense grid of dims[0] x dims[1] x dims[2] voxels, all fluid until
+ * lbm_set_boundary.  Storage: one SoA array per population, index
+ * pop * N + v (Sec. 3, SoA; Sec. 6.1 dense LBM). */
+lbm_status lbm_grid_create_dense(const int dims[3], const lbm_physics* phys,
+                                 const lbm_allocator* alloc, void* stream,
+                                 lbm_grid** out);
+
+/* Block-sparse grid (Sec. 4; Sec. 6.2).  `flags` (host, virtual box) fixes
+ * the active blocks (a block is active iff it holds a voxel of type 0, 2 or 3)
+ * and the groups: a block is a boundary block iff it holds a regularized
+ * voxel (Sec. 6.2).  Numbering: boundary blocks first, then non-boundary
+ * blocks, each in ascending Morton order of the block coordinate (x lowest
+ * bit).  Storage index ((block * 19) + pop) * E^3 + lx + E*(ly + E*lz).
+ * block_edge must be 4 or 8; periodic axes need dims divisible by it. */
+lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge,
+                                  const uint8_t* flags, const lbm_physics* phys,
+                                  const lbm_allocator* alloc, void* stream,
+                                  lbm_grid** out);
+
+lbm_status lbm_grid_destroy(lbm_grid* g);
+
+lbm_status lbm_get_info(const lbm_grid* g, lbm_info* out);
+
+/* Select the kernel schedule (LBM_SCHEDULE_*) for later lbm_step calls. */
+lbm_status lbm_set_schedule(lbm_grid* g, int schedule);
+
+/* Voxel types and boundary values of one level.
+ *   flags     host virtual box, or NULL to keep the current flags.  On a
+ *             sparse grid non-NULL flags must equal the creation flags.
+ *   bc_values host, 4 floats (ux, uy, uz, rho) per regularized voxel in
+ *             flag-scan order (x fastest), or NULL to use default_bc for all.
+ *   default_bc 4 floats, used when bc_values is NULL (may be NULL when there
+ *             are no regularized voxels).
+ * Velocity nodes use (ux, uy, uz); pressure nodes use rho (Sec. 6.2 inflow /
+ * outflow).  Dense grids re-derive their groups here: regularized voxels form
+ * the boundary group; when they are the last voxels in memory (a top lid) the
+ * interior kernel covers the rest as one contiguous range. */
+lbm_status lbm_set_boundary(lbm_grid* g, int level, const uint8_t* flags,
+                            const float* bc_values, const float default_bc[4]);
+
+/* Initial state f* = f^eq(rho, u), evaluated in FP64 on the GPU and stored in
+ * the grid's storage format.  rho: n doubles (NULL -> 1); u: 3*n doubles,
+ * component-major (ux[n], uy[n], uz[n]) (NULL -> 0); n = level's virtual box
+ * voxel count.  device_ptrs: 0 host arrays, 1 device arrays.  Voxels that are
+ * not updated are ignored. */
+lbm_status lbm_init_equilibrium(lbm_grid* g, int level, const double* rho,
+                                const double* u, int device_ptrs);
+
+/* Advance n_steps time steps (coarsest steps on a multi-resolution grid) on
+ * `stream`.  Asynchronous; device errors are latched. */
+lbm_status lbm_step(lbm_grid* g, int n_steps, void* stream);
+
+/* Density and velocity of the stored state in FP64, virtual-box order, NaN on
+ * voxels that are not updated.  rho: n doubles or NULL; u: 3*n doubles
+ * (component-major) or NULL.  Synchronises the grid's stream. */
+lbm_status lbm_get_moments(lbm_grid* g, int level, double* rho, double* u,
+                           int device_ptrs);
+
+/* Raw stored populations (checkpoint format = the grid's storage layout and
+ * precision).  bytes must equal info.population_bytes[level]. */
+lbm_status lbm_get_populations(lbm_grid* g, int level, void* dst, size_t bytes,
+                               int device_ptrs);
+lbm_status lbm_set_populations(lbm_grid* g, int level, const void* src,
+                               size_t bytes, int device_ptrs);
+
+/* Stored populations decoded to FP64 in virtual-box order:
+ * dst[pop * n + v], NaN on voxels that are not updated. */
+lbm_status lbm_get_populations_f64(lbm_grid* g, int level, double* dst,
+                                   int device_ptrs);
+
+enum {
+  LBM_LAYOUT_FLAGS = 0,        /* uint8  virtual box                           */
+  LBM_LAYOUT_BLOCK_COORDS = 1, /* int32  n_blocks x 3 (bx, by, bz)             */
+  LBM_LAYOUT_NBR = 2,          /* int32  n_blocks x 27, -1 = none              */
+  LBM_LAYOUT_BLOCK_MAP = 3,    /* int32  virtual block grid -> block id or -1  */
+  LBM_LAYOUT_XNBR_COARSE = 4,  /* int32  n_blocks x 27 (multi-res)             */
+  LBM_LAYOUT_XNBR_FINE = 5     /* int32  n_blocks x 27 x 8 (multi-res)         */
+};
+/* Copy one host-side layout table (for bit-exact checks).  bytes must equal
+ * the table's size; lbm_layout_bytes reports it. */
+lbm_status lbm_layout_bytes(const lbm_grid* g, int level, int what, size_t* bytes);
+lbm_status lbm_get_layout(const lbm_grid* g, int level, int what, void* dst,
+                          size_t bytes);
+
+/* Conservation sums over every updated voxel of every level, accumulated in
+ * FP64 on the GPU with a deterministic two-pass warp-shuffle reduction:
+ * out[0] = sum_l 8^l sum f*_i, out[1..3] = sum_l 8^l sum f*_i c_i.
+ * Returns LBM_ERR_DIVERGED when a sum is not finite.  Synchronises. */
+lbm_status lbm_conservation(lbm_grid* g, double out_mass_mom[4]);
+
+/* Wait for the grid's last stream and return (and clear) the latched device
+ * status. */
+lbm_status lbm_sync(lbm_grid* g);
+
+/* Per-kernel timing.  lbm_profile(g, 1) clears the records and makes every
+ * later kernel launch of this grid record a CUDA event pair on its own
+ * stream; lbm_profile(g, 0) stops recording.  lbm_profile_read waits for the
+ * grid's stream and aggregates the records per kernel: launches, summed
+ * event time and summed units (updated voxels the launches processed).
+ * At most `max` entries are written; *n_out receives the number of kernels. */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double total_ms;
+  int64_t units;
+} lbm_kernel_stat;
+lbm_status lbm_profile(lbm_grid* g, int enable);
+lbm_status lbm_profile_read(lbm_grid* g, lbm_kernel_stat* out, int max, int* n_out);
+
+/* Thread-local message of the last error on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,617 @@
+// api.cu - C ABI entry points of liblbm (declared in include/lbm.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "grid.h"
+#include "layout.h"
+
+namespace lbm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+lbm_status fail(lbm_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+lbm_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+            ") in " + where);
+  return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+void* Grid::dalloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  if (have_alloc) return alloc.alloc(alloc.ctx, bytes, (void*)s);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void Grid::dfree(void* p, cudaStream_t s) {
+  if (!p) return;
+  if (have_alloc) alloc.free(alloc.ctx, p, (void*)s);
+  else cudaFree(p);
+}
+
+int prof_begin(Grid& g, cudaStream_t s, const char* name, int64_t units) {
+  if (!g.prof) return -1;
+  int k = -1;
+  for (size_t i = 0; i < g.prof_names.size(); ++i)
+    if (g.prof_names[i] == name) k = (int)i;
+  if (k < 0) {
+    g.prof_names.push_back(name);
+    k = (int)g.prof_names.size() - 1;
+  }
+  ProfRec r{k, nullptr, nullptr, units};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  cudaEventRecord(r.a, s);
+  g.prof_recs.push_back(r);
+  return (int)g.prof_recs.size() - 1;
+}
+
+void prof_end(Grid& g, cudaStream_t s, int rec) {
+  if (rec < 0) return;
+  cudaEventRecord(g.prof_recs[(size_t)rec].b, s);
+}
+
+void prof_clear(Grid& g) {
+  for (auto& r : g.prof_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g.prof_recs.clear();
+  g.prof_names.clear();
+}
+
+// RAII scratch allocation through the grid's allocator.
+struct Scratch {
+  Grid& g;
+  cudaStream_t s;
+  void* p = nullptr;
+  Scratch(Grid& g_, size_t bytes, cudaStream_t s_) : g(g_), s(s_) { p = g.dalloc(bytes, s); }
+  ~Scratch() {
+    if (p) {
+      cudaStreamSynchronize(s);
+      g.dfree(p, s);
+    }
+  }
+};
+
+static void free_level(Grid& g, Level& L) {
+  cudaStream_t s = g.stream;
+  g.dfree(L.f[0], s);
+  g.dfree(L.f[1], s);
+  g.dfree(L.flags_d, s);
+  g.dfree(L.wmask_d, s);
+  g.dfree(L.reg_list_d, s);
+  g.dfree(L.bc_grp_d, s);
+  g.dfree(L.bc_full_d, s);
+  g.dfree(L.nbr_d, s);
+  g.dfree(L.bmap_d, s);
+  g.dfree(L.blk_walls_d, s);
+  L = Level();
+}
+
+static void free_grid(Grid& g) {
+  cudaStreamSynchronize(g.stream);
+  prof_clear(g);
+  for (int l = 0; l < 4; ++l) free_level(g, g.lv[l]);
+  g.dfree(g.status_d, g.stream);
+  g.dfree(g.partials_d, g.stream);
+  g.dfree(g.sums_d, g.stream);
+  g.status_d = nullptr;
+  g.partials_d = nullptr;
+  g.sums_d = nullptr;
+}
+
+static size_t storage_bytes(int storage) { return storage == LBM_STORAGE_F32 ? 4 : 2; }
+
+static lbm_status check_physics(const lbm_physics* p) {
+  if (!p) return fail(LBM_ERR_INVALID, "physics is NULL");
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(LBM_ERR_INVALID, "tau must be > 0.5");
+  if (p->collision != LBM_COLLISION_BGK && p->collision != LBM_COLLISION_REG)
+    return fail(LBM_ERR_INVALID, "unknown collision");
+  if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16)
+    return fail(LBM_ERR_INVALID, "unknown storage");
+  if (p->schedule != LBM_SCHEDULE_DISAGGREGATED && p->schedule != LBM_SCHEDULE_MONOLITHIC)
+    return fail(LBM_ERR_INVALID, "unknown schedule");
+  if (p->closure != 0) return fail(LBM_ERR_UNSUPPORTED, "closure needs a multi-resolution grid");
+  return LBM_OK;
+}
+
+template <class T>
+static lbm_status upload(Grid& g, T** dst, const T* src, size_t count) {
+  *dst = (T*)g.dalloc(count * sizeof(T), g.stream);
+  if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
+  if (count) LBM_CUDA(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, g.stream));
+  return LBM_OK;
+}
+
+static lbm_status alloc_common(Grid& g) {
+  g.status_d = (int*)g.dalloc(sizeof(int), g.stream);
+  g.partials_d = (double*)g.dalloc(sizeof(double) * 4 * kRedCtas * g.n_levels, g.stream);
+  g.sums_d = (double*)g.dalloc(sizeof(double) * 4, g.stream);
+  if (!g.status_d || !g.partials_d || !g.sums_d) return fail(LBM_ERR_OOM, "device allocation failed");
+  LBM_CUDA(cudaMemsetAsync(g.status_d, 0, sizeof(int), g.stream));
+  return LBM_OK;
+}
+
+static lbm_status alloc_populations(Grid& g, Level& L) {
+  L.pop_bytes = (size_t)Q * (size_t)L.n_slots * storage_bytes(g.phys.storage);
+  for (int k = 0; k < 2; ++k) {
+    L.f[k] = g.dalloc(L.pop_bytes, g.stream);
+    if (!L.f[k]) return fail(LBM_ERR_OOM, "population buffer allocation failed");
+    LBM_CUDA(cudaMemsetAsync(L.f[k], 0, L.pop_bytes, g.stream));
+  }
+  return LBM_OK;
+}
+
+static lbm_status begin(lbm_grid** out, const lbm_physics* phys, const lbm_allocator* alloc,
+                        void* stream, Grid*& gp) {
+  if (!out) return fail(LBM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  lbm_status st = check_physics(phys);
+  if (st) return st;
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(LBM_ERR_INVALID, "allocator needs alloc and free");
+  lbm_grid* h = new (std::nothrow) lbm_grid();
+  if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
+  gp = &h->g;
+  gp->phys = *phys;
+  if (alloc) {
+    gp->alloc = *alloc;
+    gp->have_alloc = true;
+  }
+  gp->stream = (cudaStream_t)stream;
+  cudaGetDevice(&gp->device);
+  *out = h;
+  return LBM_OK;
+}
+
+// Dense grouping (classification + mapping) from the level's host flags.
+static lbm_status dense_groups(Grid& g, Level& L, const float* bc_values, const float* def_bc) {
+  const int64_t N = L.n_slots;
+  const auto& fl = L.flags_h;
+  std::vector<int32_t> regs;
+  bool has_wall_voxel = false;
+  int64_t n_upd = 0;
+  for (int64_t v = 0; v < N; ++v) {
+    const int t = flag_type(fl[v]);
+    if (type_regularized(t)) regs.push_back((int32_t)v);
+    if (type_wall(t)) has_wall_voxel = true;
+    if (type_updated(t)) ++n_upd;
+    if (!type_updated(t) && !type_wall(t)) return fail(LBM_ERR_INVALID, "unknown voxel type");
+  }
+  for (int32_t v : regs) {
+    if (flag_normal(fl[v]) > 5) return fail(LBM_ERR_INVALID, "regularized voxel with bad normal");
+  }
+  if (!regs.empty() && !bc_values && !def_bc)
+    return fail(LBM_ERR_INVALID, "regularized voxels need bc_values or default_bc");
+  L.n_updated = n_upd;
+  L.n_reg = (int64_t)regs.size();
+  L.dense_reg_tail = !regs.empty() && regs.front() == N - (int64_t)regs.size();
+  L.dense_has_flags = has_wall_voxel || !regs.empty();
+  // free old tables
+  g.dfree(L.flags_d, g.stream);
+  g.dfree(L.wmask_d, g.stream);
+  g.dfree(L.reg_list_d, g.stream);
+  g.dfree(L.bc_grp_d, g.stream);
+  g.dfree(L.bc_full_d, g.stream);
+  L.flags_d = nullptr;
+  L.wmask_d = nullptr;
+  L.reg_list_d = nullptr;
+  L.bc_grp_d = nullptr;
+  L.bc_full_d = nullptr;
+  lbm_status st;
+  if (L.dense_has_flags) {
+    if ((st = upload(g, &L.flags_d, fl.data(), (size_t)N))) return st;
+  }
+  // per-voxel wall mask when walls are not only the box sides, or when the
+  // boundary group is not the contiguous tail
+  if (has_wall_voxel || (!regs.empty() && !L.dense_reg_tail)) {
+    std::vector<uint32_t> wm((size_t)N);
+    const int* per = g.phys.periodic;
+    for (int z = 0; z < L.nz; ++z)
+      for (int y = 0; y < L.ny; ++y)
+        for (int x = 0; x < L.nx; ++x) {
+          const int64_t v = x + (int64_t)L.nx * (y + (int64_t)L.ny * z);
+          const int t = flag_type(fl[v]);
+          uint32_t m = 0;
+          if (!type_updated(t)) m |= 1u << 31;
+          if (type_regularized(t)) m |= 1u << 30;
+          for (int i = 1; i < Q; ++i) {
+            int s[3] = {x - cx(i), y - cy(i), z - cz(i)};
+            const int n[3] = {L.nx, L.ny, L.nz};
+            bool wall = false;
+            for (int a = 0; a < 3; ++a) {
+              if (s[a] < 0 || s[a] >= n[a]) {
+                if (per[a]) s[a] = (s[a] + n[a]) % n[a];
+                else wall = true;
+              }
+            }
+            if (!wall) {
+              const int64_t sv = s[0] + (int64_t)L.nx * (s[1] + (int64_t)L.ny * s[2]);
+              wall = type_wall(flag_type(fl[sv]));
+            }
+            if (wall) m |= 1u << i;
+          }
+          wm[(size_t)v] = m;
+        }
+    if ((st = upload(g, &L.wmask_d, wm.data(), wm.size()))) return st;
+  }
+  if (!regs.empty()) {
+    if (!L.dense_reg_tail) {
+      if ((st = upload(g, &L.reg_list_d, regs.data(), regs.size()))) return st;
+    }
+    L.bc_h.assign(regs.size() * 4, 0.f);
+    for (size_t k = 0; k < regs.size(); ++k)
+      for (int c = 0; c < 4; ++c) L.bc_h[k * 4 + c] = bc_values ? bc_values[k * 4 + c] : def_bc[c];
+    if ((st = upload(g, &L.bc_grp_d, (const float4*)L.bc_h.data(), regs.size()))) return st;
+  }
+  return LBM_OK;
+}
+
+// Monolithic kernels read boundary values from a full-domain array (the
+// naive storage of Table 2); built on first use.
+static lbm_status ensure_bc_full(Grid& g, Level& L) {
+  if (L.bc_full_d || L.n_reg == 0) return LBM_OK;
+  std::vector<float4> full((size_t)L.n_slots, make_float4(0.f, 0.f, 0.f, 1.f));
+  if (L.E == 0) {
+    size_t k = 0;
+    for (int64_t v = 0; v < L.n_slots; ++v)
+      if (type_regularized(flag_type(L.flags_h[v]))) {
+        full[(size_t)v] = make_float4(L.bc_h[k * 4], L.bc_h[k * 4 + 1], L.bc_h[k * 4 + 2], L.bc_h[k * 4 + 3]);
+        ++k;
+      }
+  } else {
+    sparse_fill_bc_full(L, full.data());
+  }
+  return upload(g, &L.bc_full_d, full.data(), full.size());
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+lbm_status lbm_grid_create_dense(const int dims[3], const lbm_physics* phys,
+                                 const lbm_allocator* alloc, void* stream, lbm_grid** out) {
+  set_error("");
+  if (!dims || dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0)
+    return fail(LBM_ERR_INVALID, "dims must be positive");
+  if ((double)dims[0] * dims[1] * dims[2] * Q >= 9.0e18)
+    return fail(LBM_ERR_INVALID, "grid too large");
+  Grid* gp = nullptr;
+  lbm_status st = begin(out, phys, alloc, stream, gp);
+  if (st) return st;
+  Grid& g = *gp;
+  g.kind = 0;
+  Level& L = g.lv[0];
+  L.nx = dims[0];
+  L.ny = dims[1];
+  L.nz = dims[2];
+  L.n_slots = (int64_t)dims[0] * dims[1] * dims[2];
+  L.n_updated = L.n_slots;
+  L.flags_h.assign((size_t)L.n_slots, 0);
+  if ((st = alloc_common(g)) || (st = alloc_populations(g, L))) {
+    free_grid(g);
+    delete *out;
+    *out = nullptr;
+    return st;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge, const uint8_t* flags,
+                                  const lbm_physics* phys, const lbm_allocator* alloc,
+                                  void* stream, lbm_grid** out) {
+  set_error("");
+  if (!dims || dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0)
+    return fail(LBM_ERR_INVALID, "dims must be positive");
+  if (block_edge != 4 && block_edge != 8) return fail(LBM_ERR_INVALID, "block_edge must be 4 or 8");
+  if (!flags) return fail(LBM_ERR_INVALID, "sparse grids need flags");
+  for (int a = 0; a < 3; ++a)
+    if (phys && phys->periodic[a] && dims[a] % block_edge)
+      return fail(LBM_ERR_INVALID, "periodic axes need dims divisible by block_edge");
+  Grid* gp = nullptr;
+  lbm_status st = begin(out, phys, alloc, stream, gp);
+  if (st) return st;
+  Grid& g = *gp;
+  g.kind = 1;
+  Level& L = g.lv[0];
+  L.nx = dims[0];
+  L.ny = dims[1];
+  L.nz = dims[2];
+  L.E = block_edge;
+  L.flags_h.assign(flags, flags + (size_t)dims[0] * dims[1] * dims[2]);
+  if ((st = sparse_build(g, L)) || (st = alloc_common(g)) || (st = alloc_populations(g, L)) ||
+      (st = sparse_upload(g, L))) {
+    free_grid(g);
+    delete *out;
+    *out = nullptr;
+    return st;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_grid_destroy(lbm_grid* h) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  free_grid(h->g);
+  delete h;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_info(const lbm_grid* h, lbm_info* out) {
+  if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
+  const Grid& g = h->g;
+  std::memset(out, 0, sizeof(*out));
+  out->kind = g.kind;
+  out->n_levels = g.n_levels;
+  out->dims[0] = g.lv[0].nx;
+  out->dims[1] = g.lv[0].ny;
+  out->dims[2] = g.lv[0].nz;
+  out->block_edge = g.lv[0].E;
+  for (int l = 0; l < g.n_levels; ++l) {
+    out->n_updated[l] = g.lv[l].n_updated;
+    out->n_blocks[l] = g.lv[l].n_blocks;
+    out->n_group_b[l] = g.lv[l].n_b;
+    out->n_regularized += g.lv[l].n_reg;
+    out->population_bytes[l] = g.lv[l].pop_bytes;
+  }
+  out->steps_done = g.steps_done;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_schedule(lbm_grid* h, int schedule) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  if (schedule != LBM_SCHEDULE_DISAGGREGATED && schedule != LBM_SCHEDULE_MONOLITHIC)
+    return fail(LBM_ERR_INVALID, "unknown schedule");
+  h->g.phys.schedule = schedule;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_boundary(lbm_grid* h, int level, const uint8_t* flags,
+                            const float* bc_values, const float default_bc[4]) {
+  set_error("");
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  Level& L = g.lv[level];
+  const size_t nv = (size_t)L.nx * L.ny * L.nz;
+  if (g.kind == 0) {
+    std::vector<uint8_t> keep = L.flags_h;
+    if (flags) L.flags_h.assign(flags, flags + nv);
+    lbm_status st = dense_groups(g, L, bc_values, default_bc);
+    if (st) {
+      L.flags_h.swap(keep);
+      dense_groups(g, L, nullptr, nullptr);
+      return st;
+    }
+    return LBM_OK;
+  }
+  if (flags && std::memcmp(flags, L.flags_h.data(), nv) != 0)
+    return fail(LBM_ERR_INVALID, "sparse / multi-resolution flags are fixed at creation");
+  return sparse_set_bc(g, L, bc_values, default_bc);
+}
+
+lbm_status lbm_init_equilibrium(lbm_grid* h, int level, const double* rho, const double* u,
+                                int device_ptrs) {
+  set_error("");
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  Level& L = g.lv[level];
+  const size_t n = (size_t)L.nx * L.ny * L.nz;
+  cudaStream_t s = g.stream;
+  if (device_ptrs) {
+    lbm_status st = launch_init_equilibrium(g, L, rho, u, s);
+    if (st) return st;
+    LBM_CUDA(cudaStreamSynchronize(s));
+    return LBM_OK;
+  }
+  Scratch dr(g, rho ? n * sizeof(double) : 16, s), du(g, u ? 3 * n * sizeof(double) : 16, s);
+  if (!dr.p || !du.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  if (rho) LBM_CUDA(cudaMemcpyAsync(dr.p, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (u) LBM_CUDA(cudaMemcpyAsync(du.p, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  lbm_status st = launch_init_equilibrium(g, L, rho ? (double*)dr.p : nullptr,
+                                          u ? (double*)du.p : nullptr, s);
+  if (st) return st;
+  LBM_CUDA(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  if (n_steps < 0) return fail(LBM_ERR_INVALID, "n_steps < 0");
+  Grid& g = h->g;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g.stream;
+  g.stream = s;
+  if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
+    for (int l = 0; l < g.n_levels; ++l) {
+      lbm_status st = ensure_bc_full(g, g.lv[l]);
+      if (st) return st;
+    }
+  }
+  for (int k = 0; k < n_steps; ++k) {
+    lbm_status st = g.kind == 0 ? dense_step(g, g.lv[0], s) : sparse_step(g, g.lv[0], s);
+    if (st) return st;
+    ++g.steps_done;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_grid* h) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  Grid& g = h->g;
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  int st = 0;
+  LBM_CUDA(cudaMemcpy(&st, g.status_d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    LBM_CUDA(cudaMemset(g.status_d, 0, sizeof(int)));
+    return fail((lbm_status)st, "device status latched");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_moments(lbm_grid* h, int level, double* rho, double* u, int device_ptrs) {
+  set_error("");
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  lbm_status st = lbm_sync(h);
+  if (st) return st;
+  Level& L = g.lv[level];
+  const size_t n = (size_t)L.nx * L.ny * L.nz;
+  cudaStream_t s = g.stream;
+  if (device_ptrs) {
+    if ((st = launch_moments(g, L, rho, u, s))) return st;
+    LBM_CUDA(cudaStreamSynchronize(s));
+    return LBM_OK;
+  }
+  Scratch dr(g, rho ? n * sizeof(double) : 16, s), du(g, u ? 3 * n * sizeof(double) : 16, s);
+  if (!dr.p || !du.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  if ((st = launch_moments(g, L, rho ? (double*)dr.p : nullptr, u ? (double*)du.p : nullptr, s)))
+    return st;
+  if (rho) LBM_CUDA(cudaMemcpyAsync(rho, dr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (u) LBM_CUDA(cudaMemcpyAsync(u, du.p, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_grid* h, int level, void* dst, size_t bytes, int device_ptrs) {
+  if (!h || !dst) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  Level& L = g.lv[level];
+  if (bytes != L.pop_bytes) return fail(LBM_ERR_INVALID, "bytes != population_bytes");
+  lbm_status st = lbm_sync(h);
+  if (st) return st;
+  LBM_CUDA(cudaMemcpyAsync(dst, L.f[L.cur], bytes,
+                           device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g.stream));
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_grid* h, int level, const void* src, size_t bytes,
+                               int device_ptrs) {
+  if (!h || !src) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  Level& L = g.lv[level];
+  if (bytes != L.pop_bytes) return fail(LBM_ERR_INVALID, "bytes != population_bytes");
+  LBM_CUDA(cudaMemcpyAsync(L.f[L.cur], src, bytes,
+                           device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g.stream));
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations_f64(lbm_grid* h, int level, double* dst, int device_ptrs) {
+  if (!h || !dst) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  lbm_status st = lbm_sync(h);
+  if (st) return st;
+  Level& L = g.lv[level];
+  const size_t n = (size_t)L.nx * L.ny * L.nz * Q;
+  cudaStream_t s = g.stream;
+  if (device_ptrs) {
+    if ((st = launch_decode_f64(g, L, dst, s))) return st;
+    LBM_CUDA(cudaStreamSynchronize(s));
+    return LBM_OK;
+  }
+  Scratch d(g, n * sizeof(double), s);
+  if (!d.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  if ((st = launch_decode_f64(g, L, (double*)d.p, s))) return st;
+  LBM_CUDA(cudaMemcpyAsync(dst, d.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
+lbm_status lbm_layout_bytes(const lbm_grid* h, int level, int what, size_t* bytes) {
+  if (!h || !bytes) return fail(LBM_ERR_INVALID, "NULL argument");
+  const Grid& g = h->g;
+  if (level < 0 || level >= g.n_levels) return fail(LBM_ERR_INVALID, "bad level");
+  const Level& L = g.lv[level];
+  switch (what) {
+    case LBM_LAYOUT_FLAGS: *bytes = L.flags_h.size(); return LBM_OK;
+    case LBM_LAYOUT_BLOCK_COORDS: *bytes = L.coords_h.size() * 4; return LBM_OK;
+    case LBM_LAYOUT_NBR: *bytes = L.nbr_h.size() * 4; return LBM_OK;
+    case LBM_LAYOUT_BLOCK_MAP: *bytes = L.bmap_h.size() * 4; return LBM_OK;
+    default: return fail(LBM_ERR_UNSUPPORTED, "layout table not available for this grid");
+  }
+}
+
+lbm_status lbm_get_layout(const lbm_grid* h, int level, int what, void* dst, size_t bytes) {
+  size_t need = 0;
+  lbm_status st = lbm_layout_bytes(h, level, what, &need);
+  if (st) return st;
+  if (!dst || bytes != need) return fail(LBM_ERR_INVALID, "bytes != layout table size");
+  const Level& L = h->g.lv[level];
+  const void* src = what == LBM_LAYOUT_FLAGS ? (const void*)L.flags_h.data()
+                    : what == LBM_LAYOUT_BLOCK_COORDS ? (const void*)L.coords_h.data()
+                    : what == LBM_LAYOUT_NBR ? (const void*)L.nbr_h.data()
+                                             : (const void*)L.bmap_h.data();
+  if (need) std::memcpy(dst, src, need);
+  return LBM_OK;
+}
+
+lbm_status lbm_profile(lbm_grid* h, int enable) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  Grid& g = h->g;
+  if (enable) {
+    LBM_CUDA(cudaStreamSynchronize(g.stream));
+    prof_clear(g);
+  }
+  g.prof = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_grid* h, lbm_kernel_stat* out, int max, int* n_out) {
+  if (!h || !n_out || (max > 0 && !out)) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid& g = h->g;
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  const int nk = (int)g.prof_names.size();
+  *n_out = nk;
+  for (int k = 0; k < nk && k < max; ++k) {
+    std::memset(&out[k], 0, sizeof(out[k]));
+    std::strncpy(out[k].name, g.prof_names[(size_t)k].c_str(), sizeof(out[k].name) - 1);
+  }
+  for (const auto& r : g.prof_recs) {
+    if (r.kernel >= max) continue;
+    float ms = 0.f;
+    LBM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    out[r.kernel].launches += 1;
+    out[r.kernel].total_ms += ms;
+    out[r.kernel].units += r.units;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_conservation(lbm_grid* h, double out[4]) {
+  if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid& g = h->g;
+  lbm_status st = lbm_sync(h);
+  if (st) return st;
+  if ((st = launch_conservation(g, g.sums_d, g.stream))) return st;
+  LBM_CUDA(cudaMemcpyAsync(out, g.sums_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, g.stream));
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  for (int k = 0; k < 4; ++k)
+    if (!std::isfinite(out[k])) return fail(LBM_ERR_DIVERGED, "non-finite mass or momentum");
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// dense.cu - fused pull stream-and-collide kernels on dense grids.
+//
+// Disaggregated dense layout (Sec. 3 and Sec. 6.1, adapted to one GPU): the
+// voxels needing the register-heavy regularized boundary (Sec. 6.2) form
+// the boundary group G_b; every other voxel is in G_nb.  Populations are
+// SoA, index pop * N + v with v = x + nx (y + ny z).  When G_b is the last
+// n_b voxel ids (a lid on the top plane) both groups are contiguous ranges
+// (Table 2, "Disag - Mem": direct indexing, no extra storage) and the
+// interior kernel runs without any per-voxel flag.  Otherwise a per-voxel
+// 32-bit wall mask tells the interior kernel which pull sources bounce back
+// and which voxels to skip.
+//
+// Kernels
+//   dense_interior<S, COLL>  G_nb: pull + bounce-back + BGK / REG collision
+//                            (2Q live values; bounded to 64 registers)
+//   dense_boundary<S>        G_b : pull + regularized node (3Q live values)
+//   dense_monolithic<S,COLL> the paper's naive kernel (Sec. 4): every voxel,
+//                            per-voxel branch on its flag, boundary values
+//                            read from a full-domain array
+#include "d3q19.cuh"
+#include "grid.h"
+
+namespace lbm {
+
+constexpr uint32_t WM_REG = 1u << 30;   // voxel belongs to the boundary group
+constexpr uint32_t WM_SKIP = 1u << 31;  // voxel not updated
+
+struct DenseArgs {
+  const void* fin;
+  void* fout;
+  int nx, ny, nz;
+  int64_t N;
+  int64_t vend;  // interior: process v < vend
+  int px, py, pz;
+  const uint32_t* wmask;  // null: walls only at non-periodic box sides
+  const uint8_t* flags;
+  const float4* bc;       // boundary: compact per list entry; monolithic: per voxel
+  const int32_t* list;    // boundary voxel ids (null: contiguous from v0)
+  int64_t v0, nlist;
+  float omega;
+};
+
+// Pull population I of voxel (x, y, z) with halfway bounce-back.
+template <int S, int I>
+__device__ __forceinline__ float pull_dense(const typename Codec<S>::T* __restrict__ fin,
+                                            const DenseArgs& a, int x, int y, int z, int64_t v,
+                                            uint32_t wm) {
+  int xs = x - cx(I), ys = y - cy(I), zs = z - cz(I);
+  bool wall = false;
+  if constexpr (cx(I) != 0) {
+    if (xs < 0 || xs >= a.nx) {
+      if (a.px) xs += xs < 0 ? a.nx : -a.nx; else wall = true;
+    }
+  }
+  if constexpr (cy(I) != 0) {
+    if (ys < 0 || ys >= a.ny) {
+      if (a.py) ys += ys < 0 ? a.ny : -a.ny; else wall = true;
+    }
+  }
+  if constexpr (cz(I) != 0) {
+    if (zs < 0 || zs >= a.nz) {
+      if (a.pz) zs += zs < 0 ? a.nz : -a.nz; else wall = true;
+    }
+  }
+  if constexpr (I != 0) wall = wall || ((wm >> I) & 1u);
+  const int64_t src = wall ? (int64_t)opp(I) * a.N + v
+                           : (int64_t)I * a.N + xs + (int64_t)a.nx * (ys + (int64_t)a.ny * zs);
+  return Codec<S>::template load<I>(fin[src]);
+}
+
+template <int S>
+__device__ __forceinline__ void pull_all(const typename Codec<S>::T* __restrict__ fin,
+                                         const DenseArgs& a, int x, int y, int z, int64_t v,
+                                         uint32_t wm, float g[Q]) {
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    g[I] = pull_dense<S, I>(fin, a, x, y, z, v, wm);
+  });
+}
+
+template <int S>
+__device__ __forceinline__ void store_all(typename Codec<S>::T* __restrict__ fout,
+                                          const DenseArgs& a, int64_t v, const float g[Q]) {
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    fout[(int64_t)I * a.N + v] = Codec<S>::template store<I>(g[I]);
+  });
+}
+
+template <int S, int COLL>
+__global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
+  using T = typename Codec<S>::T;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const int64_t v = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
+  if (v >= a.vend) return;
+  uint32_t wm = 0;
+  if (a.wmask) {
+    wm = a.wmask[v];
+    if (wm & (WM_SKIP | WM_REG)) return;
+  }
+  float g[Q];
+  pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
+  collide<COLL>(g, a.omega);
+  store_all<S>((T*)a.fout, a, v, g);
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) dense_boundary(DenseArgs a) {
+  using T = typename Codec<S>::T;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nlist) return;
+  const int64_t v = a.list ? (int64_t)a.list[t] : a.v0 + t;
+  const int64_t plane = (int64_t)a.nx * a.ny;
+  const int z = (int)(v / plane);
+  const int64_t r = v - (int64_t)z * plane;
+  const int y = (int)(r / a.nx);
+  const int x = (int)(r - (int64_t)y * a.nx);
+  const uint32_t wm = a.wmask ? a.wmask[v] : 0u;
+  const uint8_t fl = a.flags[v];
+  float g[Q];
+  pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
+  regularized_node(g, flag_type(fl), flag_normal(fl), a.bc[t], a.omega);
+  store_all<S>((T*)a.fout, a, v, g);
+}
+
+template <int S, int COLL>
+__global__ void __launch_bounds__(256) dense_monolithic(DenseArgs a) {
+  using T = typename Codec<S>::T;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const int64_t v = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
+  const uint8_t fl = a.flags ? a.flags[v] : (uint8_t)0;
+  const int type = flag_type(fl);
+  if (!type_updated(type)) return;
+  const uint32_t wm = a.wmask ? (a.wmask[v] & ~WM_REG) : 0u;
+  float g[Q];
+  pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
+  if (type_regularized(type)) {
+    regularized_node(g, type, flag_normal(fl), a.bc[v], a.omega);
+  } else {
+    collide<COLL>(g, a.omega);
+  }
+  store_all<S>((T*)a.fout, a, v, g);
+}
+
+template <int S, int COLL>
+static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
+  DenseArgs a{};
+  a.fin = L.f[L.cur];
+  a.fout = L.f[L.cur ^ 1];
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.nz = L.nz;
+  a.N = L.n_slots;
+  a.px = g.phys.periodic[0];
+  a.py = g.phys.periodic[1];
+  a.pz = g.phys.periodic[2];
+  a.wmask = L.wmask_d;
+  a.flags = L.flags_d;
+  a.omega = (float)(1.0 / g.phys.tau);
+  const dim3 blk(32, 8);
+  const int gx = (L.nx + 31) / 32, gy = (L.ny + 7) / 8;
+  if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
+    a.bc = L.bc_full_d;
+    const int pr = prof_begin(g, s, "dense_monolithic", L.n_updated);
+    dense_monolithic<S, COLL><<<dim3(gx, gy, L.nz), blk, 0, s>>>(a);
+    prof_end(g, s, pr);
+  } else {
+    const int64_t plane = (int64_t)L.nx * L.ny;
+    a.vend = L.dense_reg_tail ? L.n_slots - L.n_reg : L.n_slots;
+    const int zc = (int)((a.vend + plane - 1) / plane);
+    if (zc > 0) {
+      const int pr = prof_begin(g, s, "dense_interior", L.n_updated - L.n_reg);
+      dense_interior<S, COLL><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
+      prof_end(g, s, pr);
+    }
+    if (L.n_reg > 0) {
+      a.bc = L.bc_grp_d;
+      a.list = L.dense_reg_tail ? nullptr : L.reg_list_d;
+      a.v0 = L.n_slots - L.n_reg;
+      a.nlist = L.n_reg;
+      const int pr = prof_begin(g, s, "dense_boundary", L.n_reg);
+      dense_boundary<S><<<(unsigned)((L.n_reg + 127) / 128), 128, 0, s>>>(a);
+      prof_end(g, s, pr);
+    }
+  }
+  LBM_CUDA(cudaGetLastError());
+  L.cur ^= 1;
+  return LBM_OK;
+}
+
+lbm_status dense_step(Grid& g, Level& L, cudaStream_t s) {
+  const int st = g.phys.storage, co = g.phys.collision;
+  if (st == S_F32) return co == C_BGK ? dense_step_t<S_F32, C_BGK>(g, L, s)
+                                      : dense_step_t<S_F32, C_REG>(g, L, s);
+  if (st == S_F16) return co == C_BGK ? dense_step_t<S_F16, C_BGK>(g, L, s)
+                                      : dense_step_t<S_F16, C_REG>(g, L, s);
+  return co == C_BGK ? dense_step_t<S_BF16, C_BGK>(g, L, s) : dense_step_t<S_BF16, C_REG>(g, L, s);
+}
+
+}  // namespace lbm

@@ -1,0 +1,111 @@
+// grid.h - host-side grid object of liblbm (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Status helpers -------------------------------------------------------------
+void set_error(const std::string& msg);
+lbm_status fail(lbm_status s, const std::string& msg);
+lbm_status cuda_fail(cudaError_t e, const char* where);
+#define LBM_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::lbm::cuda_fail(_e, #call); \
+  } while (0)
+
+constexpr int kRedCtas = 1216;  // reduction CTAs per level (152 SMs x 8)
+
+// Per-level data --------------------------------------------------------------
+struct Level {
+  // virtual box of this level, in this level's voxel units
+  int nx = 0, ny = 0, nz = 0;
+  int E = 0;                  // block edge (0 = dense)
+  int nbx = 0, nby = 0, nbz = 0;  // virtual block grid
+  int64_t n_blocks = 0;       // active blocks (sparse)
+  int64_t n_b = 0;            // boundary blocks, stored first (sparse)
+  int64_t n_slots = 0;        // dense: voxels; sparse: n_blocks * E^3
+  int64_t n_updated = 0;      // fluid + regularized voxels
+  int64_t n_upd_b = 0;        // updated voxels inside boundary blocks (sparse)
+  int64_t n_reg = 0;          // regularized voxels
+  size_t pop_bytes = 0;       // bytes of one population buffer (19 arrays)
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;                // f[cur] holds the current state
+
+  // host tables
+  std::vector<uint8_t> flags_h;       // virtual box
+  std::vector<int32_t> coords_h;      // n_blocks x 3
+  std::vector<int32_t> nbr_h;         // n_blocks x 27
+  std::vector<int32_t> bmap_h;        // virtual block grid -> id
+  std::vector<float> bc_h;            // 4 per regularized voxel, flag-scan order
+
+  // device tables
+  uint8_t* flags_d = nullptr;    // dense: N (null when all fluid); sparse: n_slots
+  uint32_t* wmask_d = nullptr;   // dense, general flags: per-voxel wall mask
+  int32_t* reg_list_d = nullptr; // dense: regularized voxel ids (non-contiguous case)
+  float4* bc_grp_d = nullptr;    // boundary-group BC values (dense: n_reg; sparse: n_b*E^3)
+  float4* bc_full_d = nullptr;   // monolithic kernel: BC for every slot
+  int32_t* nbr_d = nullptr;
+  int32_t* bmap_d = nullptr;
+  uint8_t* blk_walls_d = nullptr; // sparse: 1 if block or its halo has a wall voxel
+
+  // dense grouping
+  bool dense_has_flags = false;   // any non-fluid voxel
+  bool dense_reg_tail = false;    // regularized voxels are exactly the last n_reg ids
+};
+
+struct ProfRec {
+  int kernel;
+  cudaEvent_t a, b;
+  int64_t units;
+};
+
+struct Grid {
+  int kind = 0;  // 0 dense, 1 sparse, 2 multires
+  lbm_physics phys{};
+  lbm_allocator alloc{};
+  bool have_alloc = false;
+  cudaStream_t stream = nullptr;
+  int n_levels = 1;
+  Level lv[4];
+  int device = 0;
+  int* status_d = nullptr;       // latched device status
+  double* partials_d = nullptr;  // reduction partials (scratch)
+  int n_partials = 0;
+  double* sums_d = nullptr;      // 4 doubles
+  int64_t steps_done = 0;
+
+  // per-kernel event timing (lbm_profile)
+  bool prof = false;
+  std::vector<std::string> prof_names;
+  std::vector<ProfRec> prof_recs;
+
+  void* dalloc(size_t bytes, cudaStream_t s);
+  void dfree(void* p, cudaStream_t s);
+};
+
+// Event pair around one kernel launch when profiling is on (else no-op).
+int prof_begin(Grid& g, cudaStream_t s, const char* name, int64_t units);
+void prof_end(Grid& g, cudaStream_t s, int rec);
+void prof_clear(Grid& g);
+
+// Kernel launchers (defined in the .cu files) -------------------------------
+lbm_status dense_step(Grid& g, Level& L, cudaStream_t s);
+lbm_status sparse_step(Grid& g, Level& L, cudaStream_t s);
+lbm_status launch_init_equilibrium(Grid& g, Level& L, const double* rho, const double* u,
+                                   cudaStream_t s);
+lbm_status launch_moments(Grid& g, Level& L, double* rho, double* u, cudaStream_t s);
+lbm_status launch_decode_f64(Grid& g, Level& L, double* dst, cudaStream_t s);
+lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s);
+
+}  // namespace lbm
+
+struct lbm_grid {
+  lbm::Grid g;
+};

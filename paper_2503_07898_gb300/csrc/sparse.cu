@@ -1,0 +1,348 @@
+// sparse.cu - block-sparse layout (classification + mapping) and the
+// per-group fused stream-and-collide kernels.
+//
+// Disaggregation of a block-sparse grid (Sec. 4, Table 2 "Disag - Mem";
+// Sec. 6.2):
+//   definition     P_b: the block holds a voxel that needs the regularized
+//                  (register-heavy, 3Q) boundary; bounce-back voxels do not
+//                  count (Sec. 6.2).
+//   classification G_b = boundary blocks, G_nb = the rest.
+//   mapping        G_b stored first, then G_nb; inside each group blocks
+//                  follow the Morton curve of their coordinates (Sec. 4:
+//                  block-sparse grids "commonly managed by space-filling
+//                  curves").  Storage ((b * 19) + pop) * E^3 + l.
+//   operations     sparse_kernel<MODE_INTERIOR> on G_nb (lean, 2Q, bounded
+//                  registers); sparse_kernel<MODE_BOUNDARY> on G_b; both
+//                  with direct indexing and no per-voxel boundary storage
+//                  outside G_b.
+// MODE_MONOLITHIC is the paper's naive single kernel: every block, per-voxel
+// branches, boundary values read from a full-domain array.
+//
+// Each CTA stages the 27-entry neighbour list of its block(s) in shared
+// memory; a pull that leaves the block reads the neighbour block through it
+// (-1 = no block: bounce-back).  A per-block bit (blk_walls) marks blocks
+// that hold or touch a wall voxel or a missing neighbour; only those read
+// voxel flags, so uniform fluid blocks stream with no metadata traffic.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "grid.h"
+#include "layout.h"
+
+namespace lbm {
+
+// ------------------------------------------------------------- host layout
+
+static uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+lbm_status sparse_build(Grid& g, Level& L) {
+  const int E = L.E;
+  L.nbx = (L.nx + E - 1) / E;
+  L.nby = (L.ny + E - 1) / E;
+  L.nbz = (L.nz + E - 1) / E;
+  if (L.nbx > 1024 || L.nby > 1024 || L.nbz > 1024)
+    return fail(LBM_ERR_INVALID, "more than 1024 blocks along an axis");
+  const int64_t nvb = (int64_t)L.nbx * L.nby * L.nbz;
+  std::vector<uint8_t> act((size_t)nvb, 0), bnd((size_t)nvb, 0), wallb((size_t)nvb, 0);
+  int64_t n_upd = 0, n_reg = 0, n_upd_b = 0;
+  for (int z = 0; z < L.nz; ++z)
+    for (int y = 0; y < L.ny; ++y)
+      for (int x = 0; x < L.nx; ++x) {
+        const uint8_t f = L.flags_h[x + (size_t)L.nx * (y + (size_t)L.ny * z)];
+        const int t = flag_type(f);
+        if (!type_updated(t) && !type_wall(t)) return fail(LBM_ERR_INVALID, "unknown voxel type");
+        if (type_regularized(t) && flag_normal(f) > 5)
+          return fail(LBM_ERR_INVALID, "regularized voxel with bad normal");
+        const int64_t vb = x / E + (int64_t)L.nbx * (y / E + (int64_t)L.nby * (z / E));
+        if (type_updated(t)) act[(size_t)vb] = 1;
+        if (type_regularized(t)) bnd[(size_t)vb] = 1;
+        if (type_wall(t)) wallb[(size_t)vb] = 1;
+      }
+  // voxels of a partial block beyond the box edge are "not in domain"
+  if (L.nx % E || L.ny % E || L.nz % E)
+    for (int64_t vb = 0; vb < nvb; ++vb) {
+      const int bx = (int)(vb % L.nbx), by = (int)((vb / L.nbx) % L.nby), bz = (int)(vb / ((int64_t)L.nbx * L.nby));
+      if ((bx + 1) * E > L.nx || (by + 1) * E > L.ny || (bz + 1) * E > L.nz) wallb[(size_t)vb] = 1;
+    }
+  std::vector<int64_t> ids;
+  for (int64_t vb = 0; vb < nvb; ++vb)
+    if (act[(size_t)vb]) ids.push_back(vb);
+  auto key = [&](int64_t vb) {
+    const uint32_t bx = (uint32_t)(vb % L.nbx), by = (uint32_t)((vb / L.nbx) % L.nby),
+                   bz = (uint32_t)(vb / ((int64_t)L.nbx * L.nby));
+    return ((uint64_t)(bnd[(size_t)vb] ? 0 : 1) << 32) | morton3(bx, by, bz);
+  };
+  std::sort(ids.begin(), ids.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+  L.n_blocks = (int64_t)ids.size();
+  L.n_b = 0;
+  for (int64_t vb : ids) L.n_b += bnd[(size_t)vb] ? 1 : 0;
+  L.bmap_h.assign((size_t)nvb, -1);
+  L.coords_h.resize((size_t)L.n_blocks * 3);
+  for (int64_t b = 0; b < L.n_blocks; ++b) {
+    const int64_t vb = ids[(size_t)b];
+    L.bmap_h[(size_t)vb] = (int32_t)b;
+    L.coords_h[(size_t)b * 3 + 0] = (int32_t)(vb % L.nbx);
+    L.coords_h[(size_t)b * 3 + 1] = (int32_t)((vb / L.nbx) % L.nby);
+    L.coords_h[(size_t)b * 3 + 2] = (int32_t)(vb / ((int64_t)L.nbx * L.nby));
+  }
+  const int* per = g.phys.periodic;
+  const int nbd[3] = {L.nbx, L.nby, L.nbz};
+  L.nbr_h.assign((size_t)L.n_blocks * 27, -1);
+  for (int64_t b = 0; b < L.n_blocks; ++b) {
+    for (int k = 0; k < 27; ++k) {
+      int q[3] = {L.coords_h[b * 3] + k % 3 - 1, L.coords_h[b * 3 + 1] + (k / 3) % 3 - 1,
+                  L.coords_h[b * 3 + 2] + k / 9 - 1};
+      bool ok = true;
+      for (int a = 0; a < 3; ++a)
+        if (q[a] < 0 || q[a] >= nbd[a]) {
+          if (per[a]) q[a] = (q[a] + nbd[a]) % nbd[a];
+          else ok = false;
+        }
+      if (ok) L.nbr_h[(size_t)b * 27 + k] = L.bmap_h[q[0] + (size_t)L.nbx * (q[1] + (size_t)L.nby * q[2])];
+    }
+  }
+  // a block needs flag reads when it, or any of its 26 neighbours, holds a
+  // wall voxel, or when a neighbour block is missing
+  const int64_t E3 = (int64_t)E * E * E;
+  std::vector<uint8_t> bw((size_t)L.n_blocks, 0);
+  for (int64_t b = 0; b < L.n_blocks; ++b) {
+    bool w = wallb[(size_t)ids[(size_t)b]] != 0;
+    for (int k = 0; k < 27 && !w; ++k) {
+      const int32_t nb = L.nbr_h[(size_t)b * 27 + k];
+      if (nb < 0 || wallb[(size_t)ids[(size_t)nb]]) w = true;
+    }
+    bw[(size_t)b] = w ? 1 : 0;
+  }
+  L.n_slots = L.n_blocks * E3;
+  std::vector<uint8_t> sf((size_t)L.n_slots, (uint8_t)T_OUTSIDE);
+  for (int64_t b = 0; b < L.n_blocks; ++b) {
+    const int bx = L.coords_h[b * 3], by = L.coords_h[b * 3 + 1], bz = L.coords_h[b * 3 + 2];
+    for (int l = 0; l < E3; ++l) {
+      const int x = bx * E + l % E, y = by * E + (l / E) % E, z = bz * E + l / (E * E);
+      if (x < L.nx && y < L.ny && z < L.nz) {
+        const uint8_t f = L.flags_h[x + (size_t)L.nx * (y + (size_t)L.ny * z)];
+        sf[(size_t)(b * E3 + l)] = f;
+        if (type_updated(flag_type(f))) {
+          ++n_upd;
+          if (b < L.n_b) ++n_upd_b;
+        }
+        if (type_regularized(flag_type(f))) ++n_reg;
+      }
+    }
+  }
+  L.n_updated = n_upd;
+  L.n_upd_b = n_upd_b;
+  L.n_reg = n_reg;
+  // stash the per-slot flags and wall bits until upload
+  L.bc_h.clear();
+  g.dfree(L.flags_d, g.stream);
+  g.dfree(L.blk_walls_d, g.stream);
+  L.flags_d = (uint8_t*)g.dalloc(sf.size(), g.stream);
+  L.blk_walls_d = (uint8_t*)g.dalloc(bw.size() ? bw.size() : 1, g.stream);
+  if (!L.flags_d || !L.blk_walls_d) return fail(LBM_ERR_OOM, "device allocation failed");
+  LBM_CUDA(cudaMemcpy(L.flags_d, sf.data(), sf.size(), cudaMemcpyHostToDevice));
+  if (!bw.empty()) LBM_CUDA(cudaMemcpy(L.blk_walls_d, bw.data(), bw.size(), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+lbm_status sparse_upload(Grid& g, Level& L) {
+  auto up = [&](int32_t** dst, const std::vector<int32_t>& src) -> lbm_status {
+    *dst = (int32_t*)g.dalloc(src.size() * 4 + 4, g.stream);
+    if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
+    if (!src.empty()) LBM_CUDA(cudaMemcpy(*dst, src.data(), src.size() * 4, cudaMemcpyHostToDevice));
+    return LBM_OK;
+  };
+  lbm_status st;
+  if ((st = up(&L.nbr_d, L.nbr_h)) || (st = up(&L.bmap_d, L.bmap_h))) return st;
+  return LBM_OK;
+}
+
+// Regularized voxels in flag-scan order -> (slot, k).
+template <class F> static void for_each_reg(const Level& L, F&& fn) {
+  const int E = L.E;
+  const int64_t E3 = (int64_t)E * E * E;
+  int64_t k = 0;
+  for (int z = 0; z < L.nz; ++z)
+    for (int y = 0; y < L.ny; ++y)
+      for (int x = 0; x < L.nx; ++x) {
+        const uint8_t f = L.flags_h[x + (size_t)L.nx * (y + (size_t)L.ny * z)];
+        if (!type_regularized(flag_type(f))) continue;
+        const int b = L.bmap_h[x / E + (size_t)L.nbx * (y / E + (size_t)L.nby * (z / E))];
+        const int64_t slot = (int64_t)b * E3 + (x % E) + E * ((y % E) + E * (z % E));
+        fn(slot, k++);
+      }
+}
+
+lbm_status sparse_set_bc(Grid& g, Level& L, const float* bc_values, const float* def_bc) {
+  if (L.n_reg > 0 && !bc_values && !def_bc)
+    return fail(LBM_ERR_INVALID, "regularized voxels need bc_values or default_bc");
+  const int64_t E3 = (int64_t)L.E * L.E * L.E;
+  L.bc_h.assign((size_t)L.n_reg * 4, 0.f);
+  std::vector<float4> grp((size_t)(L.n_b * E3), make_float4(0.f, 0.f, 0.f, 1.f));
+  for_each_reg(L, [&](int64_t slot, int64_t k) {
+    const float* v = bc_values ? bc_values + k * 4 : def_bc;
+    for (int c = 0; c < 4; ++c) L.bc_h[(size_t)k * 4 + c] = v[c];
+    grp[(size_t)slot] = make_float4(v[0], v[1], v[2], v[3]);
+  });
+  g.dfree(L.bc_grp_d, g.stream);
+  g.dfree(L.bc_full_d, g.stream);
+  L.bc_full_d = nullptr;
+  L.bc_grp_d = (float4*)g.dalloc(grp.size() * sizeof(float4) + 16, g.stream);
+  if (!L.bc_grp_d) return fail(LBM_ERR_OOM, "device allocation failed");
+  if (!grp.empty())
+    LBM_CUDA(cudaMemcpy(L.bc_grp_d, grp.data(), grp.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+void sparse_fill_bc_full(const Level& L, float4* full) {
+  for_each_reg(L, [&](int64_t slot, int64_t k) {
+    full[slot] = make_float4(L.bc_h[k * 4], L.bc_h[k * 4 + 1], L.bc_h[k * 4 + 2], L.bc_h[k * 4 + 3]);
+  });
+}
+
+// ------------------------------------------------------------------ kernels
+
+enum { MODE_INTERIOR = 0, MODE_BOUNDARY = 1, MODE_MONOLITHIC = 2 };
+constexpr int SP_THREADS = 256;
+
+struct SparseArgs {
+  const void* fin;
+  void* fout;
+  const int32_t* nbr;
+  const uint8_t* flags;
+  const uint8_t* blk_walls;
+  const float4* bc;
+  int64_t s0, s1;  // slot range [s0, s1), block aligned
+  float omega;
+};
+
+template <int S, int E, int COLL, int MODE>
+__global__ void __launch_bounds__(SP_THREADS, MODE == MODE_INTERIOR ? 4 : 1)
+    sparse_kernel(SparseArgs a) {
+  using T = typename Codec<S>::T;
+  constexpr int E3 = E * E * E;
+  constexpr int BPC = SP_THREADS >= E3 ? SP_THREADS / E3 : 1;  // blocks touched per CTA
+  __shared__ int32_t snbr[BPC * 27];
+  const int64_t cta0 = a.s0 + (int64_t)blockIdx.x * SP_THREADS;
+  const int64_t b0 = cta0 / E3;
+  for (int t = threadIdx.x; t < BPC * 27; t += SP_THREADS) {
+    const int64_t bb = b0 + t / 27;
+    snbr[t] = bb * E3 < a.s1 ? a.nbr[bb * 27 + t % 27] : -1;
+  }
+  __syncthreads();
+  const int64_t slot = cta0 + threadIdx.x;
+  if (slot >= a.s1) return;
+  const int64_t b = slot / E3;
+  const int l = (int)(slot - b * E3);
+  const int lb = (int)(b - b0);
+  const int lx = l % E, ly = (l / E) % E, lz = l / (E * E);
+  const bool walls = MODE != MODE_INTERIOR || a.blk_walls[b];
+  uint8_t own = 0;
+  if (walls) {
+    own = a.flags[slot];
+    if (!type_updated(flag_type(own))) return;
+  }
+  const T* __restrict__ fin = (const T*)a.fin;
+  float g[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+    const int dx = sx < 0 ? -1 : (sx >= E ? 1 : 0);
+    const int dy = sy < 0 ? -1 : (sy >= E ? 1 : 0);
+    const int dz = sz < 0 ? -1 : (sz >= E ? 1 : 0);
+    int64_t nb = b;
+    if (dx | dy | dz) nb = snbr[lb * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+    sx -= dx * E;
+    sy -= dy * E;
+    sz -= dz * E;
+    const int ls = sx + E * (sy + E * sz);
+    bool wall = nb < 0;
+    if (walls && !wall) wall = type_wall(flag_type(a.flags[nb * E3 + ls]));
+    const int64_t src = wall ? (b * Q + opp(I)) * E3 + l : (nb * Q + I) * E3 + ls;
+    g[I] = Codec<S>::template load<I>(fin[src]);
+  });
+  if constexpr (MODE == MODE_INTERIOR) {
+    collide<COLL>(g, a.omega);
+  } else {
+    const int t = flag_type(own);
+    if (type_regularized(t)) regularized_node(g, t, flag_normal(own), a.bc[slot], a.omega);
+    else collide<COLL>(g, a.omega);
+  }
+  T* __restrict__ fout = (T*)a.fout;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    fout[(b * Q + I) * E3 + l] = Codec<S>::template store<I>(g[I]);
+  });
+}
+
+template <int S, int E, int COLL, int MODE>
+static void launch_range(Grid& g, SparseArgs a, cudaStream_t s, const char* name, int64_t units) {
+  if (a.s1 <= a.s0) return;
+  const unsigned nb = (unsigned)((a.s1 - a.s0 + SP_THREADS - 1) / SP_THREADS);
+  const int pr = prof_begin(g, s, name, units);
+  sparse_kernel<S, E, COLL, MODE><<<nb, SP_THREADS, 0, s>>>(a);
+  prof_end(g, s, pr);
+}
+
+template <int S, int E, int COLL>
+static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
+  constexpr int64_t E3 = (int64_t)E * E * E;
+  SparseArgs a{};
+  a.fin = L.f[L.cur];
+  a.fout = L.f[L.cur ^ 1];
+  a.nbr = L.nbr_d;
+  a.flags = L.flags_d;
+  a.blk_walls = L.blk_walls_d;
+  a.omega = (float)(1.0 / g.phys.tau);
+  if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
+    a.bc = L.bc_full_d;
+    a.s0 = 0;
+    a.s1 = L.n_blocks * E3;
+    launch_range<S, E, COLL, MODE_MONOLITHIC>(g, a, s, "sparse_monolithic", L.n_updated);
+  } else {
+    a.bc = L.bc_grp_d;
+    a.s0 = 0;
+    a.s1 = L.n_b * E3;
+    launch_range<S, E, COLL, MODE_BOUNDARY>(g, a, s, "sparse_boundary", L.n_upd_b);
+    a.s0 = L.n_b * E3;
+    a.s1 = L.n_blocks * E3;
+    launch_range<S, E, COLL, MODE_INTERIOR>(g, a, s, "sparse_interior", L.n_updated - L.n_upd_b);
+  }
+  LBM_CUDA(cudaGetLastError());
+  L.cur ^= 1;
+  return LBM_OK;
+}
+
+template <int S, int E>
+static lbm_status sparse_step_e(Grid& g, Level& L, cudaStream_t s) {
+  return g.phys.collision == C_BGK ? sparse_step_t<S, E, C_BGK>(g, L, s)
+                                   : sparse_step_t<S, E, C_REG>(g, L, s);
+}
+
+template <int S>
+static lbm_status sparse_step_s(Grid& g, Level& L, cudaStream_t s) {
+  return L.E == 8 ? sparse_step_e<S, 8>(g, L, s) : sparse_step_e<S, 4>(g, L, s);
+}
+
+lbm_status sparse_step(Grid& g, Level& L, cudaStream_t s) {
+  switch (g.phys.storage) {
+    case S_F32: return sparse_step_s<S_F32>(g, L, s);
+    case S_F16: return sparse_step_s<S_F16>(g, L, s);
+    default: return sparse_step_s<S_BF16>(g, L, s);
+  }
+}
+
+}  // namespace lbm
