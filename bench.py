@@ -164,6 +164,9 @@ def run_ours(args, rank, world, local_rank):
     info = lbm.lbm_get_info(g)
     n_upd = info["n_updated"][0]
     lbm.lbm_init_equilibrium(g, 0, None, None)
+    variant, variant_ms = lbm.lbm_autotune(g, 20) if args.variant == "auto" else (
+        {"vec16": 0, "scalar": 1, "vec8": 2}[args.variant], None)
+    lbm.lbm_set_variant(g, variant)
 
     def barrier():
         if dist is not None:
@@ -220,6 +223,7 @@ def run_ours(args, rank, world, local_rank):
             gv = lbm.lbm_grid_create_dense(dims, lbm.physics(tau, **kw), stream=stream)
             lbm.lbm_set_boundary(gv, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
             lbm.lbm_init_equilibrium(gv, 0, None, None)
+            lbm.lbm_autotune(gv, 20)
             lbm.lbm_step(gv, 20, stream)
             torch.cuda.synchronize()
             kv = min(args.steps, 200)
@@ -276,6 +280,10 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": f"cavity{n} dense D3Q19 lid-driven cavity", "dims": list(dims),
                        "tau": tau, "lid_u": 0.05, "collision": "bgk", "storage": args.storage,
                        "schedule": args.schedule, "updated_voxels": n_upd,
+                       "variant": lbm.VARIANT_NAMES[variant],
+                       "autotune_ms_per_step": (None if variant_ms is None else
+                                                {lbm.VARIANT_NAMES[k]: round(t, 5)
+                                                 for k, t in enumerate(variant_ms)}),
                        "l2": "inputs larger than L2 (population state "
                              f"{2 * info['population_bytes'][0] / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},
@@ -305,6 +313,7 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--schedule", default="disaggregated", choices=["disaggregated", "monolithic"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "vec16", "scalar", "vec8"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -125,6 +125,24 @@ lbm_status lbm_get_info(const lbm_grid* g, lbm_info* out);
 /* Select the kernel schedule (LBM_SCHEDULE_*) for later lbm_step calls. */
 lbm_status lbm_set_schedule(lbm_grid* g, int schedule);
 
+/* Interior-kernel variant of a dense grid (no counterpart in the paper; a
+ * tuning knob of this implementation):
+ *   LBM_VARIANT_VEC16  a thread moves 16-byte vectors of consecutive voxels
+ *                      (default),
+ *   LBM_VARIANT_SCALAR one voxel per thread,
+ *   LBM_VARIANT_VEC8   8-byte vectors.
+ * Vector variants apply when walls are only box sides, dims[0] is a multiple
+ * of the vector length and the boundary group is whole top planes; otherwise
+ * the scalar kernel runs.  Results are identical across variants. */
+enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2 };
+lbm_status lbm_set_variant(lbm_grid* g, int variant);
+
+/* Autotuner: times each variant over n_steps steps (CUDA events on the grid's
+ * stream) starting from the grid's current state, restores that state, and
+ * keeps the fastest variant.  *chosen receives it; ms_per_step (3 doubles, or
+ * NULL) receives the measured time per step of each variant. */
+lbm_status lbm_autotune(lbm_grid* g, int n_steps, int* chosen, double* ms_per_step);
+
 /* Voxel types and boundary values of one level.
  *   flags     host virtual box, or NULL to keep the current flags.  On a
  *             sparse grid non-NULL flags must equal the creation flags.

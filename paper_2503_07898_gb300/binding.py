@@ -89,6 +89,8 @@ def load():
         "lbm_get_layout": [vp, I, I, vp, C.c_size_t],
         "lbm_conservation": [vp, P(C.c_double)],
         "lbm_sync": [vp],
+        "lbm_set_variant": [vp, I],
+        "lbm_autotune": [vp, I, P(I), P(C.c_double)],
         "lbm_profile": [vp, I],
         "lbm_profile_read": [vp, P(lbm_kernel_stat), I, P(I)],
     }
@@ -247,6 +249,22 @@ def lbm_get_info(grid):
 def lbm_set_schedule(grid, schedule):
     s = {"disaggregated": 0, "monolithic": 1}[schedule] if isinstance(schedule, str) else schedule
     _check(load().lbm_set_schedule(grid.ptr, int(s)), "lbm_set_schedule")
+
+
+LBM_VARIANT_VEC16, LBM_VARIANT_SCALAR, LBM_VARIANT_VEC8 = 0, 1, 2
+VARIANT_NAMES = {0: "vec16", 1: "scalar", 2: "vec8"}
+
+
+def lbm_set_variant(grid, variant):
+    _check(load().lbm_set_variant(grid.ptr, int(variant)), "lbm_set_variant")
+
+
+def lbm_autotune(grid, n_steps):
+    """Returns (chosen variant, [ms per step of each variant])."""
+    chosen = C.c_int()
+    ms = (C.c_double * 3)()
+    _check(load().lbm_autotune(grid.ptr, int(n_steps), C.byref(chosen), ms), "lbm_autotune")
+    return chosen.value, list(ms)
 
 
 def lbm_set_boundary(grid, level, flags=None, bc_values=None, default_bc=None):

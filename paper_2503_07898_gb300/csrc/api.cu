@@ -384,6 +384,72 @@ lbm_status lbm_set_schedule(lbm_grid* h, int schedule) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_variant(lbm_grid* h, int variant) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  if (variant < 0 || variant >= N_VARIANTS) return fail(LBM_ERR_INVALID, "unknown variant");
+  for (int l = 0; l < 4; ++l) h->g.lv[l].variant = variant;
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_grid* h, int n_steps, int* chosen, double* ms_per_step) {
+  if (!h || n_steps <= 0) return fail(LBM_ERR_INVALID, "bad autotune arguments");
+  Grid& g = h->g;
+  cudaStream_t s = g.stream;
+  // save the state of every level
+  std::vector<Scratch*> saved;
+  int cur[4];
+  for (int l = 0; l < g.n_levels; ++l) {
+    Level& L = g.lv[l];
+    cur[l] = L.cur;
+    saved.push_back(new Scratch(g, L.pop_bytes, s));
+    if (!saved.back()->p) {
+      for (auto* p : saved) delete p;
+      return fail(LBM_ERR_OOM, "autotune scratch allocation failed");
+    }
+    LBM_CUDA(cudaMemcpyAsync(saved.back()->p, L.f[L.cur], L.pop_bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  const int64_t steps0 = g.steps_done;
+  const int old_variant = g.lv[0].variant;
+  double best = 1e30;
+  int best_v = old_variant;
+  cudaEvent_t e0, e1;
+  LBM_CUDA(cudaEventCreate(&e0));
+  LBM_CUDA(cudaEventCreate(&e1));
+  lbm_status st = LBM_OK;
+  for (int v = 0; v < N_VARIANTS && st == LBM_OK; ++v) {
+    for (int l = 0; l < g.n_levels; ++l) g.lv[l].variant = v;
+    st = lbm_step(h, 2, s);  // warm-up of this variant
+    if (st) break;
+    cudaEventRecord(e0, s);
+    st = lbm_step(h, n_steps, s);
+    cudaEventRecord(e1, s);
+    if (st) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / n_steps;
+    if (ms_per_step) ms_per_step[v] = per;
+    if (per < best) {
+      best = per;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int l = 0; l < g.n_levels; ++l) {
+    Level& L = g.lv[l];
+    L.cur = cur[l];
+    cudaMemcpyAsync(L.f[L.cur], saved[(size_t)l]->p, L.pop_bytes, cudaMemcpyDeviceToDevice, s);
+    L.variant = st == LBM_OK ? best_v : old_variant;
+  }
+  cudaStreamSynchronize(s);
+  for (auto* p : saved) delete p;
+  g.steps_done = steps0;
+  if (st) return st;
+  if (chosen) *chosen = best_v;
+  return LBM_OK;
+}
+
 lbm_status lbm_set_boundary(lbm_grid* h, int level, const uint8_t* flags,
                             const float* bc_values, const float default_bc[4]) {
   set_error("");

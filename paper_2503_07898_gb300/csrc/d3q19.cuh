@@ -171,21 +171,40 @@ __device__ __forceinline__ void pi_neq(const float g[Q], float rho, float ux, fl
 enum Collision { C_BGK = 0, C_REG = 1 };
 
 // In-place collision of pulled populations g -> f*.  omega = 1 / tau.
+//
+// The FP32-rounded weights sum to 1 + 1.5e-8, which would add a systematic
+// omega * 1.5e-8 * rho of mass per voxel and step.  The rest direction
+// therefore closes the balance: f^eq_0 = rho - sum_{i>0} f^eq_i (and the
+// regularized non-equilibrium part of i = 0 is minus the sum of the others),
+// so each update conserves mass up to unbiased rounding.
 template <int COLL>
 __device__ __forceinline__ void collide(float g[Q], float omega) {
   float rho, ux, uy, uz;
   moments(g, rho, ux, uy, uz);
   const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
   if constexpr (COLL == C_BGK) {
+    float s = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) g[i] = g[i] + omega * (feq_i(i, rho, ux, uy, uz, usq15) - g[i]);
+    for (int i = 1; i < Q; ++i) {
+      const float fe = feq_i(i, rho, ux, uy, uz, usq15);
+      s += fe;
+      g[i] = g[i] + omega * (fe - g[i]);
+    }
+    g[0] = g[0] + omega * ((rho - s) - g[0]);
   } else {
     float pxx, pyy, pzz, pxy, pxz, pyz;
     pi_neq(g, rho, ux, uy, uz, pxx, pyy, pzz, pxy, pxz, pyz);
     const float k = 1.f - omega;
+    float s = 0.f, sn = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      g[i] = feq_i(i, rho, ux, uy, uz, usq15) + k * reg_neq_i(i, pxx, pyy, pzz, pxy, pxz, pyz);
+    for (int i = 1; i < Q; ++i) {
+      const float fe = feq_i(i, rho, ux, uy, uz, usq15);
+      const float fn = reg_neq_i(i, pxx, pyy, pzz, pxy, pxz, pyz);
+      s += fe;
+      sn += fn;
+      g[i] = fe + k * fn;
+    }
+    g[0] = (rho - s) - k * sn;
   }
 }
 
@@ -218,8 +237,13 @@ __device__ __forceinline__ void regularized_node(float g[Q], int type, int norma
   }
   const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
   float feq[Q];
+  float s_eq = 0.f;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) feq[i] = feq_i(i, rho, ux, uy, uz, usq15);
+  for (int i = 1; i < Q; ++i) {
+    feq[i] = feq_i(i, rho, ux, uy, uz, usq15);
+    s_eq += feq[i];
+  }
+  feq[0] = rho - s_eq;  // mass-closing rest equilibrium (see collide)
   // non-equilibrium bounce-back of the unknown set (unknowns read known opposites)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -239,8 +263,14 @@ __device__ __forceinline__ void regularized_node(float g[Q], int type, int norma
   }
   // the rest population enters Pi only through the trace-free projection: c_0 = 0
   const float k = 1.f - omega;
+  float s_neq = 0.f;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) g[i] = feq[i] + k * reg_neq_i(i, pxx, pyy, pzz, pxy, pxz, pyz);
+  for (int i = 1; i < Q; ++i) {
+    const float fn = reg_neq_i(i, pxx, pyy, pzz, pxy, pxz, pyz);
+    s_neq += fn;
+    g[i] = feq[i] + k * fn;
+  }
+  g[0] = feq[0] - k * s_neq;
 }
 
 // Equilibrium in FP64 (initial state).

@@ -107,6 +107,125 @@ __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
   store_all<S>((T*)a.fout, a, v, g);
 }
 
+// ------------------------------------------------------------------------
+// Vectorized interior kernel for grids whose walls are only box sides.
+// A thread owns V consecutive voxels along x and moves every population as
+// one aligned vector (V * sizeof(T) = 16 bytes: 4 FP32 or 8 FP16 / BF16
+// values), so a warp reads and writes 512 contiguous bytes per population.
+// A pull with c_x = +1 needs the element left of the vector: it comes from
+// lane - 1 by a warp shuffle; lane 0 (and the thread at x = 0) fetches it
+// itself, wrapping or bouncing back at the box side.  c_x = -1 mirrors this
+// with lane + 1.  Rows whose source (y - c_y, z - c_z) leaves a non-periodic
+// box side bounce back as a whole (warp-uniform).  Loads and stores use the
+// streaming cache hint: every population value is read exactly once.
+template <class T, int V> struct alignas(sizeof(T) * V) PVec { T e[V]; };
+
+template <class T, int V>
+__device__ __forceinline__ PVec<T, V> ld_vec(const T* p) {
+  PVec<T, V> r;
+  if constexpr (sizeof(T) * V == 16) {
+    uint4 u = __ldcs(reinterpret_cast<const uint4*>(p));
+    memcpy(&r, &u, 16);
+  } else {
+    uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
+    memcpy(&r, &u, 8);
+  }
+  return r;
+}
+
+template <class T, int V>
+__device__ __forceinline__ void st_vec(T* p, const PVec<T, V>& r) {
+  if constexpr (sizeof(T) * V == 16) {
+    uint4 u;
+    memcpy(&u, &r, 16);
+    __stcs(reinterpret_cast<uint4*>(p), u);
+  } else {
+    uint2 u;
+    memcpy(&u, &r, 8);
+    __stcs(reinterpret_cast<uint2*>(p), u);
+  }
+}
+
+constexpr int VEC_ROWS = 4;  // warps (rows along y) per CTA
+
+template <int S, int COLL, int V>
+__global__ void __launch_bounds__(32 * VEC_ROWS) dense_interior_vec(DenseArgs a) {
+  using T = typename Codec<S>::T;
+  using Vt = PVec<T, V>;
+  const T* __restrict__ fin = (const T*)a.fin;
+  T* __restrict__ fout = (T*)a.fout;
+  const int lane = threadIdx.x;
+  const int x = (blockIdx.x * 32 + lane) * V;
+  const int y = blockIdx.y * VEC_ROWS + threadIdx.y;
+  const int z = blockIdx.z;
+  if (y >= a.ny) return;  // uniform per warp
+  const bool active = x < a.nx;
+  const int64_t v = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
+  const bool last = lane == 31 || x + V >= a.nx;  // the next lane holds no voxel of this row
+  Vt f[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    int ys = y - cy(I), zs = z - cz(I);
+    bool rwall = false;
+    if constexpr (cy(I) != 0) {
+      if (ys < 0 || ys >= a.ny) {
+        if (a.py) ys += ys < 0 ? a.ny : -a.ny; else rwall = true;
+      }
+    }
+    if constexpr (cz(I) != 0) {
+      if (zs < 0 || zs >= a.nz) {
+        if (a.pz) zs += zs < 0 ? a.nz : -a.nz; else rwall = true;
+      }
+    }
+    if (rwall) {
+      if (active) f[I] = ld_vec<T, V>(fin + (int64_t)opp(I) * a.N + v);
+      return;
+    }
+    const T* src = fin + (int64_t)I * a.N + (int64_t)a.nx * (ys + (int64_t)a.ny * zs);
+    Vt A;
+    if (active) A = ld_vec<T, V>(src + x);
+    if constexpr (cx(I) == 0) {
+      f[I] = A;
+    } else if constexpr (cx(I) == 1) {
+      T left = __shfl_up_sync(0xffffffffu, A.e[V - 1], 1);
+      if (active && lane == 0) {
+        if (x > 0) left = src[x - 1];
+        else left = a.px ? src[a.nx - 1] : fin[(int64_t)opp(I) * a.N + v];
+      }
+      f[I].e[0] = left;
+#pragma unroll
+      for (int k = 1; k < V; ++k) f[I].e[k] = A.e[k - 1];
+    } else {
+      T right = __shfl_down_sync(0xffffffffu, A.e[0], 1);
+      if (active && last) {
+        if (x + V < a.nx) right = src[x + V];
+        else right = a.px ? src[0] : fin[(int64_t)opp(I) * a.N + v + V - 1];
+      }
+#pragma unroll
+      for (int k = 0; k < V - 1; ++k) f[I].e[k] = A.e[k + 1];
+      f[I].e[V - 1] = right;
+    }
+  });
+  if (!active) return;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    float g[Q];
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      g[I] = Codec<S>::template load<I>(f[I].e[k]);
+    });
+    collide<COLL>(g, a.omega);
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      f[I].e[k] = Codec<S>::template store<I>(g[I]);
+    });
+  }
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    st_vec<T, V>(fout + (int64_t)I * a.N + v, f[I]);
+  });
+}
+
 template <int S>
 __global__ void __launch_bounds__(128) dense_boundary(DenseArgs a) {
   using T = typename Codec<S>::T;
@@ -174,7 +293,20 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
     const int64_t plane = (int64_t)L.nx * L.ny;
     a.vend = L.dense_reg_tail ? L.n_slots - L.n_reg : L.n_slots;
     const int zc = (int)((a.vend + plane - 1) / plane);
-    if (zc > 0) {
+    // vector widths: 16 bytes (default) or 8 bytes; scalar when the grid has
+    // per-voxel walls, an x extent that is not a multiple of V, or a
+    // boundary group that is not a whole number of top planes
+    constexpr int V16 = 16 / (int)sizeof(typename Codec<S>::T);
+    constexpr int V8 = 8 / (int)sizeof(typename Codec<S>::T);
+    const int vw = L.variant == VARIANT_SCALAR ? 0 : (L.variant == VARIANT_VEC8 ? V8 : V16);
+    const bool vec_ok = vw > 0 && !L.wmask_d && L.nx % vw == 0 && a.vend % plane == 0;
+    if (zc > 0 && vec_ok) {
+      const int pr = prof_begin(g, s, "dense_interior_vec", L.n_updated - L.n_reg);
+      const dim3 vb(32, VEC_ROWS), vg((L.nx + 32 * vw - 1) / (32 * vw), (L.ny + VEC_ROWS - 1) / VEC_ROWS, zc);
+      if (vw == V16) dense_interior_vec<S, COLL, V16><<<vg, vb, 0, s>>>(a);
+      else dense_interior_vec<S, COLL, V8><<<vg, vb, 0, s>>>(a);
+      prof_end(g, s, pr);
+    } else if (zc > 0) {
       const int pr = prof_begin(g, s, "dense_interior", L.n_updated - L.n_reg);
       dense_interior<S, COLL><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
       prof_end(g, s, pr);

@@ -22,6 +22,9 @@ lbm_status cuda_fail(cudaError_t e, const char* where);
 
 constexpr int kRedCtas = 1216;  // reduction CTAs per level (152 SMs x 8)
 
+// Interior-kernel variants (dense grids): 16-byte vectors, scalar, 8-byte vectors.
+enum { VARIANT_VEC16 = 0, VARIANT_SCALAR = 1, VARIANT_VEC8 = 2, N_VARIANTS = 3 };
+
 // Per-level data --------------------------------------------------------------
 struct Level {
   // virtual box of this level, in this level's voxel units
@@ -54,6 +57,8 @@ struct Level {
   int32_t* nbr_d = nullptr;
   int32_t* bmap_d = nullptr;
   uint8_t* blk_walls_d = nullptr; // sparse: 1 if block or its halo has a wall voxel
+
+  int variant = 0;                // kernel variant (VARIANT_*), set by lbm_set_variant / autotune
 
   // dense grouping
   bool dense_has_flags = false;   // any non-fluid voxel
