@@ -1,0 +1,153 @@
+"""Multi-resolution D3Q19 lattice-Boltzmann step (oracle, FP64).
+
+The paper (Sec. 5; Sec. 6.3) uses one uniform grid per level, refinement
+factor 2, and two inter-level operations per time step: explosion (collision
+results of a coarse level feed the finer level) and coalescence (streaming
+data of the finer level merges into coarse voxels).  It gives no formulas.
+Reading implemented here (a volumetric, mass-conserving scheme of the family
+of the multi-resolution LBM the paper builds on):
+
+* level 0 is the finest; a level-l voxel is a cube of 2^l finest voxels;
+  acoustic scaling dx_l = dt_l = 2^l, so lattice velocities are the same on
+  every level and tau_l - 1/2 = (tau_0 - 1/2) / 2^l keeps one physical
+  viscosity;
+* every region of the box is owned by exactly one level (a level map), with
+  2:1 grading;
+* one step of a level l > 0 contains two steps of level l-1; the exchange
+  across a level jump is defined as level-(l-1) streaming over those two
+  substeps in which every level-l voxel is represented by its 8 virtual
+  subcells.  Virtual subcells start the coarse step holding the coarse
+  post-collision populations C, stream but do not collide;
+* explosion (a level-(l-1) voxel p pulls population i from q = p - c_i):
+    substep 1: q virtual -> C_i(cell(q));
+    substep 2: q virtual -> the value q received in substep 1:
+               F0_i(q - c_i) if q - c_i is a level-(l-1) voxel, else
+               C_i(cell(q - c_i))            (F0 = fine state at the start);
+* coalescence: a level-l voxel X next to level l-1 pulls, for every i, the
+  mean over its 8 subcells p of the value p receives in substep 2:
+    F1_i(p - c_i) if p - c_i is a level-(l-1) voxel (F1 = fine state after
+    substep 1), else the value p - c_i received in substep 1 (as above);
+  then X collides with tau_l.
+Away from level jumps both rules reduce to plain streaming.  Pure streaming
+at the finest resolution is a permutation and averaging keeps the sum of the
+8 subcells, so mass and momentum weighted by voxel volume (8^l) are conserved
+exactly in a periodic box.  There is no rescaling of non-equilibrium parts
+between levels.
+
+State: f[l] is a (19, nz_l, ny_l, nx_l) array over the whole level-l virtual
+box, zero where level l does not own the region.  The box is periodic.
+"""
+import numpy as np
+
+from . import lattice as L
+from . import lbm
+
+
+def tau_of_level(tau0, level):
+    return 0.5 + (tau0 - 0.5) / (2 ** level)
+
+
+def upsample(a):
+    """Level l -> level l-1 resolution: every voxel becomes 2x2x2 copies."""
+    return a.repeat(2, axis=-1).repeat(2, axis=-2).repeat(2, axis=-3)
+
+
+def subcell_mean(a):
+    """Mean over 2x2x2 subcells by three pairwise means (exact for equal values)."""
+    a = 0.5 * (a[..., 0::2] + a[..., 1::2])
+    a = 0.5 * (a[..., 0::2, :] + a[..., 1::2, :])
+    a = 0.5 * (a[..., 0::2, :, :] + a[..., 1::2, :, :])
+    return a
+
+
+def shift(a, c, k=1):
+    """Value at x - k c on a periodic box (last three axes are z, y, x)."""
+    return np.roll(a, shift=(k * int(c[2]), k * int(c[1]), k * int(c[0])), axis=(-3, -2, -1))
+
+
+class MultiRes:
+    """Multi-resolution grid: level_map (Mz, My, Mx) gives the owning level of
+    every cube of `cell` finest voxels; cell must be a multiple of 2^(L-1)."""
+
+    def __init__(self, level_map, n_levels, cell, tau0, collision="bgk"):
+        level_map = np.asarray(level_map, dtype=np.int64)
+        assert cell % (2 ** (n_levels - 1)) == 0
+        self.L = n_levels
+        self.tau0 = tau0
+        self.collision = collision
+        self.own = []
+        for lv in range(n_levels):
+            r = cell // (2 ** lv)
+            self.own.append(level_map.repeat(r, 0).repeat(r, 1).repeat(r, 2))
+        self.f = [np.zeros((L.Q,) + o.shape) for o in self.own]
+
+    def dims(self, level):
+        nz, ny, nx = self.own[level].shape
+        return nx, ny, nz
+
+    def init_equilibrium(self, level, rho, u):
+        feq = L.equilibrium(rho, u)
+        self.f[level] = np.where(self.own[level][None] == level, feq, 0.0)
+
+    def _neighbour_levels(self, lv):
+        own = self.own[lv]
+        finer = np.zeros(own.shape, bool)
+        coarser = np.zeros(own.shape, bool)
+        for i in range(1, L.Q):
+            nb = shift(own, L.C[i])
+            finer |= nb == lv - 1
+            coarser |= nb == lv + 1
+        return finer, coarser
+
+    def _advance(self, lv, k, f0_self):
+        """One step of level lv; k = 1 or 2 is its substep inside the step of
+        level lv+1; f0_self = level-lv state at the start of that step."""
+        if lv > 0:
+            f0_fine = self.f[lv - 1].copy()
+            self._advance(lv - 1, 1, f0_fine)
+            f1_fine = self.f[lv - 1].copy()
+            self._advance(lv - 1, 2, f0_fine)
+        S = self.f[lv]
+        own = self.own[lv]
+        has_finer, _ = self._neighbour_levels(lv)
+        g = np.empty_like(S)
+        for i in range(L.Q):
+            c = L.C[i]
+            val = shift(S[i], c)
+            if lv + 1 < self.L:                       # explosion from level lv+1
+                c_up = upsample(self.f[lv + 1][i])
+                if k == 1:
+                    ex = shift(c_up, c)
+                else:
+                    ex = np.where(shift(own, c, 2) == lv, shift(f0_self[i], c, 2),
+                                  shift(c_up, c, 2))
+                val = np.where(shift(own, c) == lv + 1, ex, val)
+            if lv > 0:                                # coalescence from level lv-1
+                own_f = self.own[lv - 1]
+                s_up = upsample(S[i])
+                v1 = np.where(shift(own_f, c) == lv - 1, shift(f0_fine[i], c), shift(s_up, c))
+                held = np.where(own_f == lv - 1, f1_fine[i], v1)
+                coal = subcell_mean(shift(held, c))
+                val = np.where(has_finer, coal, val)
+            g[i] = val
+        with np.errstate(invalid="ignore", divide="ignore"):   # unowned voxels hold zeros
+            fnew, _, _ = lbm.collide(g, tau_of_level(self.tau0, lv), self.collision)
+        self.f[lv] = np.where(own[None] == lv, fnew, 0.0)
+
+    def step(self):
+        """One step of the coarsest level (2^(L-1-l) steps of every level l)."""
+        self._advance(self.L - 1, 1, None)
+
+    def run(self, n):
+        for _ in range(n):
+            self.step()
+
+    def conservation(self):
+        """(M, Jx, Jy, Jz) weighted by voxel volume 8^l."""
+        out = np.zeros(4)
+        for lv in range(self.L):
+            out += (8.0 ** lv) * lbm.conservation(self.f[lv])
+        return out
+
+    def updates_per_step(self):
+        return sum(int((self.own[lv] == lv).sum()) * 2 ** (self.L - 1 - lv) for lv in range(self.L))

@@ -1,0 +1,140 @@
+"""Pins of the multi-resolution oracle (oracle/multires.py).
+
+The paper gives no explosion / coalescence formulas, so these pins tie the
+reading to what must hold for any correct scheme of this family: exact
+volume-weighted conservation, invariance of a uniform state, reduction to
+the single-resolution oracle away from level jumps, and the viscous decay
+rate of a Taylor-Green vortex crossing a level jump.
+"""
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+from oracle import lbm as olbm
+from oracle import multires as mr
+from paper_2503_07898_gb300 import workloads as wl
+
+
+def three_level(tau0=0.6):
+    # z-slabs of 8 finest voxels: level 2, 1, 0, 1 (periodic in z)
+    return mr.MultiRes(np.array([2, 1, 0, 1]).reshape(4, 1, 1), 3, 8, tau0)
+
+
+def init_random(g, seed):
+    for lv in range(g.L):
+        nx, ny, nz = g.dims(lv)
+        rho, u = wl.random_fields((nz, ny, nx), seed=seed + lv)
+        g.init_equilibrium(lv, rho, u)
+
+
+@pytest.mark.parametrize("collision", ["bgk", "reg"])
+def test_volume_weighted_conservation_exact(collision):
+    g = three_level()
+    g.collision = collision
+    init_random(g, 50)
+    m0 = g.conservation()
+    g.run(6)
+    m1 = g.conservation()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
+    assert np.all(np.abs(m1[1:] - m0[1:]) < 1e-12 * m0[0])
+
+
+def test_uniform_state_is_stationary():
+    g = three_level(0.57)
+    for lv in range(3):
+        nx, ny, nz = g.dims(lv)
+        rho = np.full((nz, ny, nx), 1.01)
+        u = np.zeros((3, nz, ny, nx))
+        u[:] = np.array([0.02, -0.01, 0.03])[:, None, None, None]
+        g.init_equilibrium(lv, rho, u)
+    f0 = [a.copy() for a in g.f]
+    g.run(3)
+    for a, b in zip(f0, g.f):
+        assert np.max(np.abs(a - b)) < 1e-15
+
+
+def test_single_level_equals_plain_oracle():
+    g = mr.MultiRes(np.zeros((1, 1, 1), int), 1, 12, 0.6)
+    rho, u = wl.random_fields((12, 12, 12), seed=51)
+    g.init_equilibrium(0, rho, u)
+    g.run(5)
+    ref = olbm.run(olbm.init_equilibrium(rho, u), np.zeros((12, 12, 12), np.uint8), 0.6, 5,
+                   periodic=(True, True, True))
+    assert np.max(np.abs(g.f[0] - ref)) < 1e-15
+    # every region on level 1: a plain coarse run with tau_1
+    g = mr.MultiRes(np.ones((2, 1, 1), int), 2, 8, 0.6)
+    rho, u = wl.random_fields((8, 4, 4), seed=52)
+    g.init_equilibrium(1, rho, u)
+    g.run(4)
+    ref = olbm.run(olbm.init_equilibrium(rho, u), np.zeros((8, 4, 4), np.uint8),
+                   mr.tau_of_level(0.6, 1), 4, periodic=(True, True, True))
+    assert np.max(np.abs(g.f[1] - ref)) < 1e-15
+
+
+def block_mean(a):
+    return mr.subcell_mean(a)
+
+
+def test_far_field_equals_single_resolution():
+    """Coarse voxels beyond the light cone of the level jump evolve exactly as
+    in a pure coarse run; fine voxels likewise as in a pure fine run."""
+    # coarse far field: fine slab z in [16, 24) of a 48-voxel column
+    lmap = np.array([1, 1, 0, 1, 1, 1]).reshape(6, 1, 1)
+    g = mr.MultiRes(lmap, 2, 8, 0.6)
+    rho_f, u_f = wl.random_fields((48, 8, 8), seed=53)
+    rho_c, u_c = block_mean(rho_f), block_mean(u_f)
+    g.init_equilibrium(0, rho_f, u_f)
+    g.init_equilibrium(1, rho_c, u_c)
+    n = 2
+    g.run(n)
+    ref = olbm.run(olbm.init_equilibrium(rho_c, u_c), np.zeros(rho_c.shape, np.uint8),
+                   mr.tau_of_level(0.6, 1), n, periodic=(True, True, True))
+    # coarse z index range of the fine slab: [8, 12); far = distance >= n + 2
+    far = [z for z in range(24) if min(abs(z - 8), abs(z - 11), 24 - abs(z - 8)) >= n + 2
+           and not 8 <= z < 12]
+    assert far
+    assert np.max(np.abs(g.f[1][:, far] - ref[:, far])) < 1e-14
+    # fine far field: fine slab z in [8, 32)
+    lmap = np.array([1, 0, 0, 0, 1, 1]).reshape(6, 1, 1)
+    g = mr.MultiRes(lmap, 2, 8, 0.6)
+    g.init_equilibrium(0, rho_f, u_f)
+    g.init_equilibrium(1, rho_c, u_c)
+    g.run(1)
+    ref = olbm.run(olbm.init_equilibrium(rho_f, u_f), np.zeros(rho_f.shape, np.uint8), 0.6, 2,
+                   periodic=(True, True, True))
+    far = list(range(8 + 5, 32 - 5))
+    assert np.max(np.abs(g.f[0][:, far] - ref[:, far])) < 1e-14
+
+
+def test_taylor_green_across_level_jump():
+    """A z-uniform Taylor-Green vortex on two levels (z slabs) decays at the
+    viscous rate -2 nu k^2 on both levels (physical time, finest units)."""
+    n = 32
+    lmap = np.broadcast_to(np.array([0, 0, 1, 1]).reshape(4, 1, 1), (4, 2, 2))
+    g = mr.MultiRes(lmap, 2, 16, 0.6)
+    rho_f, u_f = wl.taylor_green_2d(n, u0=0.01, dims=(n, n, 64))
+    g.init_equilibrium(0, rho_f, u_f)
+    g.init_equilibrium(1, block_mean(rho_f), block_mean(u_f))
+    k = 2 * np.pi / n
+    nu = (0.6 - 0.5) / 3
+
+    def layer_amps(lv):
+        nx, ny, nz = g.dims(lv)
+        x = (np.arange(nx) + 0.5) * 2 ** lv - 0.5     # voxel centres in finest units
+        mode = np.sin(k * x)[None, :] * np.cos(k * x)[:, None]
+        _, v = olbm.state_moments(g.f[lv])
+        return np.array([(v[1][z] * mode).sum() / (mode * mode).sum() for z in range(nz)])
+
+    g.run(20)
+    a20 = [layer_amps(0)[:32], layer_amps(1)[16:]]
+    g.run(20)
+    a40 = [layer_amps(0)[:32], layer_amps(1)[16:]]
+    want = -2 * nu * k * k
+    ratio = [np.log(b / a) / 40.0 / want for a, b in zip(a20, a40)]   # 20 coarse = 40 finest units
+    # layers away from the level jump (>= 6 fine / 3 coarse voxels) decay at the viscous rate
+    assert np.all(np.abs(ratio[0][6:26] - 1) < 1e-2), ratio[0]
+    assert np.all(np.abs(ratio[1][3:13] - 1) < 1e-2), ratio[1]
+    # next to the jump the plain volumetric transfer (no non-equilibrium
+    # rescaling) damps faster, within a bounded band
+    assert np.all(np.abs(ratio[0] - 1) < 0.25) and np.all(np.abs(ratio[1] - 1) < 0.25)
+    assert np.all(np.isfinite(g.conservation()))
