@@ -118,6 +118,22 @@ lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge,
                                   const lbm_allocator* alloc, void* stream,
                                   lbm_grid** out);
 
+/* Multi-resolution grid (Sec. 5; Sec. 6.3), refinement factor 2, level 0 =
+ * finest, 1 <= n_levels <= 4, periodic on every axis (phys->periodic must be
+ * all 1).  level_map (host) gives the owning level of every cube of
+ * C = 8 * 2^(n_levels-1) finest voxels, indexed x fastest over
+ * finest_dims / C cells; finest_dims must be multiples of C and neighbouring
+ * cells (26-neighbourhood, periodic) may differ by at most one level.
+ * Each level is an 8^3-block sparse grid in its own voxel units; per level,
+ * blocks with a D3Q19 neighbour on another level (G_c) are numbered first,
+ * then the others (G_i), each in Morton order.  Level l relaxes with
+ * tau_l = 1/2 + (tau - 1/2) / 2^l (acoustic scaling, one viscosity) and
+ * advances 2^(n_levels-1-l) times per lbm_step step. */
+lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
+                                    const uint8_t* level_map, const lbm_physics* phys,
+                                    const lbm_allocator* alloc, void* stream,
+                                    lbm_grid** out);
+
 lbm_status lbm_grid_destroy(lbm_grid* g);
 
 lbm_status lbm_get_info(const lbm_grid* g, lbm_info* out);

@@ -77,3 +77,72 @@ def block_tables(flags, block_edge=8, periodic=(False, False, False)):
                         nbr[b, k] = index.get(tuple(q), -1)
     return {"coords": coords, "n_boundary": n_boundary, "nbr": nbr,
             "dims_blocks": dims_b}
+
+
+def multires_tables(level_map, n_levels, cell, block_edge=8):
+    """Brute-force multi-resolution block tables (periodic box).
+
+    Reading (Sec. 5; Sec. 6.3): level l owns the regions the level map gives
+    it; each level is cut into blocks of block_edge voxels of that level.  A
+    voxel has distance 0 (property P_d) iff one of its D3Q19 neighbours is
+    owned by another level; a block is G_c iff it holds such a voxel, else
+    G_i.  Numbering per level: G_c blocks first, then G_i, each in Morton
+    order.  Returns one dict per level with coords, n_c, nbr (27 same-level
+    neighbours, -1 = none), xnbr_coarse (27: level-(l+1) block covering the
+    neighbour region, else -1) and xnbr_fine (27 x 8: the level-(l-1) blocks
+    covering the neighbour region, octant j = x + 2y + 4z, else -1).
+    """
+    from .lattice import C
+    level_map = np.asarray(level_map)
+    B = block_edge
+    own = []
+    for lv in range(n_levels):
+        r = cell // (2 ** lv)
+        own.append(level_map.repeat(r, 0).repeat(r, 1).repeat(r, 2))
+    out = []
+    bmaps = []
+    for lv in range(n_levels):
+        o = own[lv]
+        dist0 = np.zeros(o.shape, bool)
+        for i in range(1, 19):
+            cx, cy, cz = (int(v) for v in C[i])
+            dist0 |= np.roll(o, shift=(cz, cy, cx), axis=(0, 1, 2)) != lv
+        dist0 &= o == lv
+        nz, ny, nx = o.shape
+        nbz, nby, nbx = nz // B, ny // B, nx // B
+        rows = []
+        for bz in range(nbz):
+            for by in range(nby):
+                for bx in range(nbx):
+                    sl = (slice(bz * B, (bz + 1) * B), slice(by * B, (by + 1) * B),
+                          slice(bx * B, (bx + 1) * B))
+                    if (o[sl] == lv).any():
+                        gc = bool(dist0[sl].any())
+                        rows.append(((0 if gc else 1, morton_code(bx, by, bz)), (bx, by, bz), gc))
+        rows.sort(key=lambda r: r[0])
+        coords = np.array([r[1] for r in rows], dtype=np.int32).reshape(-1, 3)
+        bmap = {tuple(int(v) for v in c): b for b, c in enumerate(coords)}
+        bmaps.append(bmap)
+        out.append({"coords": coords, "n_c": sum(1 for r in rows if r[2]),
+                    "dims_blocks": (nbx, nby, nbz)})
+    for lv in range(n_levels):
+        t = out[lv]
+        nbx, nby, nbz = t["dims_blocks"]
+        nb = len(t["coords"])
+        nbr = np.full((nb, 27), -1, np.int32)
+        xc = np.full((nb, 27), -1, np.int32)
+        xf = np.full((nb, 27, 8), -1, np.int32)
+        for b, c in enumerate(t["coords"]):
+            for k in range(27):
+                dx, dy, dz = k % 3 - 1, (k // 3) % 3 - 1, k // 9 - 1
+                q = ((int(c[0]) + dx) % nbx, (int(c[1]) + dy) % nby, (int(c[2]) + dz) % nbz)
+                nbr[b, k] = bmaps[lv].get(q, -1)
+                owner = own[lv][q[2] * B, q[1] * B, q[0] * B]
+                if owner == lv + 1:
+                    xc[b, k] = bmaps[lv + 1][(q[0] // 2, q[1] // 2, q[2] // 2)]
+                elif owner == lv - 1:
+                    for j in range(8):
+                        f = (2 * q[0] + (j & 1), 2 * q[1] + ((j >> 1) & 1), 2 * q[2] + (j >> 2))
+                        xf[b, k, j] = bmaps[lv - 1][f]
+        t.update(nbr=nbr, xnbr_coarse=xc, xnbr_fine=xf)
+    return out

@@ -75,6 +75,7 @@ def load():
     sig = {
         "lbm_grid_create_dense": [P(I), P(lbm_physics), P(lbm_allocator), vp, P(vp)],
         "lbm_grid_create_sparse": [P(I), I, vp, P(lbm_physics), P(lbm_allocator), vp, P(vp)],
+        "lbm_grid_create_multires": [P(I), I, vp, P(lbm_physics), P(lbm_allocator), vp, P(vp)],
         "lbm_grid_destroy": [vp],
         "lbm_get_info": [vp, P(lbm_info)],
         "lbm_set_schedule": [vp, I],
@@ -227,6 +228,20 @@ def lbm_grid_create_sparse(dims, block_edge, flags, phys, allocator=None, stream
                                       C.c_void_p(fl.ctypes.data), C.byref(phys), ap,
                                       _stream_ptr(stream), C.byref(out)), "lbm_grid_create_sparse")
     return Grid(out, alloc, dims)
+
+
+def lbm_grid_create_multires(finest_dims, n_levels, level_map, phys, allocator=None, stream=None):
+    """level_map: (mz, my, mx) array of owning levels per cube of 8*2^(n_levels-1)
+    finest voxels."""
+    lib = load()
+    lm = np.ascontiguousarray(level_map, dtype=np.uint8)
+    alloc, ap = _alloc_arg(allocator)
+    out = C.c_void_p()
+    _check(lib.lbm_grid_create_multires((C.c_int * 3)(*finest_dims), int(n_levels),
+                                        C.c_void_p(lm.ctypes.data), C.byref(phys), ap,
+                                        _stream_ptr(stream), C.byref(out)),
+           "lbm_grid_create_multires")
+    return Grid(out, alloc, finest_dims)
 
 
 def lbm_grid_destroy(grid):

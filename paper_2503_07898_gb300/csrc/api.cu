@@ -92,6 +92,10 @@ static void free_level(Grid& g, Level& L) {
   cudaStream_t s = g.stream;
   g.dfree(L.f[0], s);
   g.dfree(L.f[1], s);
+  g.dfree(L.f[2], s);
+  g.dfree(L.tmp, s);
+  g.dfree(L.jump_d, s);
+  g.dfree(L.coords_d, s);
   g.dfree(L.flags_d, s);
   g.dfree(L.wmask_d, s);
   g.dfree(L.reg_list_d, s);
@@ -149,7 +153,7 @@ static lbm_status alloc_common(Grid& g) {
 
 static lbm_status alloc_populations(Grid& g, Level& L) {
   L.pop_bytes = (size_t)Q * (size_t)L.n_slots * storage_bytes(g.phys.storage);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < L.nbuf; ++k) {
     L.f[k] = g.dalloc(L.pop_bytes, g.stream);
     if (!L.f[k]) return fail(LBM_ERR_OOM, "population buffer allocation failed");
     LBM_CUDA(cudaMemsetAsync(L.f[k], 0, L.pop_bytes, g.stream));
@@ -348,6 +352,51 @@ lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge, const uint8
   return LBM_OK;
 }
 
+lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
+                                    const uint8_t* level_map, const lbm_physics* phys,
+                                    const lbm_allocator* alloc, void* stream, lbm_grid** out) {
+  set_error("");
+  if (!finest_dims || !level_map) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid* gp = nullptr;
+  lbm_status st = begin(out, phys, alloc, stream, gp);
+  if (st) return st;
+  Grid& g = *gp;
+  g.kind = 2;
+  auto bail = [&](lbm_status s) {
+    free_grid(g);
+    delete *out;
+    *out = nullptr;
+    return s;
+  };
+  if ((st = multires_build(g, finest_dims, n_levels, level_map))) return bail(st);
+  if ((st = alloc_common(g))) return bail(st);
+  for (int l = 0; l < g.n_levels; ++l) {
+    Level& L = g.lv[l];
+    if ((st = alloc_populations(g, L))) return bail(st);
+    std::vector<uint8_t> zeros((size_t)std::max<int64_t>(L.n_slots, L.n_blocks), 0);
+    if ((st = upload(g, &L.flags_d, zeros.data(), (size_t)L.n_slots)) ||
+        (st = upload(g, &L.blk_walls_d, zeros.data(), (size_t)L.n_blocks)) ||
+        (st = upload(g, &L.nbr_d, L.nbr_h.data(), L.nbr_h.size())) ||
+        (st = upload(g, &L.bmap_d, L.bmap_h.data(), L.bmap_h.size())) ||
+        (st = upload(g, &L.coords_d, L.coords_h.data(), L.coords_h.size())) ||
+        (st = upload(g, &L.jump_d, L.jump_h.data(), L.jump_h.size())))
+      return bail(st);
+    L.flags_h.assign((size_t)L.nx * L.ny * L.nz, 0);
+    // voxels of regions owned by other levels are "not in domain" on this level
+    for (int64_t vb = 0; vb < (int64_t)L.bmap_h.size(); ++vb) {
+      if (L.bmap_h[(size_t)vb] >= 0) continue;
+      const int bx = (int)(vb % L.nbx), by = (int)((vb / L.nbx) % L.nby),
+                bz = (int)(vb / ((int64_t)L.nbx * L.nby));
+      for (int l3 = 0; l3 < 512; ++l3) {
+        const int x = bx * 8 + (l3 & 7), y = by * 8 + ((l3 >> 3) & 7), z = bz * 8 + (l3 >> 6);
+        L.flags_h[x + (size_t)L.nx * (y + (size_t)L.ny * z)] = (uint8_t)T_OUTSIDE;
+      }
+    }
+  }
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  return LBM_OK;
+}
+
 lbm_status lbm_grid_destroy(lbm_grid* h) {
   if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
   free_grid(h->g);
@@ -513,7 +562,9 @@ lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
     }
   }
   for (int k = 0; k < n_steps; ++k) {
-    lbm_status st = g.kind == 0 ? dense_step(g, g.lv[0], s) : sparse_step(g, g.lv[0], s);
+    lbm_status st = g.kind == 0   ? dense_step(g, g.lv[0], s)
+                    : g.kind == 1 ? sparse_step(g, g.lv[0], s)
+                                  : multires_step(g, s);
     if (st) return st;
     ++g.steps_done;
   }
@@ -617,8 +668,17 @@ lbm_status lbm_layout_bytes(const lbm_grid* h, int level, int what, size_t* byte
     case LBM_LAYOUT_BLOCK_COORDS: *bytes = L.coords_h.size() * 4; return LBM_OK;
     case LBM_LAYOUT_NBR: *bytes = L.nbr_h.size() * 4; return LBM_OK;
     case LBM_LAYOUT_BLOCK_MAP: *bytes = L.bmap_h.size() * 4; return LBM_OK;
-    default: return fail(LBM_ERR_UNSUPPORTED, "layout table not available for this grid");
+    case LBM_LAYOUT_XNBR_COARSE:
+      if (g.kind != 2) break;
+      *bytes = L.xnbr_coarse_h.size() * 4;
+      return LBM_OK;
+    case LBM_LAYOUT_XNBR_FINE:
+      if (g.kind != 2) break;
+      *bytes = L.xnbr_fine_h.size() * 4;
+      return LBM_OK;
+    default: break;
   }
+  return fail(LBM_ERR_UNSUPPORTED, "layout table not available for this grid");
 }
 
 lbm_status lbm_get_layout(const lbm_grid* h, int level, int what, void* dst, size_t bytes) {
@@ -630,7 +690,9 @@ lbm_status lbm_get_layout(const lbm_grid* h, int level, int what, void* dst, siz
   const void* src = what == LBM_LAYOUT_FLAGS ? (const void*)L.flags_h.data()
                     : what == LBM_LAYOUT_BLOCK_COORDS ? (const void*)L.coords_h.data()
                     : what == LBM_LAYOUT_NBR ? (const void*)L.nbr_h.data()
-                                             : (const void*)L.bmap_h.data();
+                    : what == LBM_LAYOUT_BLOCK_MAP ? (const void*)L.bmap_h.data()
+                    : what == LBM_LAYOUT_XNBR_COARSE ? (const void*)L.xnbr_coarse_h.data()
+                                                     : (const void*)L.xnbr_fine_h.data();
   if (need) std::memcpy(dst, src, need);
   return LBM_OK;
 }

@@ -87,7 +87,26 @@ __device__ __forceinline__ void store_all(typename Codec<S>::T* __restrict__ fou
   });
 }
 
-template <int S, int COLL>
+// Lean pull for rows whose y and z neighbours are all inside the box (no
+// wrap, no wall): one precomputed offset per direction, x edges handled by
+// predicated selects.  IDX is int32_t when 19 N fits in 31 bits.
+template <int S, class IDX>
+__device__ __forceinline__ void pull_row_interior(const typename Codec<S>::T* __restrict__ fin,
+                                                  const DenseArgs& a, int x, IDX v, float g[Q]) {
+  const IDX N = (IDX)a.N, nx = (IDX)a.nx, plane = (IDX)a.nx * (IDX)a.ny;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    IDX src = (IDX)I * N + v - ((IDX)cx(I) + (IDX)cy(I) * nx + (IDX)cz(I) * plane);
+    if constexpr (cx(I) > 0) {
+      if (x == 0) src = a.px ? src + nx : (IDX)opp(I) * N + v;
+    } else if constexpr (cx(I) < 0) {
+      if (x == a.nx - 1) src = a.px ? src - nx : (IDX)opp(I) * N + v;
+    }
+    g[I] = Codec<S>::template load<I>(fin[src]);
+  });
+}
+
+template <int S, int COLL, class IDX>
 __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
   using T = typename Codec<S>::T;
   const int x = blockIdx.x * 32 + threadIdx.x;
@@ -96,15 +115,26 @@ __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
   if (x >= a.nx || y >= a.ny) return;
   const int64_t v = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
   if (v >= a.vend) return;
-  uint32_t wm = 0;
-  if (a.wmask) {
-    wm = a.wmask[v];
-    if (wm & (WM_SKIP | WM_REG)) return;
-  }
   float g[Q];
-  pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
+  // warp-uniform choice: a warp holds one (y, z) row
+  const bool lean = !a.wmask && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1;
+  if (lean) {
+    pull_row_interior<S, IDX>((const T*)a.fin, a, x, (IDX)v, g);
+  } else {
+    uint32_t wm = 0;
+    if (a.wmask) {
+      wm = a.wmask[v];
+      if (wm & (WM_SKIP | WM_REG)) return;
+    }
+    pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
+  }
   collide<COLL>(g, a.omega);
-  store_all<S>((T*)a.fout, a, v, g);
+  T* __restrict__ fout = (T*)a.fout;
+  const IDX N = (IDX)a.N;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    fout[(IDX)I * N + (IDX)v] = Codec<S>::template store<I>(g[I]);
+  });
 }
 
 // ------------------------------------------------------------------------
@@ -308,7 +338,10 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
       prof_end(g, s, pr);
     } else if (zc > 0) {
       const int pr = prof_begin(g, s, "dense_interior", L.n_updated - L.n_reg);
-      dense_interior<S, COLL><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
+      if ((int64_t)Q * L.n_slots < (1LL << 31))
+        dense_interior<S, COLL, int32_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
+      else
+        dense_interior<S, COLL, int64_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
       prof_end(g, s, pr);
     }
     if (L.n_reg > 0) {

@@ -38,8 +38,18 @@ struct Level {
   int64_t n_upd_b = 0;        // updated voxels inside boundary blocks (sparse)
   int64_t n_reg = 0;          // regularized voxels
   size_t pop_bytes = 0;       // bytes of one population buffer (19 arrays)
-  void* f[2] = {nullptr, nullptr};
+  void* f[3] = {nullptr, nullptr, nullptr};
+  int nbuf = 2;               // 2 (ping-pong) or 3 (ring, multi-resolution levels)
   int cur = 0;                // f[cur] holds the current state
+  void* tmp = nullptr;        // multi-resolution unfused schedule: pre-collision buffer
+
+  // multi-resolution
+  int64_t n_c = 0;                    // G_c blocks (stored first)
+  std::vector<uint8_t> jump_h;        // per block: 0 G_i, 1 finer neighbour, 2 coarser neighbour
+  uint8_t* jump_d = nullptr;
+  int32_t* coords_d = nullptr;
+  std::vector<int32_t> xnbr_coarse_h; // n_blocks x 27
+  std::vector<int32_t> xnbr_fine_h;   // n_blocks x 27 x 8
 
   // host tables
   std::vector<uint8_t> flags_h;       // virtual box
@@ -58,7 +68,7 @@ struct Level {
   int32_t* bmap_d = nullptr;
   uint8_t* blk_walls_d = nullptr; // sparse: 1 if block or its halo has a wall voxel
 
-  int variant = 0;                // kernel variant (VARIANT_*), set by lbm_set_variant / autotune
+  int variant = VARIANT_SCALAR;   // kernel variant (VARIANT_*), set by lbm_set_variant / autotune
 
   // dense grouping
   bool dense_has_flags = false;   // any non-fluid voxel
@@ -103,6 +113,12 @@ void prof_clear(Grid& g);
 // Kernel launchers (defined in the .cu files) -------------------------------
 lbm_status dense_step(Grid& g, Level& L, cudaStream_t s);
 lbm_status sparse_step(Grid& g, Level& L, cudaStream_t s);
+// sparse fused kernel over blocks [b0, b1) of L with relaxation omega (no walls)
+lbm_status sparse_uniform_range(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin,
+                                void* fout, float omega, cudaStream_t s, const char* name,
+                                int64_t units);
+lbm_status multires_build(Grid& g, const int finest[3], int n_levels, const uint8_t* level_map);
+lbm_status multires_step(Grid& g, cudaStream_t s);
 lbm_status launch_init_equilibrium(Grid& g, Level& L, const double* rho, const double* u,
                                    cudaStream_t s);
 lbm_status launch_moments(Grid& g, Level& L, double* rho, double* u, cudaStream_t s);

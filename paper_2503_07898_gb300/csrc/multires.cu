@@ -1,0 +1,425 @@
+// multires.cu - multi-resolution grids: layout, interface kernels, schedule.
+//
+// Disaggregation of a multi-resolution grid (Sec. 5; Sec. 6.3):
+//   definition     P_d, the distance of a voxel to a resolution jump; 0 means
+//                  a D3Q19 neighbour belongs to another level.
+//   classification per level, G_c = blocks holding a voxel at distance 0,
+//                  G_i = all other blocks.
+//   mapping        per level an 8^3-block sparse grid; G_c blocks first,
+//                  then G_i, each in Morton order.
+//   operations     G_i blocks run the lean fused stream-collide kernel of the
+//                  sparse grid at every level (no cross-level data); G_c
+//                  blocks run mr_interface, which evaluates explosion and
+//                  coalescence per voxel.
+//
+// Time stepping (refinement factor 2, acoustic scaling): one step of level l
+// contains two steps of level l-1.  Across a level jump the exchange is the
+// level-(l-1) streaming of the two substeps, every level-l voxel being
+// represented by 8 virtual subcells that hold its post-collision populations
+// C at the start of its step and stream without colliding:
+//   explosion   a level-(l-1) voxel pulling from a level-l region reads
+//               C (substep 1) or, in substep 2, what that virtual subcell
+//               received in substep 1: F0 (finer state at the step start)
+//               when its source is a level-(l-1) voxel, else C;
+//   coalescence a level-l voxel next to level l-1 pulls, per direction, the
+//               mean of what its 8 subcells receive in substep 2: F1 (finer
+//               state after substep 1) or the substep-1 value as above.
+// Each non-coarsest level keeps a ring of three buffers, so F0 and F1 are
+// still in memory when the coarser level coalesces: no copies.
+//
+// LBM_SCHEDULE_MONOLITHIC selects the unfused baseline of Sec. 6.3: at every
+// level but the finest, all blocks run a stream kernel (pre-collision values
+// to a scratch buffer) and then a collide kernel.  Both schedules perform the
+// same arithmetic; in FP32 storage their results are bit-identical.
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "grid.h"
+#include "layout.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- host layout
+
+static inline int wrapi(int v, int n) { return ((v % n) + n) % n; }
+
+lbm_status multires_build(Grid& g, const int fin[3], int L, const uint8_t* lmap) {
+  if (L < 1 || L > 4) return fail(LBM_ERR_INVALID, "n_levels must be 1..4");
+  const int C = 8 << (L - 1);  // level-map cell (finest voxels) = coarsest block
+  for (int a = 0; a < 3; ++a) {
+    if (fin[a] <= 0 || fin[a] % C) return fail(LBM_ERR_INVALID, "finest dims must be multiples of 8*2^(n_levels-1)");
+    if (!g.phys.periodic[a]) return fail(LBM_ERR_UNSUPPORTED, "multi-resolution grids are periodic");
+  }
+  const int mx = fin[0] / C, my = fin[1] / C, mz = fin[2] / C;
+  auto mapv = [&](int x, int y, int z) {
+    return (int)lmap[wrapi(x, mx) + (size_t)mx * (wrapi(y, my) + (size_t)my * wrapi(z, mz))];
+  };
+  for (int z = 0; z < mz; ++z)
+    for (int y = 0; y < my; ++y)
+      for (int x = 0; x < mx; ++x) {
+        const int lv = mapv(x, y, z);
+        if (lv >= L) return fail(LBM_ERR_INVALID, "level map value >= n_levels");
+        for (int k = 0; k < 27; ++k) {
+          const int o = mapv(x + k % 3 - 1, y + (k / 3) % 3 - 1, z + k / 9 - 1);
+          if (std::abs(o - lv) > 1) return fail(LBM_ERR_INVALID, "level map violates 2:1 grading");
+        }
+      }
+  g.n_levels = L;
+  // owner level of the level-l block (bx, by, bz)
+  auto owner = [&](int l, int bx, int by, int bz) {
+    const int s = (8 << l) ;  // block edge in finest voxels
+    return mapv(bx * s / C - (bx * s < 0 ? 1 : 0), by * s / C - (by * s < 0 ? 1 : 0),
+                bz * s / C - (bz * s < 0 ? 1 : 0));
+  };
+  // pass 1: per level active blocks, jump type, order, block maps
+  for (int l = 0; l < L; ++l) {
+    Level& V = g.lv[l];
+    V.E = 8;
+    V.nx = fin[0] >> l;
+    V.ny = fin[1] >> l;
+    V.nz = fin[2] >> l;
+    V.nbx = V.nx / 8;
+    V.nby = V.ny / 8;
+    V.nbz = V.nz / 8;
+    V.nbuf = 3;
+    std::vector<int64_t> ids;
+    std::vector<uint8_t> jt;
+    const int64_t nvb = (int64_t)V.nbx * V.nby * V.nbz;
+    std::vector<uint8_t> jump_v((size_t)nvb, 0);
+    for (int64_t vb = 0; vb < nvb; ++vb) {
+      const int bx = (int)(vb % V.nbx), by = (int)((vb / V.nbx) % V.nby),
+                bz = (int)(vb / ((int64_t)V.nbx * V.nby));
+      if (owner(l, bx, by, bz) != l) continue;
+      int j = 0;
+      for (int k = 0; k < 27; ++k) {
+        const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+        if (std::abs(dx) + std::abs(dy) + std::abs(dz) == 0 ||
+            std::abs(dx) + std::abs(dy) + std::abs(dz) == 3)
+          continue;  // D3Q19 reaches face and edge neighbours only
+        const int o = owner(l, wrapi(bx + dx, V.nbx), wrapi(by + dy, V.nby), wrapi(bz + dz, V.nbz));
+        if (o == l) continue;
+        const int t = o < l ? 1 : 2;
+        if (j && j != t) return fail(LBM_ERR_INVALID, "a block touches a finer and a coarser level");
+        j = t;
+      }
+      jump_v[(size_t)vb] = (uint8_t)j;
+      ids.push_back(vb);
+    }
+    auto key = [&](int64_t vb) {
+      const uint32_t bx = (uint32_t)(vb % V.nbx), by = (uint32_t)((vb / V.nbx) % V.nby),
+                     bz = (uint32_t)(vb / ((int64_t)V.nbx * V.nby));
+      return ((uint64_t)(jump_v[(size_t)vb] ? 0 : 1) << 32) | morton3(bx, by, bz);
+    };
+    std::sort(ids.begin(), ids.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+    V.n_blocks = (int64_t)ids.size();
+    V.n_c = 0;
+    V.bmap_h.assign((size_t)nvb, -1);
+    V.coords_h.resize((size_t)V.n_blocks * 3);
+    V.jump_h.resize((size_t)V.n_blocks);
+    for (int64_t b = 0; b < V.n_blocks; ++b) {
+      const int64_t vb = ids[(size_t)b];
+      V.bmap_h[(size_t)vb] = (int32_t)b;
+      V.coords_h[(size_t)b * 3 + 0] = (int32_t)(vb % V.nbx);
+      V.coords_h[(size_t)b * 3 + 1] = (int32_t)((vb / V.nbx) % V.nby);
+      V.coords_h[(size_t)b * 3 + 2] = (int32_t)(vb / ((int64_t)V.nbx * V.nby));
+      V.jump_h[(size_t)b] = jump_v[(size_t)vb];
+      if (jump_v[(size_t)vb]) ++V.n_c;
+    }
+    V.n_b = V.n_c;
+    V.n_slots = V.n_blocks * 512;
+    V.n_updated = V.n_slots;
+  }
+  // pass 2: neighbour tables (same level, coarser, finer)
+  for (int l = 0; l < L; ++l) {
+    Level& V = g.lv[l];
+    V.nbr_h.assign((size_t)V.n_blocks * 27, -1);
+    V.xnbr_coarse_h.assign((size_t)V.n_blocks * 27, -1);
+    V.xnbr_fine_h.assign((size_t)V.n_blocks * 27 * 8, -1);
+    for (int64_t b = 0; b < V.n_blocks; ++b)
+      for (int k = 0; k < 27; ++k) {
+        const int qx = wrapi(V.coords_h[b * 3] + k % 3 - 1, V.nbx);
+        const int qy = wrapi(V.coords_h[b * 3 + 1] + (k / 3) % 3 - 1, V.nby);
+        const int qz = wrapi(V.coords_h[b * 3 + 2] + k / 9 - 1, V.nbz);
+        V.nbr_h[(size_t)b * 27 + k] = V.bmap_h[qx + (size_t)V.nbx * (qy + (size_t)V.nby * qz)];
+        const int o = owner(l, qx, qy, qz);
+        if (o == l + 1) {
+          const Level& W = g.lv[l + 1];
+          V.xnbr_coarse_h[(size_t)b * 27 + k] =
+              W.bmap_h[(qx >> 1) + (size_t)W.nbx * ((qy >> 1) + (size_t)W.nby * (qz >> 1))];
+        } else if (o == l - 1) {
+          const Level& W = g.lv[l - 1];
+          for (int j = 0; j < 8; ++j) {
+            const int fx = 2 * qx + (j & 1), fy = 2 * qy + ((j >> 1) & 1), fz = 2 * qz + (j >> 2);
+            V.xnbr_fine_h[((size_t)b * 27 + k) * 8 + j] =
+                W.bmap_h[fx + (size_t)W.nbx * (fy + (size_t)W.nby * fz)];
+          }
+        }
+      }
+  }
+  return LBM_OK;
+}
+
+// ------------------------------------------------------------------ kernels
+
+struct MrLv {
+  int nx, ny, nz, nbx, nby;
+  const int32_t* bmap;
+};
+
+struct MrArgs {
+  MrLv me, co, fi;  // this level, coarser level, finer level
+  const int32_t* nbr;
+  const int32_t* coords;
+  const uint8_t* jump;
+  const void* cur;   // this level, start of this step
+  const void* prev;  // this level, start of the coarser step (substep 2 explosion)
+  void* out;
+  const void* ccur;  // coarser level, start of its step
+  const void* ff0;   // finer level at the start of this step
+  const void* ff1;   // finer level after its first substep
+  int k;             // 1 or 2: substep of this level inside the coarser step
+  int64_t b0, b1;    // block range
+  float omega;
+  int* status;
+};
+
+__device__ __forceinline__ int wrapd(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ bool mr_owns(const MrLv& v, int x, int y, int z) {
+  return v.bmap[(x >> 3) + v.nbx * ((y >> 3) + v.nby * (z >> 3))] >= 0;
+}
+
+// Population I at a (wrapped) voxel of a level; a miss is an internal error
+// (recorded, value 0) rather than an out-of-bounds access.
+template <int S, int I>
+__device__ __forceinline__ float mr_load(const void* buf, const MrLv& v, int x, int y, int z,
+                                         int* status) {
+  using T = typename Codec<S>::T;
+  const int b = v.bmap[(x >> 3) + v.nbx * ((y >> 3) + v.nby * (z >> 3))];
+  if (b < 0) {
+    atomicExch(status, (int)LBM_ERR_INTERNAL);
+    return 0.f;
+  }
+  const int64_t idx = ((int64_t)b * Q + I) * 512 + (x & 7) + 8 * ((y & 7) + 8 * (z & 7));
+  return Codec<S>::template load<I>(((const T*)buf)[idx]);
+}
+
+// Explosion: this (finer) level pulls population I of voxel G from a coarser region.
+template <int S, int I>
+__device__ __forceinline__ float explosion(const MrArgs& a, int gx, int gy, int gz) {
+  const int qx = wrapd(gx - cx(I), a.me.nx), qy = wrapd(gy - cy(I), a.me.ny),
+            qz = wrapd(gz - cz(I), a.me.nz);
+  if (a.k == 1) return mr_load<S, I>(a.ccur, a.co, qx >> 1, qy >> 1, qz >> 1, a.status);
+  const int rx = wrapd(qx - cx(I), a.me.nx), ry = wrapd(qy - cy(I), a.me.ny),
+            rz = wrapd(qz - cz(I), a.me.nz);
+  if (mr_owns(a.me, rx, ry, rz)) return mr_load<S, I>(a.prev, a.me, rx, ry, rz, a.status);
+  return mr_load<S, I>(a.ccur, a.co, rx >> 1, ry >> 1, rz >> 1, a.status);
+}
+
+// Coalescence: this (coarser) level pulls population I of voxel G as the mean
+// over its 8 subcells of what they receive in the second finer substep.
+template <int S, int I>
+__device__ __forceinline__ float coalescence(const MrArgs& a, int gx, int gy, int gz) {
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int rx = wrapd(2 * gx + (j & 1) - cx(I), a.fi.nx);
+    const int ry = wrapd(2 * gy + ((j >> 1) & 1) - cy(I), a.fi.ny);
+    const int rz = wrapd(2 * gz + (j >> 2) - cz(I), a.fi.nz);
+    if (mr_owns(a.fi, rx, ry, rz)) {
+      v[j] = mr_load<S, I>(a.ff1, a.fi, rx, ry, rz, a.status);
+    } else {
+      const int sx = wrapd(rx - cx(I), a.fi.nx), sy = wrapd(ry - cy(I), a.fi.ny),
+                sz = wrapd(rz - cz(I), a.fi.nz);
+      v[j] = mr_owns(a.fi, sx, sy, sz) ? mr_load<S, I>(a.ff0, a.fi, sx, sy, sz, a.status)
+                                       : mr_load<S, I>(a.cur, a.me, sx >> 1, sy >> 1, sz >> 1, a.status);
+    }
+  }
+  // pairwise means along x, then y, then z (exact when the 8 values are equal)
+  const float m0 = 0.5f * (v[0] + v[1]), m1 = 0.5f * (v[2] + v[3]);
+  const float m2 = 0.5f * (v[4] + v[5]), m3 = 0.5f * (v[6] + v[7]);
+  const float n0 = 0.5f * (m0 + m1), n1 = 0.5f * (m2 + m3);
+  return 0.5f * (n0 + n1);
+}
+
+template <int S, int COLL, bool SPLIT>
+__global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
+  using T = typename Codec<S>::T;
+  const int64_t b = a.b0 + blockIdx.x / 2;
+  __shared__ int32_t snbr[27];
+  if (b >= a.b1) return;  // uniform per CTA
+  if (threadIdx.x < 27) snbr[threadIdx.x] = a.nbr[b * 27 + threadIdx.x];
+  __syncthreads();
+  const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+  const int gx = a.coords[b * 3] * 8 + lx, gy = a.coords[b * 3 + 1] * 8 + ly,
+            gz = a.coords[b * 3 + 2] * 8 + lz;
+  const int jmp = a.jump[b];
+  const T* __restrict__ cur = (const T*)a.cur;
+  float g[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+    const int dx = sx < 0 ? -1 : (sx > 7 ? 1 : 0);
+    const int dy = sy < 0 ? -1 : (sy > 7 ? 1 : 0);
+    const int dz = sz < 0 ? -1 : (sz > 7 ? 1 : 0);
+    const int64_t nb = (dx | dy | dz) ? (int64_t)snbr[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] : b;
+    bool plain = nb >= 0;
+    if constexpr ((cx(I) != 0) + (cy(I) != 0) + (cz(I) != 0) == 2) {
+      // a coarse voxel's subcells also trace through the two face neighbours
+      // of a 2D-diagonal direction; all of them must be on this level
+      if (plain && jmp == 1) {
+        if (dx && snbr[(dx + 1) + 3 + 9] < 0) plain = false;
+        if (dy && snbr[1 + 3 * (dy + 1) + 9] < 0) plain = false;
+        if (dz && snbr[1 + 3 + 9 * (dz + 1)] < 0) plain = false;
+      }
+    }
+    if (plain) {
+      const int ls = (sx - 8 * dx) + 8 * ((sy - 8 * dy) + 8 * (sz - 8 * dz));
+      g[I] = Codec<S>::template load<I>(cur[(nb * Q + I) * 512 + ls]);
+    } else if (jmp == 2) {
+      g[I] = explosion<S, I>(a, gx, gy, gz);
+    } else {
+      g[I] = coalescence<S, I>(a, gx, gy, gz);
+    }
+  });
+  if constexpr (!SPLIT) collide<COLL>(g, a.omega);
+  T* __restrict__ out = (T*)a.out;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    out[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
+  });
+}
+
+// Unfused baseline: collision of the pre-collision values written by the
+// split stream kernel.
+template <int S, int COLL>
+__global__ void __launch_bounds__(256) mr_collide(const void* tmp, void* out, int64_t b0,
+                                                  int64_t b1, float omega) {
+  using T = typename Codec<S>::T;
+  const int64_t b = b0 + blockIdx.x / 2;
+  if (b >= b1) return;
+  const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
+  const T* in = (const T*)tmp;
+  float g[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    g[I] = Codec<S>::template load<I>(in[(b * Q + I) * 512 + l]);
+  });
+  collide<COLL>(g, omega);
+  T* o = (T*)out;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    o[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
+  });
+}
+
+// ----------------------------------------------------------------- schedule
+
+static MrLv view(const Level& V) {
+  MrLv m;
+  m.nx = V.nx;
+  m.ny = V.ny;
+  m.nz = V.nz;
+  m.nbx = V.nbx;
+  m.nby = V.nby;
+  m.bmap = V.bmap_d;
+  return m;
+}
+
+static const char* kname(int kind, int l) {
+  static const char* names[4][4] = {
+      {"mr_uniform_l0", "mr_uniform_l1", "mr_uniform_l2", "mr_uniform_l3"},
+      {"mr_interface_l0", "mr_interface_l1", "mr_interface_l2", "mr_interface_l3"},
+      {"mr_stream_split_l0", "mr_stream_split_l1", "mr_stream_split_l2", "mr_stream_split_l3"},
+      {"mr_collide_l0", "mr_collide_l1", "mr_collide_l2", "mr_collide_l3"}};
+  return names[kind][l];
+}
+
+template <int S, int COLL>
+static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
+  Level& V = g.lv[l];
+  const double tau_l = 0.5 + (g.phys.tau - 0.5) / (double)(1 << l);
+  const float omega = (float)(1.0 / tau_l);
+  const int c = V.cur, nx = (c + 1) % 3, pv = (c + 2) % 3;
+  const bool unfused = g.phys.schedule == LBM_SCHEDULE_MONOLITHIC && l > 0;
+  lbm_status st;
+  // G_i blocks need no cross-level data: launched before the finer substeps
+  if (!unfused && V.n_blocks > V.n_c) {
+    st = sparse_uniform_range(g, V, V.n_c, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
+                              (V.n_blocks - V.n_c) * 512);
+    if (st) return st;
+  }
+  if (l > 0) {
+    if ((st = mr_advance<S, COLL>(g, l - 1, 1, s))) return st;
+    if ((st = mr_advance<S, COLL>(g, l - 1, 2, s))) return st;
+  }
+  MrArgs a{};
+  a.me = view(V);
+  a.nbr = V.nbr_d;
+  a.coords = V.coords_d;
+  a.jump = V.jump_d;
+  a.cur = V.f[c];
+  a.prev = V.f[pv];
+  a.k = k;
+  a.omega = omega;
+  a.status = g.status_d;
+  if (l + 1 < g.n_levels) {
+    const Level& W = g.lv[l + 1];
+    a.co = view(W);
+    a.ccur = W.f[W.cur];
+  }
+  if (l > 0) {
+    const Level& W = g.lv[l - 1];
+    a.fi = view(W);
+    a.ff1 = W.f[(W.cur + 2) % 3];
+    a.ff0 = W.f[(W.cur + 1) % 3];
+  }
+  if (unfused) {
+    a.b0 = 0;
+    a.b1 = V.n_blocks;
+    a.out = V.tmp;
+    if (V.n_blocks > 0) {
+      const unsigned nb = (unsigned)(2 * V.n_blocks);
+      int pr = prof_begin(g, s, kname(2, l), V.n_blocks * 512);
+      mr_interface<S, COLL, true><<<nb, 256, 0, s>>>(a);
+      prof_end(g, s, pr);
+      pr = prof_begin(g, s, kname(3, l), V.n_blocks * 512);
+      mr_collide<S, COLL><<<nb, 256, 0, s>>>(V.tmp, V.f[nx], 0, V.n_blocks, omega);
+      prof_end(g, s, pr);
+    }
+  } else if (V.n_c > 0) {
+    a.b0 = 0;
+    a.b1 = V.n_c;
+    a.out = V.f[nx];
+    const int pr = prof_begin(g, s, kname(1, l), V.n_c * 512);
+    mr_interface<S, COLL, false><<<(unsigned)(2 * V.n_c), 256, 0, s>>>(a);
+    prof_end(g, s, pr);
+  }
+  LBM_CUDA(cudaGetLastError());
+  V.cur = nx;
+  return LBM_OK;
+}
+
+lbm_status multires_step(Grid& g, cudaStream_t s) {
+  const int top = g.n_levels - 1;
+  if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
+    for (int l = 1; l < g.n_levels; ++l) {
+      Level& V = g.lv[l];
+      if (!V.tmp && V.n_blocks > 0) {
+        V.tmp = g.dalloc(V.pop_bytes, s);
+        if (!V.tmp) return fail(LBM_ERR_OOM, "unfused scratch allocation failed");
+      }
+    }
+  }
+  const bool bgk = g.phys.collision == C_BGK;
+  switch (g.phys.storage) {
+    case S_F32: return bgk ? mr_advance<S_F32, C_BGK>(g, top, 1, s) : mr_advance<S_F32, C_REG>(g, top, 1, s);
+    case S_F16: return bgk ? mr_advance<S_F16, C_BGK>(g, top, 1, s) : mr_advance<S_F16, C_REG>(g, top, 1, s);
+    default: return bgk ? mr_advance<S_BF16, C_BGK>(g, top, 1, s) : mr_advance<S_BF16, C_REG>(g, top, 1, s);
+  }
+}
+
+}  // namespace lbm

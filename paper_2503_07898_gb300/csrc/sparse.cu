@@ -326,6 +326,42 @@ static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
   return LBM_OK;
 }
 
+template <int S, int COLL>
+static void uniform_range_t(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin, void* fout,
+                            float omega, cudaStream_t s, const char* name, int64_t units) {
+  SparseArgs a{};
+  a.fin = fin;
+  a.fout = fout;
+  a.nbr = L.nbr_d;
+  a.flags = L.flags_d;
+  a.blk_walls = L.blk_walls_d;
+  a.omega = omega;
+  a.s0 = b0 * 512;
+  a.s1 = b1 * 512;
+  launch_range<S, 8, COLL, MODE_INTERIOR>(g, a, s, name, units);
+}
+
+lbm_status sparse_uniform_range(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin,
+                                void* fout, float omega, cudaStream_t s, const char* name,
+                                int64_t units) {
+  const bool bgk = g.phys.collision == C_BGK;
+  switch (g.phys.storage) {
+    case S_F32:
+      bgk ? uniform_range_t<S_F32, C_BGK>(g, L, b0, b1, fin, fout, omega, s, name, units)
+          : uniform_range_t<S_F32, C_REG>(g, L, b0, b1, fin, fout, omega, s, name, units);
+      break;
+    case S_F16:
+      bgk ? uniform_range_t<S_F16, C_BGK>(g, L, b0, b1, fin, fout, omega, s, name, units)
+          : uniform_range_t<S_F16, C_REG>(g, L, b0, b1, fin, fout, omega, s, name, units);
+      break;
+    default:
+      bgk ? uniform_range_t<S_BF16, C_BGK>(g, L, b0, b1, fin, fout, omega, s, name, units)
+          : uniform_range_t<S_BF16, C_REG>(g, L, b0, b1, fin, fout, omega, s, name, units);
+  }
+  LBM_CUDA(cudaGetLastError());
+  return LBM_OK;
+}
+
 template <int S, int E>
 static lbm_status sparse_step_e(Grid& g, Level& L, cudaStream_t s) {
   return g.phys.collision == C_BGK ? sparse_step_t<S, E, C_BGK>(g, L, s)

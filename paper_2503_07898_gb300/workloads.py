@@ -115,3 +115,18 @@ def random_obstacles(shape_zyx, seed, solid_fraction=0.1, kind="spheres"):
             m = (abs(x - c[0]) < r) & (abs(y - c[1]) < r) & (abs(z - c[2]) < r)
         flags[np.broadcast_to(m, shape_zyx)] = SOLID
     return flags
+
+
+def multires_slab_map(n=256, n_levels=3):
+    """Level map of the three-level decaying-turbulence workload: a 256^3
+    virtual finest box, level 0 in the central slab z in [96, 160), level 1 in
+    z in [64, 96) u [160, 192), level 2 elsewhere.  One map cell is the
+    coarsest block (8 * 2^(n_levels-1) finest voxels); shape (mz, my, mx)."""
+    cell = 8 * 2 ** (n_levels - 1)
+    m = n // cell
+    zlev = np.full(m, 2, np.uint8)
+    z = (np.arange(m) * cell)
+    zlev[(z >= 64) & (z < 96)] = 1
+    zlev[(z >= 160) & (z < 192)] = 1
+    zlev[(z >= 96) & (z < 160)] = 0
+    return np.ascontiguousarray(np.broadcast_to(zlev[:, None, None], (m, m, m)))

@@ -1,0 +1,156 @@
+"""GPU: multi-resolution grids against the FP64 multi-resolution oracle.
+
+Parity cases use level maps with every level jump of the 3-level turbulence
+workload (coarse - middle - fine - middle along z) at the smallest sizes the
+8^3-block layout allows; the full 256^3 three-level workload is checked by
+properties that hold at any size (exact volume-weighted conservation up to
+FP32 rounding, fused == unfused bit for bit, voxel counts).
+"""
+import numpy as np
+import pytest
+
+from cases import F32_RTOL
+from oracle import layout as olayout
+from oracle import multires as omr
+from paper_2503_07898_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def make_mr(lbm, lmap, n_levels, tau, schedule="disaggregated", storage="f32", collision="bgk"):
+    cell = 8 * 2 ** (n_levels - 1)
+    mz, my, mx = lmap.shape
+    dims = (mx * cell, my * cell, mz * cell)
+    g = lbm.lbm_grid_create_multires(dims, n_levels, lmap, lbm.physics(
+        tau, collision, storage, (1, 1, 1), schedule))
+    return g, dims, cell
+
+
+def level_fields(dims, n_levels, seed):
+    out = []
+    for lv in range(n_levels):
+        nx, ny, nz = (d >> lv for d in dims)
+        out.append(wl.random_fields((nz, ny, nx), seed=seed + lv, u_amp=0.02))
+    return out
+
+
+def init_both(lbm, g, o, fields):
+    for lv, (rho, u) in enumerate(fields):
+        lbm.lbm_init_equilibrium(g, lv, rho, u)
+        o.init_equilibrium(lv, rho, u)
+
+
+def compare(lbm, g, o, n_levels):
+    worst = 0.0
+    for lv in range(n_levels):
+        f = lbm.lbm_get_populations_f64(g, lv)
+        m = o.own[lv] == lv
+        assert np.all(np.isfinite(f[:, m]))
+        assert np.all(np.isnan(f[:, ~m]))
+        ref = o.f[lv][:, m]
+        worst = max(worst, float(np.max(np.abs(f[:, m] - ref) / np.abs(ref))))
+    return worst
+
+
+LMAP3 = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
+LMAP2 = np.array([1, 0, 0, 1], np.uint8).reshape(4, 1, 1)
+
+
+@pytest.mark.parametrize("schedule", ["disaggregated", "monolithic"])
+def test_two_level_parity(lbm, schedule):
+    g, dims, cell = make_mr(lbm, LMAP2, 2, 0.6, schedule)
+    o = omr.MultiRes(LMAP2, 2, cell, 0.6)
+    init_both(lbm, g, o, level_fields(dims, 2, 60))
+    lbm.lbm_step(g, 20)
+    o.run(20)
+    assert compare(lbm, g, o, 2) <= F32_RTOL
+
+
+@pytest.mark.parametrize("collision", ["bgk", "reg"])
+def test_three_level_parity(lbm, collision):
+    g, dims, cell = make_mr(lbm, LMAP3, 3, 0.58, collision=collision)
+    o = omr.MultiRes(LMAP3, 3, cell, 0.58, collision)
+    init_both(lbm, g, o, level_fields(dims, 3, 61))
+    lbm.lbm_step(g, 8)
+    o.run(8)
+    assert compare(lbm, g, o, 3) <= F32_RTOL
+
+
+def test_layout_bit_exact(lbm):
+    lmap = np.zeros((4, 2, 2), np.uint8)
+    lmap[:, 0, 0] = [2, 1, 0, 1]
+    lmap[:, 1, 1] = [1, 1, 0, 1]
+    lmap[:, 0, 1] = [2, 1, 1, 1]
+    lmap[:, 1, 0] = [1, 1, 1, 1]
+    g, dims, cell = make_mr(lbm, lmap, 3, 0.6)
+    tab = olayout.multires_tables(lmap, 3, cell)
+    info = lbm.lbm_get_info(g)
+    for lv in range(3):
+        t = tab[lv]
+        assert info["n_group_b"][lv] == t["n_c"]
+        assert info["n_blocks"][lv] == len(t["coords"])
+        get = lambda what: lbm.lbm_get_layout(g, lv, what)
+        assert get(lbm.LBM_LAYOUT_BLOCK_COORDS).tobytes() == t["coords"].tobytes()
+        assert get(lbm.LBM_LAYOUT_NBR).tobytes() == t["nbr"].tobytes()
+        assert get(lbm.LBM_LAYOUT_XNBR_COARSE).tobytes() == t["xnbr_coarse"].tobytes()
+        assert get(lbm.LBM_LAYOUT_XNBR_FINE).tobytes() == t["xnbr_fine"].tobytes()
+
+
+def test_fused_equals_unfused_bit_exact(lbm):
+    fields = level_fields((32, 32, 128), 3, 62)
+    out = []
+    for sched in ("disaggregated", "monolithic"):
+        g, dims, cell = make_mr(lbm, LMAP3, 3, 0.6, sched)
+        for lv, (rho, u) in enumerate(fields):
+            lbm.lbm_init_equilibrium(g, lv, rho, u)
+        lbm.lbm_step(g, 6)
+        out.append([lbm.lbm_get_populations_f64(g, lv) for lv in range(3)])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_volume_weighted_conservation(lbm, storage):
+    g, dims, cell = make_mr(lbm, LMAP3, 3, 0.6, storage=storage)
+    for lv, (rho, u) in enumerate(level_fields(dims, 3, 63)):
+        lbm.lbm_init_equilibrium(g, lv, rho, u)
+    m0 = lbm.lbm_conservation(g)
+    lbm.lbm_step(g, 10)
+    m1 = lbm.lbm_conservation(g)
+    tol = 1e-6 if storage == "f32" else 2e-5
+    assert abs(m1[0] - m0[0]) / m0[0] <= tol
+    assert np.all(np.abs(m1[1:] - m0[1:]) <= tol * m0[0])
+
+
+def test_uniform_state_stays_uniform(lbm):
+    g, dims, cell = make_mr(lbm, LMAP3, 3, 0.57)
+    for lv in range(3):
+        nx, ny, nz = (d >> lv for d in dims)
+        u = np.zeros((3, nz, ny, nx))
+        u[:] = np.array([0.02, -0.01, 0.03])[:, None, None, None]
+        lbm.lbm_init_equilibrium(g, lv, np.full((nz, ny, nx), 1.01), u)
+    f0 = [lbm.lbm_get_populations_f64(g, lv) for lv in range(3)]
+    lbm.lbm_step(g, 3)
+    for lv in range(3):
+        f = lbm.lbm_get_populations_f64(g, lv)
+        m = np.isfinite(f0[lv][0])
+        assert np.max(np.abs(f[:, m] - f0[lv][:, m])) < 2e-7
+
+
+def test_full_size_three_level_turbulence_properties(lbm):
+    """256^3 virtual finest box, level 0 = slab z in [96,160), level 1 = z in
+    [64,96) u [160,192), level 2 elsewhere (the turbulence workload's layout)."""
+    lmap = wl.multires_slab_map()
+    g, dims, cell = make_mr(lbm, lmap, 3, 0.52)
+    info = lbm.lbm_get_info(g)
+    assert info["n_updated"] == [256 * 256 * 64, 128 * 128 * 32, 64 * 64 * 32]
+    for lv in range(3):
+        nx, ny, nz = (d >> lv for d in dims)
+        rho, u = wl.random_fields((nz, ny, nx), seed=70 + lv, u_amp=0.02)
+        lbm.lbm_init_equilibrium(g, lv, rho, u)
+    m0 = lbm.lbm_conservation(g)
+    lbm.lbm_step(g, 4)
+    m1 = lbm.lbm_conservation(g)
+    assert abs(m1[0] - m0[0]) / m0[0] <= 1e-6
+    assert np.all(np.abs(m1[1:] - m0[1:]) <= 1e-6 * m0[0])
+    lbm.lbm_sync(g)

@@ -163,7 +163,10 @@ def test_moments_and_conservation(lbm):
     ref = run_oracle(flags, None, rho, u, 0.6, 100, periodic=(1, 1, 1))
     rr, vr = olbm.state_moments(ref)
     assert np.max(np.abs(r / rr - 1)) < 1e-6
-    assert velocity_l2(v, vr, flags) < 1e-5
+    # the field has decayed to |u| ~ 1e-3: bound the absolute error (populations
+    # agree to 1e-5 relative, so |du| <~ 18 * 1e-5 * max f_i / rho)
+    assert np.max(np.abs(v - vr)) < 1e-6
+    assert velocity_l2(v, vr, flags) < 1e-3
 
 
 def test_checkpoint_roundtrip_bit_exact(lbm):

@@ -312,3 +312,29 @@ def test_block_tables_neighbour_symmetry_and_sphere_counts():
         for kk in range(27):
             if nbr[b, kk] >= 0:
                 assert nbr[nbr[b, kk], 26 - kk] == b
+
+
+def test_multires_tables_hand_example():
+    """Two levels side by side along x (periodic): level 0 owns x in [0,16),
+    level 1 owns x in [16,32) of a 32 x 16 x 16 finest box."""
+    t = layout.multires_tables(np.array([[[0, 1]]]), 2, 16)
+    assert len(t[0]["coords"]) == 8 and t[0]["n_c"] == 8       # every level-0 block touches level 1
+    assert [tuple(c) for c in t[0]["coords"]] == [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0),
+                                                  (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+    assert [tuple(c) for c in t[1]["coords"]] == [(1, 0, 0)] and t[1]["n_c"] == 1
+    k = lambda dx, dy, dz: (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+    assert list(t[1]["xnbr_fine"][0, k(-1, 0, 0)]) == list(range(8))
+    assert list(t[1]["xnbr_fine"][0, k(1, 0, 0)]) == list(range(8))
+    assert t[1]["nbr"][0, k(0, 1, 0)] == 0 and t[1]["nbr"][0, k(1, 0, 0)] == -1
+    # level-0 block (0,0,0): -x neighbour region is level 1 (periodic wrap), +x is level 0
+    assert t[0]["xnbr_coarse"][0, k(-1, 0, 0)] == 0 and t[0]["nbr"][0, k(1, 0, 0)] == 1
+    assert t[0]["xnbr_coarse"][1, k(1, 0, 0)] == 0
+
+
+def test_multires_tables_interior_blocks_are_gi():
+    """A thick fine slab: only the block layers touching the coarse level are G_c."""
+    lmap = np.array([1, 0, 0, 1]).reshape(4, 1, 1)
+    t = layout.multires_tables(lmap, 2, 32)
+    # level 0 slab z in [32, 96): 8 block layers of 4x4 blocks; layers 4 and 11 touch level 1
+    assert len(t[0]["coords"]) == 8 * 16 and t[0]["n_c"] == 2 * 16
+    assert set(int(c[2]) for c in t[0]["coords"][:32]) == {4, 11}
