@@ -13,6 +13,13 @@
 //   pressure node   u   = ((S0 + 2 S+) / rho_b - 1) n
 //   unknown c_i.n < 0: g_i = f^eq_i + g_opp(i) - f^eq_opp(i), then the
 //   whole node is regularized: f* = f^eq + (1 - omega) 9/2 w_i Q_i:Pi^neq.
+//
+// All arithmetic runs on shifted populations s_i = f_i - w_i held in FP32
+// registers: rho = 1 + sum s, j = sum c s, Pi^neq = sum c c s - (rho-1)/3 I
+// - rho u u.  No O(1) constant enters an FP32 sum, so the rounding of the
+// moment sums is not the same in every voxel and step (with unshifted
+// values, whose low-order bits are those of the FP32 weights, that rounding
+// is systematic and drifts the mass by ~3e-7 per step under 16-bit storage).
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -59,27 +66,26 @@ __host__ __device__ inline bool type_regularized(int t) {
 }
 
 // ------------------------------------------------------------ storage codecs
-// F32 stores f_i.  F16 / BF16 store s_i = f_i - w_i rounded to nearest even;
-// a load returns w_i + s_i in FP32.
+// F32 stores f_i.  F16 / BF16 store s_i = f_i - w_i rounded to nearest even.
+// load<I> returns the shifted value s_i in FP32, store<I> takes it; abs_d
+// returns the absolute f_i in FP64 (moments, reductions).
 enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
 
 template <int S> struct Codec;
 template <> struct Codec<S_F32> {
   using T = float;
-  template <int I> __device__ static __forceinline__ float load(T v) { return v; }
-  template <int I> __device__ static __forceinline__ T store(float f) { return f; }
-  __device__ static __forceinline__ float load_i(T v, int) { return v; }
+  template <int I> __device__ static __forceinline__ float load(T v) { return v - wf(I); }
+  template <int I> __device__ static __forceinline__ T store(float s) { return wf(I) + s; }
+  __device__ static __forceinline__ double abs_d(T v, int) { return (double)v; }
   __device__ static __forceinline__ T from_double(double f, int) { return (float)f; }
 };
 template <> struct Codec<S_F16> {
   using T = __half;
-  template <int I> __device__ static __forceinline__ float load(T v) {
-    return wf(I) + __half2float(v);
+  template <int I> __device__ static __forceinline__ float load(T v) { return __half2float(v); }
+  template <int I> __device__ static __forceinline__ T store(float s) { return __float2half_rn(s); }
+  __device__ static __forceinline__ double abs_d(T v, int i) {
+    return wd(i) + (double)__half2float(v);
   }
-  template <int I> __device__ static __forceinline__ T store(float f) {
-    return __float2half_rn(f - wf(I));
-  }
-  __device__ static __forceinline__ float load_i(T v, int i) { return wf(i) + __half2float(v); }
   __device__ static __forceinline__ T from_double(double f, int i) {
     return __double2half(f - wd(i));
   }
@@ -87,13 +93,13 @@ template <> struct Codec<S_F16> {
 template <> struct Codec<S_BF16> {
   using T = __nv_bfloat16;
   template <int I> __device__ static __forceinline__ float load(T v) {
-    return wf(I) + __bfloat162float(v);
+    return __bfloat162float(v);
   }
-  template <int I> __device__ static __forceinline__ T store(float f) {
-    return __float2bfloat16_rn(f - wf(I));
+  template <int I> __device__ static __forceinline__ T store(float s) {
+    return __float2bfloat16_rn(s);
   }
-  __device__ static __forceinline__ float load_i(T v, int i) {
-    return wf(i) + __bfloat162float(v);
+  __device__ static __forceinline__ double abs_d(T v, int i) {
+    return wd(i) + (double)__bfloat162float(v);
   }
   __device__ static __forceinline__ T from_double(double f, int i) {
     return __double2bfloat16(f - wd(i));
@@ -110,29 +116,30 @@ template <int N, int I = 0, class F> __device__ __forceinline__ void static_for(
 }
 
 // ------------------------------------------------------------ collision
+// Every function below takes and returns shifted populations s_i = f_i - w_i.
 
-// Moments of a population set.
-__device__ __forceinline__ void moments(const float g[Q], float& rho, float& ux, float& uy,
-                                        float& uz) {
-  float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+// drho = rho - 1 = sum s, j = sum c s.
+__device__ __forceinline__ void moments_s(const float s[Q], float& drho, float& jx, float& jy,
+                                          float& jz) {
+  float r = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    r += g[i];
-    if (cx(i)) jx += cx(i) > 0 ? g[i] : -g[i];
-    if (cy(i)) jy += cy(i) > 0 ? g[i] : -g[i];
-    if (cz(i)) jz += cz(i) > 0 ? g[i] : -g[i];
+    r += s[i];
+    if (cx(i)) ax += cx(i) > 0 ? s[i] : -s[i];
+    if (cy(i)) ay += cy(i) > 0 ? s[i] : -s[i];
+    if (cz(i)) az += cz(i) > 0 ? s[i] : -s[i];
   }
-  float inv = 1.f / r;
-  rho = r;
-  ux = jx * inv;
-  uy = jy * inv;
-  uz = jz * inv;
+  drho = r;
+  jx = ax;
+  jy = ay;
+  jz = az;
 }
 
-__device__ __forceinline__ float feq_i(int i, float rho, float ux, float uy, float uz,
-                                       float usq15) {
-  float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
-  return wf(i) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - usq15);
+// Shifted equilibrium f^eq_i - w_i = w_i (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)).
+__device__ __forceinline__ float eq_s(int i, float drho, float rho, float ux, float uy, float uz,
+                                      float usq15) {
+  const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+  return wf(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - usq15));
 }
 
 // 9/2 w_i Q_i : P for a symmetric tensor P given by its 6 components.
@@ -145,135 +152,133 @@ __device__ __forceinline__ float reg_neq_i(int i, float pxx, float pyy, float pz
   return 4.5f * wf(i) * q;
 }
 
-// Non-equilibrium second moment Pi^neq = sum c c g - rho (I/3 + u u).
-__device__ __forceinline__ void pi_neq(const float g[Q], float rho, float ux, float uy, float uz,
-                                       float& pxx, float& pyy, float& pzz, float& pxy,
-                                       float& pxz, float& pyz) {
-  float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
+// sum_i c_ia c_ib d_i for the 6 components of a symmetric tensor.
+__device__ __forceinline__ void second_moment(const float d[Q], float& sxx, float& syy, float& szz,
+                                              float& sxy, float& sxz, float& syz) {
+  sxx = syy = szz = sxy = sxz = syz = 0.f;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    if (cx(i)) sxx += g[i];
-    if (cy(i)) syy += g[i];
-    if (cz(i)) szz += g[i];
-    if (cx(i) && cy(i)) sxy += (cx(i) * cy(i) > 0) ? g[i] : -g[i];
-    if (cx(i) && cz(i)) sxz += (cx(i) * cz(i) > 0) ? g[i] : -g[i];
-    if (cy(i) && cz(i)) syz += (cy(i) * cz(i) > 0) ? g[i] : -g[i];
+    if (cx(i)) sxx += d[i];
+    if (cy(i)) syy += d[i];
+    if (cz(i)) szz += d[i];
+    if (cx(i) && cy(i)) sxy += (cx(i) * cy(i) > 0) ? d[i] : -d[i];
+    if (cx(i) && cz(i)) sxz += (cx(i) * cz(i) > 0) ? d[i] : -d[i];
+    if (cy(i) && cz(i)) syz += (cy(i) * cz(i) > 0) ? d[i] : -d[i];
   }
-  const float r3 = rho * (1.f / 3.f);
-  pxx = sxx - r3 - rho * ux * ux;
-  pyy = syy - r3 - rho * uy * uy;
-  pzz = szz - r3 - rho * uz * uz;
-  pxy = sxy - rho * ux * uy;
-  pxz = sxz - rho * ux * uz;
-  pyz = syz - rho * uy * uz;
 }
 
 enum Collision { C_BGK = 0, C_REG = 1 };
 
-// In-place collision of pulled populations g -> f*.  omega = 1 / tau.
-//
-// The FP32-rounded weights sum to 1 + 1.5e-8, which would add a systematic
-// omega * 1.5e-8 * rho of mass per voxel and step.  The rest direction
-// therefore closes the balance: f^eq_0 = rho - sum_{i>0} f^eq_i (and the
-// regularized non-equilibrium part of i = 0 is minus the sum of the others),
-// so each update conserves mass up to unbiased rounding.
+// In-place collision s -> s* (omega = 1 / tau).  The rest direction closes
+// the mass balance: its equilibrium is drho minus the others' (the FP32
+// weights sum to 1 + 1.5e-8), and for REG its non-equilibrium part is minus
+// the sum of the others, so each update conserves mass up to unbiased
+// rounding.
 template <int COLL>
-__device__ __forceinline__ void collide(float g[Q], float omega) {
-  float rho, ux, uy, uz;
-  moments(g, rho, ux, uy, uz);
+__device__ __forceinline__ void collide(float s[Q], float omega) {
+  float drho, jx, jy, jz;
+  moments_s(s, drho, jx, jy, jz);
+  const float rho = 1.f + drho;
+  const float inv = 1.f / rho;
+  const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
   const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
   if constexpr (COLL == C_BGK) {
-    float s = 0.f;
+    float e = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const float fe = feq_i(i, rho, ux, uy, uz, usq15);
-      s += fe;
-      g[i] = g[i] + omega * (fe - g[i]);
+      const float E = eq_s(i, drho, rho, ux, uy, uz, usq15);
+      e += E;
+      s[i] = s[i] + omega * (E - s[i]);
     }
-    g[0] = g[0] + omega * ((rho - s) - g[0]);
+    s[0] = s[0] + omega * ((drho - e) - s[0]);
   } else {
     float pxx, pyy, pzz, pxy, pxz, pyz;
-    pi_neq(g, rho, ux, uy, uz, pxx, pyy, pzz, pxy, pxz, pyz);
+    second_moment(s, pxx, pyy, pzz, pxy, pxz, pyz);
+    const float d3 = drho * (1.f / 3.f);
+    pxx = pxx - d3 - rho * ux * ux;
+    pyy = pyy - d3 - rho * uy * uy;
+    pzz = pzz - d3 - rho * uz * uz;
+    pxy = pxy - rho * ux * uy;
+    pxz = pxz - rho * ux * uz;
+    pyz = pyz - rho * uy * uz;
     const float k = 1.f - omega;
-    float s = 0.f, sn = 0.f;
+    float e = 0.f, sn = 0.f;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const float fe = feq_i(i, rho, ux, uy, uz, usq15);
+      const float E = eq_s(i, drho, rho, ux, uy, uz, usq15);
       const float fn = reg_neq_i(i, pxx, pyy, pzz, pxy, pxz, pyz);
-      s += fe;
+      e += E;
       sn += fn;
-      g[i] = fe + k * fn;
+      s[i] = E + k * fn;
     }
-    g[0] = (rho - s) - k * sn;
+    s[0] = (drho - e) - k * sn;
   }
 }
 
-// Regularized velocity / pressure node (3Q live values: g, f^eq, result).
-// g holds the pulled populations with bounce-back already applied to every
-// missing source outside the unknown set; bc = (ux, uy, uz, rho).
-__device__ __forceinline__ void regularized_node(float g[Q], int type, int normal, float4 bc,
+// Regularized velocity / pressure node (3Q live values: s, equilibrium,
+// result).  s holds the pulled populations with bounce-back already applied
+// to every missing source outside the unknown set; bc = (ux, uy, uz, rho).
+// With D3Q19 the weights of {c.n = 0} plus twice those of {c.n > 0} sum to
+// 1, so the Zou-He density in shifted form is rho = (1 + S0 + 2 S+)/(1 + u_n).
+__device__ __forceinline__ void regularized_node(float s[Q], int type, int normal, float4 bc,
                                                  float omega) {
   const int nx = normal == 0 ? 1 : (normal == 1 ? -1 : 0);
   const int ny = normal == 2 ? 1 : (normal == 3 ? -1 : 0);
   const int nz = normal == 4 ? 1 : (normal == 5 ? -1 : 0);
-  float s = 0.f;
+  float sum = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cn = cx(i) * nx + cy(i) * ny + cz(i) * nz;
-    s += cn == 0 ? g[i] : (cn > 0 ? 2.f * g[i] : 0.f);
+    sum += cn == 0 ? s[i] : (cn > 0 ? 2.f * s[i] : 0.f);
   }
-  float rho, ux, uy, uz;
+  float drho, rho, ux, uy, uz;
   if (type == T_VELOCITY) {
     ux = bc.x;
     uy = bc.y;
     uz = bc.z;
-    rho = s / (1.f + (ux * nx + uy * ny + uz * nz));
+    const float un = ux * nx + uy * ny + uz * nz;
+    drho = (sum - un) / (1.f + un);
+    rho = 1.f + drho;
   } else {
     rho = bc.w;
-    const float un = s / rho - 1.f;
+    drho = bc.w - 1.f;
+    const float un = (sum - drho) / rho;
     ux = un * nx;
     uy = un * ny;
     uz = un * nz;
   }
   const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  float feq[Q];
-  float s_eq = 0.f;
+  float E[Q];
+  float e = 0.f;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    feq[i] = feq_i(i, rho, ux, uy, uz, usq15);
-    s_eq += feq[i];
+    E[i] = eq_s(i, drho, rho, ux, uy, uz, usq15);
+    e += E[i];
   }
-  feq[0] = rho - s_eq;  // mass-closing rest equilibrium (see collide)
+  E[0] = drho - e;  // mass-closing rest equilibrium (see collide)
   // non-equilibrium bounce-back of the unknown set (unknowns read known opposites)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cn = cx(i) * nx + cy(i) * ny + cz(i) * nz;
-    if (cn < 0) g[i] = feq[i] + (g[opp(i)] - feq[opp(i)]);
+    if (cn < 0) s[i] = E[i] + (s[opp(i)] - E[opp(i)]);
   }
-  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+  float d[Q];
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const float d = g[i] - feq[i];
-    if (cx(i)) pxx += d;
-    if (cy(i)) pyy += d;
-    if (cz(i)) pzz += d;
-    if (cx(i) && cy(i)) pxy += (cx(i) * cy(i) > 0) ? d : -d;
-    if (cx(i) && cz(i)) pxz += (cx(i) * cz(i) > 0) ? d : -d;
-    if (cy(i) && cz(i)) pyz += (cy(i) * cz(i) > 0) ? d : -d;
-  }
-  // the rest population enters Pi only through the trace-free projection: c_0 = 0
+  for (int i = 0; i < Q; ++i) d[i] = s[i] - E[i];
+  float pxx, pyy, pzz, pxy, pxz, pyz;
+  second_moment(d, pxx, pyy, pzz, pxy, pxz, pyz);
   const float k = 1.f - omega;
-  float s_neq = 0.f;
+  float sn = 0.f;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const float fn = reg_neq_i(i, pxx, pyy, pzz, pxy, pxz, pyz);
-    s_neq += fn;
-    g[i] = feq[i] + k * fn;
+    sn += fn;
+    s[i] = E[i] + k * fn;
   }
-  g[0] = feq[0] - k * s_neq;
+  s[0] = E[0] - k * sn;
 }
 
-// Equilibrium in FP64 (initial state).
+// Equilibrium in FP64 (initial state, absolute).
 __device__ __forceinline__ double feq_d(int i, double rho, double ux, double uy, double uz) {
   double cu = (double)cx(i) * ux + (double)cy(i) * uy + (double)cz(i) * uz;
   double usq = ux * ux + uy * uy + uz * uz;

@@ -93,7 +93,7 @@ __global__ void k_moments(LevelDev d, const void* f, double* rho, double* u) {
       double m = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const double fi = (double)Codec<S>::load_i(in[base + i * stride], i);
+        const double fi = Codec<S>::abs_d(in[base + i * stride], i);
         m += fi;
         jx += cx(i) * fi;
         jy += cy(i) * fi;
@@ -129,7 +129,7 @@ __global__ void k_decode(LevelDev d, const void* f, double* dst) {
     const T* in = (const T*)f;
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      dst[i * n + v] = ok ? (double)Codec<S>::load_i(in[base + i * stride], i) : nan;
+      dst[i * n + v] = ok ? Codec<S>::abs_d(in[base + i * stride], i) : nan;
   }
 }
 
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cons_partial(LevelDev d, const 
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double fi = (double)Codec<S>::load_i(in[base + i * stride], i);
+      const double fi = Codec<S>::abs_d(in[base + i * stride], i);
       acc[0] += fi;
       if (cx(i)) acc[1] += cx(i) * fi;
       if (cy(i)) acc[2] += cy(i) * fi;
