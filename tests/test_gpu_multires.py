@@ -134,7 +134,8 @@ def test_uniform_state_stays_uniform(lbm):
     for lv in range(3):
         f = lbm.lbm_get_populations_f64(g, lv)
         m = np.isfinite(f0[lv][0])
-        assert np.max(np.abs(f[:, m] - f0[lv][:, m])) < 2e-7
+        # 3 coarse steps = 12 finest updates, each within a few FP32 ulps (3e-8 at 1/3)
+        assert np.max(np.abs(f[:, m] - f0[lv][:, m])) < 1e-6
 
 
 def test_full_size_three_level_turbulence_properties(lbm):
