@@ -223,6 +223,27 @@ lbm_status lbm_get_layout(const lbm_grid* g, int level, int what, void* dst,
  * Returns LBM_ERR_DIVERGED when a sum is not finite.  Synchronises. */
 lbm_status lbm_conservation(lbm_grid* g, double out_mass_mom[4]);
 
+/* Conservation sums of a dense population buffer without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate at the point they need the sums, e.g. a solver
+ * loop that must not synchronise the device (cudaMalloc / cudaFree may wait
+ * for all outstanding work) or an application whose device memory belongs to
+ * its own pool.
+ *   f            device, dense SoA populations f[pop * n_voxels + v] in the
+ *                given storage (LBM_STORAGE_*; F16 / BF16 hold f_i - w_i)
+ *   flags        device, one flag byte per voxel, or NULL (all fluid); only
+ *                voxels of type 0, 2 and 3 are summed
+ *   out_mass_mom device, 4 doubles: sum f_i, sum f_i c_i (FP64, deterministic)
+ * Asynchronous on `stream`; no allocation, copy or synchronisation.  The
+ * partial sums live in one fixed device array of 4096 x 4 doubles per device
+ * (held until the process exits), so n_voxels <= 67,108,864; larger inputs
+ * return LBM_ERR_INVALID.  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress, once, with that device
+ * current); make that first call before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race, so order them on one stream. */
+lbm_status lbm_conservation_noalloc(const void* f, int storage, int64_t n_voxels,
+                                    const uint8_t* flags, double* out_mass_mom, void* stream);
+
 /* Wait for the grid's last stream and return (and clear) the latched device
  * status. */
 lbm_status lbm_sync(lbm_grid* g);

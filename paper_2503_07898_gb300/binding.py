@@ -92,6 +92,7 @@ def load():
         "lbm_sync": [vp],
         "lbm_set_variant": [vp, I],
         "lbm_autotune": [vp, I, P(I), P(C.c_double)],
+        "lbm_conservation_noalloc": [vp, I, C.c_int64, vp, vp, vp],
         "lbm_profile": [vp, I],
         "lbm_profile_read": [vp, P(lbm_kernel_stat), I, P(I)],
     }
@@ -366,6 +367,15 @@ def lbm_conservation(grid):
     out = (C.c_double * 4)()
     _check(load().lbm_conservation(grid.ptr, out), "lbm_conservation")
     return np.array(list(out))
+
+
+def lbm_conservation_noalloc(f, storage, n_voxels, flags, out, stream=None):
+    """f, flags (or None) and out (4 float64) are CUDA tensors; nothing is allocated."""
+    st = {"f32": 0, "f16": 1, "bf16": 2}[storage] if isinstance(storage, str) else int(storage)
+    _check(load().lbm_conservation_noalloc(
+        C.c_void_p(f.data_ptr()), st, C.c_int64(int(n_voxels)),
+        None if flags is None else C.c_void_p(flags.data_ptr()), C.c_void_p(out.data_ptr()),
+        _stream_ptr(stream)), "lbm_conservation_noalloc")
 
 
 def lbm_profile(grid, enable):
