@@ -244,6 +244,24 @@ __device__ __forceinline__ float coalescence(const MrArgs& a, int gx, int gy, in
   return 0.5f * (n0 + n1);
 }
 
+// Pre-collision scratch of the unfused schedule: shifted values stay raw FP32
+// under FP32 storage (an exact round trip, so both schedules agree bit for
+// bit); under 16-bit storage the scratch uses the storage type.
+template <int S> struct TmpCodec {
+  using T = typename Codec<S>::T;
+  template <int I> __device__ static __forceinline__ float load(T v) {
+    return Codec<S>::template load<I>(v);
+  }
+  template <int I> __device__ static __forceinline__ T store(float s) {
+    return Codec<S>::template store<I>(s);
+  }
+};
+template <> struct TmpCodec<S_F32> {
+  using T = float;
+  template <int I> __device__ static __forceinline__ float load(T v) { return v; }
+  template <int I> __device__ static __forceinline__ T store(float s) { return s; }
+};
+
 template <int S, int COLL, bool SPLIT>
 __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;
@@ -285,12 +303,21 @@ __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
       g[I] = coalescence<S, I>(a, gx, gy, gz);
     }
   });
-  if constexpr (!SPLIT) collide<COLL>(g, a.omega);
-  T* __restrict__ out = (T*)a.out;
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    out[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
-  });
+  if constexpr (SPLIT) {
+    using TT = typename TmpCodec<S>::T;
+    TT* __restrict__ out = (TT*)a.out;
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      out[(b * Q + I) * 512 + l] = TmpCodec<S>::template store<I>(g[I]);
+    });
+  } else {
+    collide<COLL>(g, a.omega);
+    T* __restrict__ out = (T*)a.out;
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      out[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
+    });
+  }
 }
 
 // Unfused baseline: collision of the pre-collision values written by the
@@ -302,11 +329,12 @@ __global__ void __launch_bounds__(256) mr_collide(const void* tmp, void* out, in
   const int64_t b = b0 + blockIdx.x / 2;
   if (b >= b1) return;
   const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
-  const T* in = (const T*)tmp;
+  using TT = typename TmpCodec<S>::T;
+  const TT* in = (const TT*)tmp;
   float g[Q];
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
-    g[I] = Codec<S>::template load<I>(in[(b * Q + I) * 512 + l]);
+    g[I] = TmpCodec<S>::template load<I>(in[(b * Q + I) * 512 + l]);
   });
   collide<COLL>(g, omega);
   T* o = (T*)out;
