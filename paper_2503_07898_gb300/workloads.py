@@ -130,3 +130,32 @@ def multires_slab_map(n=256, n_levels=3):
     zlev[(z >= 160) & (z < 192)] = 1
     zlev[(z >= 96) & (z < 160)] = 0
     return np.ascontiguousarray(np.broadcast_to(zlev[:, None, None], (m, m, m)))
+
+
+def turbulence(n, seed=7898, u_rms=0.03, kmax=None, dims=None):
+    """Decaying-turbulence start: random-phase Fourier modes on integer wave
+    vectors 1 <= |k| <= kmax with shell amplitude sqrt(E(k) / shell count),
+    E(k) ~ k^(-5/3), projected divergence-free, real part of the inverse FFT,
+    scaled to a component RMS of u_rms; rho = 1.  Returns (rho, u)."""
+    nx, ny, nz = dims if dims is not None else (n, n, n)
+    kmax = kmax if kmax is not None else min(nx, ny, nz) // 8
+    rng = np.random.default_rng(seed)
+    kz = np.fft.fftfreq(nz, 1.0 / nz)[:, None, None]
+    ky = np.fft.fftfreq(ny, 1.0 / ny)[None, :, None]
+    kx = np.fft.fftfreq(nx, 1.0 / nx)[None, None, :]
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    shell = np.rint(kk).astype(int)
+    counts = np.bincount(shell.ravel())
+    amp = np.zeros_like(kk)
+    ok = (shell >= 1) & (kk <= kmax)
+    amp[ok] = np.sqrt(shell[ok].astype(float) ** (-5.0 / 3.0) / counts[shell[ok]])
+    uh = amp[None] * (rng.standard_normal((3,) + kk.shape) + 1j * rng.standard_normal((3,) + kk.shape))
+    kvec = np.broadcast_arrays(kx, ky, kz)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        kdotu = sum(kvec[a] * uh[a] for a in range(3)) / np.where(kk > 0, kk * kk, 1.0)
+    for a in range(3):
+        uh[a] = uh[a] - kvec[a] * kdotu
+    u = np.real(np.fft.ifftn(uh, axes=(1, 2, 3)))
+    u -= u.mean(axis=(1, 2, 3), keepdims=True)
+    u *= u_rms / np.sqrt(np.mean(u * u))
+    return np.ones((nz, ny, nx)), u

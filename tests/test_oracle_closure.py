@@ -1,0 +1,136 @@
+"""Pins of the learned-closure oracle (oracle/closure.py): the network's
+gradient against finite differences, a hand-built network, Adam's first step,
+the features on inputs whose moments are known, and the training target's
+invariances."""
+import numpy as np
+
+from oracle import closure as cl
+from oracle import lattice as L
+from paper_2503_07898_gb300 import workloads as wl
+
+
+def random_theta(seed, scale=0.3):
+    return np.random.default_rng(seed).standard_normal(cl.N_PARAMS) * scale
+
+
+def test_parameter_count():
+    assert cl.N_PARAMS == 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1 == 5313
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    theta = random_theta(2)
+    X = rng.standard_normal((37, 16))
+    t = rng.standard_normal(37)
+    _, g = cl.loss_and_grad(theta, X, t)
+    h = 1e-6
+    for k in list(range(0, 1024, 97)) + [1024 + 5, 1088 + 700, 5184 + 3, 5248 + 10, 5312]:
+        e = np.zeros_like(theta)
+        e[k] = h
+        fd = (cl.loss_and_grad(theta + e, X, t)[0] - cl.loss_and_grad(theta - e, X, t)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), (k, fd, g[k])
+
+
+def test_hand_built_network():
+    """W1 copies the 16 features into units 0..15, W2 is the identity, W3 sums:
+    the output is the sum of the positive parts of the features (+ b3)."""
+    p = {"W1": np.zeros((64, 16)), "b1": np.zeros(64), "W2": np.eye(64), "b2": np.zeros(64),
+         "W3": np.ones(64), "b3": np.array([0.25])}
+    p["W1"][:16] = np.eye(16)
+    X = np.random.default_rng(3).standard_normal((9, 16))
+    y, _ = cl.forward(cl.pack(p), X)
+    assert np.allclose(y, np.maximum(X, 0).sum(axis=1) + 0.25, atol=1e-14)
+
+
+def test_adam_first_step_moves_each_parameter_by_lr():
+    theta = random_theta(4)
+    grad = np.random.default_rng(5).standard_normal(cl.N_PARAMS)
+    new, m, v = cl.adam(theta, grad, np.zeros_like(theta), np.zeros_like(theta), 1, lr=1e-3)
+    # bias-corrected moments are g and g^2 after one step: the update is
+    # -lr g / (|g| + eps), i.e. -lr sign(g) away from tiny gradients
+    assert np.allclose(new - theta, -1e-3 * grad / (np.abs(grad) + 1e-8), rtol=1e-9, atol=0)
+    big = np.abs(grad) > 1e-2
+    assert np.allclose((new - theta)[big], -1e-3 * np.sign(grad[big]), rtol=1e-5)
+
+
+def test_features_of_known_populations():
+    rho, u = np.array([1.03, 0.98]), np.array([[0.02, -0.01], [0.0, 0.03], [-0.015, 0.005]])
+    feq = L.equilibrium(rho, u)
+    F = cl.features(feq, 0.51)
+    assert np.allclose(F[:, 0], rho - 1, atol=1e-15)
+    assert np.allclose(F[:, 1:4], u.T, atol=1e-15)
+    assert np.allclose(F[:, 4:15], 0, atol=1e-14)
+    assert np.allclose(F[:, 15], 0.51)
+    # regularized non-equilibrium with a known Pi: normalised Pi, its norm and trace
+    Pi = np.array([[1e-3, 2e-4, -3e-4], [2e-4, -5e-4, 1e-4], [-3e-4, 1e-4, 2e-4]])
+    g = feq + L.regularized_neq(np.broadcast_to(Pi[:, :, None], (3, 3, 2)))
+    F = cl.features(g, 0.51)
+    s = rho / 3
+    want = np.array([Pi[0, 0], Pi[1, 1], Pi[2, 2], Pi[0, 1], Pi[0, 2], Pi[1, 2]])
+    assert np.allclose(F[:, 4:10], want[None] / s[:, None], rtol=1e-9, atol=0)
+    assert np.allclose(F[:, 11], np.trace(Pi) / s, rtol=1e-9)
+    assert np.allclose(F[:, 10], np.sqrt((Pi * Pi).sum()) / s, rtol=1e-9)
+    # one perturbed population: third-order features pick c_x (c_y^2 + c_z^2) etc.
+    i = 7                                                    # (+1, +1, 0)
+    g = feq.copy()
+    g[i] += 1e-4 * np.array([1.0, 1.0])
+    F = cl.features(g, 0.51)
+    # the equilibrium is re-evaluated at the perturbed moments; compare with the
+    # features computed from the definition directly
+    r2 = g.sum(0)
+    u2 = np.stack([(L.C[:, a, None] * g).sum(0) for a in range(3)]) / r2
+    d = g - L.equilibrium(r2, u2)
+    qx = (L.C[:, 0] * (L.C[:, 1] ** 2 + L.C[:, 2] ** 2)) @ d / (r2 / 3)
+    assert np.allclose(F[:, 12], qx, rtol=1e-10)
+
+
+def _fine_feq(u, rho=None):
+    shape = u.shape[1:]
+    rho = np.ones(shape) if rho is None else rho
+    return L.equilibrium(rho, u)
+
+
+def test_eddy_target_zero_for_box_uniform_fields():
+    rng = np.random.default_rng(6)
+    uc = 0.01 * rng.standard_normal((3, 4, 4, 4))
+    u = uc.repeat(2, 1).repeat(2, 2).repeat(2, 3)          # constant in every 2^3 box
+    t = cl.eddy_target(_fine_feq(u), 2, 0.51)
+    assert np.allclose(t, 0.0, atol=1e-15)
+    # a varying density does not create sub-filter stress when u is box-uniform
+    rho = 1.0 + 0.02 * rng.random((8, 8, 8))
+    t = cl.eddy_target(_fine_feq(u, rho), 2, 0.51)
+    assert np.allclose(t, 0.0, atol=1e-12)
+
+
+def test_eddy_target_galilean_invariance_and_linearity():
+    """With rho = 1 the target is unchanged by a uniform velocity and scales
+    linearly with the velocity fluctuation amplitude (tau_sgs ~ A^2, S ~ A)."""
+    _, u = wl.turbulence(16, seed=8, u_rms=1e-3, kmax=6)
+    t1 = cl.eddy_target(_fine_feq(u), 2, 0.51)
+    shift = np.array([0.01, -0.02, 0.005])[:, None, None, None]
+    t2 = cl.eddy_target(_fine_feq(u + shift), 2, 0.51)
+    t3 = cl.eddy_target(_fine_feq(2 * u), 2, 0.51)
+    inner = (t1 > -0.009) & (t1 < 0.49) & (t3 > -0.009) & (t3 < 0.49)   # unclamped
+    assert inner.mean() > 0.9
+    assert np.allclose(t1, t2, atol=1e-9)
+    assert np.allclose(t3[inner], 2 * t1[inner], rtol=1e-6, atol=1e-12)
+
+
+def test_fold_normalisation_is_exact():
+    rng = np.random.default_rng(9)
+    theta = random_theta(10)
+    X = rng.standard_normal((11, 16)) * 3 + 1
+    mu, sd = X.mean(0), X.std(0)
+    y_n, _ = cl.forward(theta, (X - mu) / sd)
+    folded = cl.fold_normalisation(theta, mu, sd, 0.3, 2.0)
+    y, _ = cl.forward(folded, X)
+    assert np.allclose(y, y_n * 2.0 + 0.3, rtol=1e-12, atol=1e-12)
+
+
+def test_coarse_pulled_uniform_flow_is_stationary():
+    rho = np.full((8, 8, 8), 1.01)
+    u = np.zeros((3, 8, 8, 8))
+    u[:] = np.array([0.02, 0.0, -0.01])[:, None, None, None]
+    f = L.equilibrium(rho, u)
+    assert np.allclose(cl.coarse_pulled(f, 2), L.equilibrium(rho[:4, :4, :4], u[:, :4, :4, :4]),
+                       atol=1e-15)
