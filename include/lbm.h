@@ -244,6 +244,57 @@ lbm_status lbm_conservation(lbm_grid* g, double out_mass_mom[4]);
 lbm_status lbm_conservation_noalloc(const void* f, int storage, int64_t n_voxels,
                                     const uint8_t* flags, double* out_mass_mom, void* stream);
 
+/* ------------------------------------------------------- learned closure
+ * Not in the paper (the learned part of this implementation): a per-voxel
+ * network 16 -> 64 (ReLU) -> 64 (ReLU) -> 1 predicts a relaxation-time
+ * correction d_tau on multi-resolution levels >= 1; those voxels relax with
+ * tau_eff = max(tau_l + d_tau, 1/2 + 1e-3).  Features per voxel, from the
+ * pulled populations g (d = g - f^eq):  rho - 1, u (3), Pi^neq (xx, yy, zz,
+ * xy, xz, yz) / (rho/3), |Pi^neq|_F / (rho/3), tr Pi^neq / (rho/3),
+ * q_x, q_y, q_z / (rho/3) with q_x = sum_i c_ix (c_iy^2 + c_iz^2) d_i and
+ * cyclic, tau_l.  Parameters: 5313 FP32 values, W1 (64 x 16, row per unit),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1).  Inference runs inside the
+ * collision kernels as BF16 tensor-core MMAs (weights rounded to BF16, biases
+ * FP32, FP32 accumulation). */
+
+/* Training data made by the solver from a dense periodic grid's current
+ * state: the state is box-filtered by r^3 (mean populations), streamed one
+ * coarse step, and turned into 16 features per coarse voxel; the target is
+ * the least-squares eddy viscosity over each coarse voxel's 3^3 neighbourhood,
+ * d_tau = -3 sum(tau_sgs_dev : S) / sum(2 rho S : S), clamped to
+ * [-(tau_coarse - 1/2) + 1e-3, 1/2].  feats (n_c x 16) and targets (n_c) are
+ * device arrays, n_c = voxels / r^3 in coarse x-fastest order.  Synchronises. */
+lbm_status lbm_closure_dataset(lbm_grid* fine, int r, double tau_coarse, float* feats,
+                               float* targets);
+
+/* Train the network on device arrays feats (n x 16) and targets (n) with
+ * MSE loss and Adam (beta 0.9 / 0.999, eps 1e-8, learning rate lr) for
+ * `steps` minibatches of `batch` samples drawn by SplitMix64 on counter
+ * step*batch + b plus `seed`.  Features and targets are standardised
+ * internally; theta_io (device, 5313 FP32) holds the initial weights for the
+ * standardised problem and receives the trained weights with the
+ * standardisation folded in (they take raw features).  loss_out (host, may
+ * be NULL) receives the last minibatch loss (standardised).  Synchronises. */
+lbm_status lbm_closure_train(const float* feats, const float* targets, int64_t n, int steps,
+                             int batch, float lr, uint64_t seed, float* theta_io,
+                             float* loss_out, void* stream);
+
+/* Loss (MSE) and gradient (5313 FP32) of one minibatch, samples idx[0..batch),
+ * at weights theta, in FP32; all device pointers.  Synchronises. */
+lbm_status lbm_closure_grad(const float* theta, const float* feats, const float* targets,
+                            const int32_t* idx, int batch, float* grad, float* loss,
+                            void* stream);
+
+/* Network output for n feature rows (device): bf16 = 1 uses the tensor-core
+ * path of the collision kernels, bf16 = 0 an FP32 reference on CUDA cores. */
+lbm_status lbm_closure_forward(const float* theta, const float* feats, int64_t n, int bf16,
+                               float* out, void* stream);
+
+/* Load trained weights (host, n = 5313 FP32) into a multi-resolution grid;
+ * with phys.closure = 1 every later step applies the closure on levels >= 1
+ * (disaggregated schedule only). */
+lbm_status lbm_closure_load(lbm_grid* g, const float* theta, size_t n);
+
 /* Wait for the grid's last stream and return (and clear) the latched device
  * status. */
 lbm_status lbm_sync(lbm_grid* g);

@@ -93,6 +93,11 @@ def load():
         "lbm_set_variant": [vp, I],
         "lbm_autotune": [vp, I, P(I), P(C.c_double)],
         "lbm_conservation_noalloc": [vp, I, C.c_int64, vp, vp, vp],
+        "lbm_closure_dataset": [vp, I, C.c_double, vp, vp],
+        "lbm_closure_train": [vp, vp, C.c_int64, I, I, C.c_float, C.c_uint64, vp, vp, vp],
+        "lbm_closure_grad": [vp, vp, vp, vp, I, vp, vp, vp],
+        "lbm_closure_forward": [vp, vp, C.c_int64, I, vp, vp],
+        "lbm_closure_load": [vp, vp, C.c_size_t],
         "lbm_profile": [vp, I],
         "lbm_profile_read": [vp, P(lbm_kernel_stat), I, P(I)],
     }
@@ -167,13 +172,14 @@ def _ptr(a, dtype):
     return C.c_void_p(arr.ctypes.data), 0, arr
 
 
-def physics(tau, collision="bgk", storage="f32", periodic=(0, 0, 0), schedule="disaggregated"):
+def physics(tau, collision="bgk", storage="f32", periodic=(0, 0, 0), schedule="disaggregated",
+            closure=0):
     p = lbm_physics()
     p.tau = float(tau)
     p.collision = {"bgk": 0, "reg": 1}[collision] if isinstance(collision, str) else int(collision)
     p.storage = ({"f32": 0, "f16": 1, "bf16": 2}[storage] if isinstance(storage, str)
                  else int(storage))
-    p.closure = 0
+    p.closure = int(closure)
     for a in range(3):
         p.periodic[a] = int(bool(periodic[a]))
     p.schedule = ({"disaggregated": 0, "monolithic": 1}[schedule] if isinstance(schedule, str)
@@ -376,6 +382,49 @@ def lbm_conservation_noalloc(f, storage, n_voxels, flags, out, stream=None):
         C.c_void_p(f.data_ptr()), st, C.c_int64(int(n_voxels)),
         None if flags is None else C.c_void_p(flags.data_ptr()), C.c_void_p(out.data_ptr()),
         _stream_ptr(stream)), "lbm_conservation_noalloc")
+
+
+CLOSURE_PARAMS = 5313
+
+
+def _dev(t):
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def lbm_closure_dataset(grid, r, tau_coarse, feats, targets):
+    """feats (n_c x 16) and targets (n_c) are float32 CUDA tensors."""
+    _check(load().lbm_closure_dataset(grid.ptr, int(r), float(tau_coarse), _dev(feats),
+                                      _dev(targets)), "lbm_closure_dataset")
+
+
+def lbm_closure_train(feats, targets, steps, batch, lr, seed, theta, stream=None):
+    """Trains theta (float32 CUDA tensor, 5313) in place; returns the last loss."""
+    loss = C.c_float()
+    _check(load().lbm_closure_train(_dev(feats), _dev(targets), C.c_int64(targets.numel()),
+                                    int(steps), int(batch), C.c_float(lr), C.c_uint64(seed),
+                                    _dev(theta), C.byref(loss), _stream_ptr(stream)),
+           "lbm_closure_train")
+    return loss.value
+
+
+def lbm_closure_grad(theta, feats, targets, idx, grad, loss, stream=None):
+    _check(load().lbm_closure_grad(_dev(theta), _dev(feats), _dev(targets), _dev(idx),
+                                   int(idx.numel()), _dev(grad), _dev(loss), _stream_ptr(stream)),
+           "lbm_closure_grad")
+
+
+def lbm_closure_forward(theta, feats, out, bf16=True, stream=None):
+    _check(load().lbm_closure_forward(_dev(theta), _dev(feats), C.c_int64(out.numel()),
+                                      int(bool(bf16)), _dev(out), _stream_ptr(stream)),
+           "lbm_closure_forward")
+
+
+def lbm_closure_load(grid, theta):
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(load().lbm_closure_load(grid.ptr, C.c_void_p(th.ctypes.data), th.size),
+           "lbm_closure_load")
 
 
 def lbm_profile(grid, enable):

@@ -114,6 +114,8 @@ static void free_grid(Grid& g) {
   g.dfree(g.status_d, g.stream);
   g.dfree(g.partials_d, g.stream);
   g.dfree(g.sums_d, g.stream);
+  g.dfree(g.closure_d, g.stream);
+  g.closure_d = nullptr;
   g.status_d = nullptr;
   g.partials_d = nullptr;
   g.sums_d = nullptr;
@@ -130,7 +132,7 @@ static lbm_status check_physics(const lbm_physics* p) {
     return fail(LBM_ERR_INVALID, "unknown storage");
   if (p->schedule != LBM_SCHEDULE_DISAGGREGATED && p->schedule != LBM_SCHEDULE_MONOLITHIC)
     return fail(LBM_ERR_INVALID, "unknown schedule");
-  if (p->closure != 0) return fail(LBM_ERR_UNSUPPORTED, "closure needs a multi-resolution grid");
+  if (p->closure != 0 && p->closure != 1) return fail(LBM_ERR_INVALID, "closure must be 0 or 1");
   return LBM_OK;
 }
 
@@ -299,6 +301,7 @@ lbm_status lbm_grid_create_dense(const int dims[3], const lbm_physics* phys,
     return fail(LBM_ERR_INVALID, "dims must be positive");
   if ((double)dims[0] * dims[1] * dims[2] * Q >= 9.0e18)
     return fail(LBM_ERR_INVALID, "grid too large");
+  if (phys && phys->closure) return fail(LBM_ERR_UNSUPPORTED, "the closure runs on multi-resolution grids");
   Grid* gp = nullptr;
   lbm_status st = begin(out, phys, alloc, stream, gp);
   if (st) return st;
@@ -331,6 +334,7 @@ lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge, const uint8
   for (int a = 0; a < 3; ++a)
     if (phys && phys->periodic[a] && dims[a] % block_edge)
       return fail(LBM_ERR_INVALID, "periodic axes need dims divisible by block_edge");
+  if (phys && phys->closure) return fail(LBM_ERR_UNSUPPORTED, "the closure runs on multi-resolution grids");
   Grid* gp = nullptr;
   lbm_status st = begin(out, phys, alloc, stream, gp);
   if (st) return st;

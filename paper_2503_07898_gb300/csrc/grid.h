@@ -96,6 +96,10 @@ struct Grid {
   double* sums_d = nullptr;      // 4 doubles
   int64_t steps_done = 0;
 
+  // learned closure (multi-resolution levels >= 1)
+  void* closure_d = nullptr;     // ClosureParams on the device
+  bool closure_loaded = false;
+
   // per-kernel event timing (lbm_profile)
   bool prof = false;
   std::vector<std::string> prof_names;

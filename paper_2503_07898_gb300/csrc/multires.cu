@@ -37,6 +37,7 @@
 
 #include "d3q19.cuh"
 #include "grid.h"
+#include "closure.cuh"
 #include "layout.h"
 
 namespace lbm {
@@ -182,6 +183,8 @@ struct MrArgs {
   int k;             // 1 or 2: substep of this level inside the coarser step
   int64_t b0, b1;    // block range
   float omega;
+  float tau;                  // relaxation time of this level (closure input)
+  const ClosureParams* cp;    // learned closure (CLOSURE kernels only)
   int* status;
 };
 
@@ -262,13 +265,22 @@ template <> struct TmpCodec<S_F32> {
   template <int I> __device__ static __forceinline__ T store(float s) { return s; }
 };
 
-template <int S, int COLL, bool SPLIT>
+// Shared memory of the closure variant: network weights and per-warp
+// feature staging (dynamic, so the plain variants stay without it).
+struct ClosureCta {
+  ClosureSmem w;
+  __nv_bfloat16 stage[8][32 * FSTAGE];
+};
+
+template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
 __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;
   const int64_t b = a.b0 + blockIdx.x / 2;
   __shared__ int32_t snbr[27];
+  extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
   if (b >= a.b1) return;  // uniform per CTA
   if (threadIdx.x < 27) snbr[threadIdx.x] = a.nbr[b * 27 + threadIdx.x];
+  if constexpr (CLOSURE) closure_load_smem(reinterpret_cast<ClosureCta*>(mr_dyn_smem)->w, a.cp);
   __syncthreads();
   const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
@@ -311,7 +323,17 @@ __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
       out[(b * Q + I) * 512 + l] = TmpCodec<S>::template store<I>(g[I]);
     });
   } else {
-    collide<COLL>(g, a.omega);
+    float omega = a.omega;
+    if constexpr (CLOSURE) {
+      // every thread of the CTA holds a voxel, so the warp-collective MMAs
+      // run with full warps
+      ClosureCta* sm = reinterpret_cast<ClosureCta*>(mr_dyn_smem);
+      float x[MLP_IN];
+      closure_features(g, a.tau, x);
+      const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
+      omega = 1.f / fmaxf(a.tau + dtau, TAU_MIN);
+    }
+    collide<COLL>(g, omega);
     T* __restrict__ out = (T*)a.out;
     static_for<Q>([&](auto ic) {
       constexpr int I = decltype(ic)::value;
@@ -373,17 +395,9 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
   const float omega = (float)(1.0 / tau_l);
   const int c = V.cur, nx = (c + 1) % 3, pv = (c + 2) % 3;
   const bool unfused = g.phys.schedule == LBM_SCHEDULE_MONOLITHIC && l > 0;
+  const bool closure = g.phys.closure && g.closure_loaded && l > 0;
+  const size_t csm = closure ? sizeof(ClosureCta) : 0;
   lbm_status st;
-  // G_i blocks need no cross-level data: launched before the finer substeps
-  if (!unfused && V.n_blocks > V.n_c) {
-    st = sparse_uniform_range(g, V, V.n_c, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
-                              (V.n_blocks - V.n_c) * 512);
-    if (st) return st;
-  }
-  if (l > 0) {
-    if ((st = mr_advance<S, COLL>(g, l - 1, 1, s))) return st;
-    if ((st = mr_advance<S, COLL>(g, l - 1, 2, s))) return st;
-  }
   MrArgs a{};
   a.me = view(V);
   a.nbr = V.nbr_d;
@@ -393,11 +407,33 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
   a.prev = V.f[pv];
   a.k = k;
   a.omega = omega;
+  a.tau = (float)tau_l;
+  a.cp = (const ClosureParams*)g.closure_d;
   a.status = g.status_d;
   if (l + 1 < g.n_levels) {
     const Level& W = g.lv[l + 1];
     a.co = view(W);
     a.ccur = W.f[W.cur];
+  }
+  // G_i blocks need no cross-level data: launched before the finer substeps
+  if (!unfused && V.n_blocks > V.n_c) {
+    if (closure) {
+      MrArgs ai = a;
+      ai.b0 = V.n_c;
+      ai.b1 = V.n_blocks;
+      ai.out = V.f[nx];
+      const int pr = prof_begin(g, s, kname(0, l), (V.n_blocks - V.n_c) * 512);
+      mr_interface<S, COLL, false, true><<<(unsigned)(2 * (V.n_blocks - V.n_c)), 256, csm, s>>>(ai);
+      prof_end(g, s, pr);
+    } else {
+      st = sparse_uniform_range(g, V, V.n_c, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
+                                (V.n_blocks - V.n_c) * 512);
+      if (st) return st;
+    }
+  }
+  if (l > 0) {
+    if ((st = mr_advance<S, COLL>(g, l - 1, 1, s))) return st;
+    if ((st = mr_advance<S, COLL>(g, l - 1, 2, s))) return st;
   }
   if (l > 0) {
     const Level& W = g.lv[l - 1];
@@ -423,7 +459,10 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
     a.b1 = V.n_c;
     a.out = V.f[nx];
     const int pr = prof_begin(g, s, kname(1, l), V.n_c * 512);
-    mr_interface<S, COLL, false><<<(unsigned)(2 * V.n_c), 256, 0, s>>>(a);
+    if (closure)
+      mr_interface<S, COLL, false, true><<<(unsigned)(2 * V.n_c), 256, csm, s>>>(a);
+    else
+      mr_interface<S, COLL, false><<<(unsigned)(2 * V.n_c), 256, 0, s>>>(a);
     prof_end(g, s, pr);
   }
   LBM_CUDA(cudaGetLastError());
@@ -433,6 +472,10 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
 
 lbm_status multires_step(Grid& g, cudaStream_t s) {
   const int top = g.n_levels - 1;
+  if (g.phys.closure && !g.closure_loaded)
+    return fail(LBM_ERR_INVALID, "closure enabled but no weights loaded (lbm_closure_load)");
+  if (g.phys.closure && g.phys.schedule == LBM_SCHEDULE_MONOLITHIC)
+    return fail(LBM_ERR_UNSUPPORTED, "the closure runs with the disaggregated schedule");
   if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
     for (int l = 1; l < g.n_levels; ++l) {
       Level& V = g.lv[l];
