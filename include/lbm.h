@@ -295,6 +295,28 @@ lbm_status lbm_closure_forward(const float* theta, const float* feats, int64_t n
  * (disaggregated schedule only). */
 lbm_status lbm_closure_load(lbm_grid* g, const float* theta, size_t n);
 
+/* ------------------------------------------------------------- batching
+ * Not in the paper (a serving-style use of the same update): many
+ * independent dense and 8^3 block-sparse grids advance together, one
+ * persistent kernel launch per step over a work list of 256-voxel items
+ * (dense: consecutive voxel ids; sparse: half blocks), the steps of one
+ * lbm_batch_step call captured once into a CUDA graph and replayed.
+ * Cases keep their own state, walls and tau; they must share storage and
+ * collision and have no regularized voxels.  A case may still be used on its
+ * own (lbm_get_moments, lbm_step, ...) between batch steps. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out);
+lbm_status lbm_batch_destroy(lbm_batch* b);
+/* Advance every case by n_steps steps on `stream` (graph replay; the graph
+ * for a given n_steps is captured on first use). */
+lbm_status lbm_batch_step(lbm_batch* b, int n_steps, void* stream);
+/* Autotuner of the persistent grid: times n_steps steps for 1, 2, 3, 4, 6 and
+ * 8 CTAs per SM from the current states (restored afterwards), keeps the
+ * fastest; *chosen gets it, ms_per_step (6 doubles or NULL) the timings. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int n_steps, int* chosen, double* ms_per_step);
+lbm_status lbm_batch_info(const lbm_batch* b, int64_t* n_updated, int64_t* n_items,
+                          int* ctas_per_sm);
+
 /* Wait for the grid's last stream and return (and clear) the latched device
  * status. */
 lbm_status lbm_sync(lbm_grid* g);

@@ -98,6 +98,11 @@ def load():
         "lbm_closure_grad": [vp, vp, vp, vp, I, vp, vp, vp],
         "lbm_closure_forward": [vp, vp, C.c_int64, I, vp, vp],
         "lbm_closure_load": [vp, vp, C.c_size_t],
+        "lbm_batch_create": [I, vp, P(vp)],
+        "lbm_batch_destroy": [vp],
+        "lbm_batch_step": [vp, I, vp],
+        "lbm_batch_autotune": [vp, I, P(I), P(C.c_double)],
+        "lbm_batch_info": [vp, P(C.c_int64), P(C.c_int64), P(I)],
         "lbm_profile": [vp, I],
         "lbm_profile_read": [vp, P(lbm_kernel_stat), I, P(I)],
     }
@@ -425,6 +430,55 @@ def lbm_closure_load(grid, theta):
     th = np.ascontiguousarray(theta, dtype=np.float32)
     _check(load().lbm_closure_load(grid.ptr, C.c_void_p(th.ctypes.data), th.size),
            "lbm_closure_load")
+
+
+class Batch:
+    """Handle of lbm_batch_create; keeps the member grids alive."""
+
+    def __init__(self, ptr, grids):
+        self.ptr = ptr
+        self.grids = list(grids)
+
+    def __del__(self):
+        try:
+            if getattr(self, "ptr", None) and _lib is not None:
+                _lib.lbm_batch_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def lbm_batch_create(grids):
+    arr = (C.c_void_p * len(grids))(*[g.ptr.value if hasattr(g.ptr, "value") else g.ptr
+                                      for g in grids])
+    out = C.c_void_p()
+    _check(load().lbm_batch_create(len(grids), arr, C.byref(out)), "lbm_batch_create")
+    return Batch(out, grids)
+
+
+def lbm_batch_destroy(batch):
+    if batch.ptr:
+        _check(load().lbm_batch_destroy(batch.ptr), "lbm_batch_destroy")
+        batch.ptr = None
+
+
+def lbm_batch_step(batch, n_steps, stream=None):
+    _check(load().lbm_batch_step(batch.ptr, int(n_steps), _stream_ptr(stream)), "lbm_batch_step")
+
+
+def lbm_batch_autotune(batch, n_steps):
+    chosen = C.c_int()
+    ms = (C.c_double * 6)()
+    _check(load().lbm_batch_autotune(batch.ptr, int(n_steps), C.byref(chosen), ms),
+           "lbm_batch_autotune")
+    return chosen.value, list(ms)
+
+
+def lbm_batch_info(batch):
+    nu, ni, k = C.c_int64(), C.c_int64(), C.c_int()
+    _check(load().lbm_batch_info(batch.ptr, C.byref(nu), C.byref(ni), C.byref(k)),
+           "lbm_batch_info")
+    return {"n_updated": nu.value, "n_items": ni.value, "ctas_per_sm": k.value}
 
 
 def lbm_profile(grid, enable):

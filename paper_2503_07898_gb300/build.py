@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2"]
-SOURCES = ["api.cu", "dense.cu", "sparse.cu", "fields.cu", "multires.cu", "noalloc.cu", "closure.cu"]
+SOURCES = ["api.cu", "dense.cu", "sparse.cu", "fields.cu", "multires.cu", "noalloc.cu", "closure.cu", "batch.cu"]
 
 
 def _nvcc():

@@ -1,0 +1,350 @@
+// batch.cu - many independent simulations in one persistent launch per step.
+//
+// Not in the paper (a serving-style use of the same update): a batch holds
+// dense and 8^3 block-sparse grids of different sizes, walls and relaxation
+// times.  Their voxels are cut into work items of 256 voxels (dense: 256
+// consecutive voxel ids; sparse: half a block) listed case after case; one
+// persistent kernel per step walks the list with a grid-stride loop, so a
+// step over the whole batch is a single launch whatever the number of cases.
+// A sequence of steps is captured once into a CUDA graph and replayed.  The
+// persistent grid size (CTAs per SM) is the tuning knob of lbm_batch_autotune.
+#include <map>
+#include <vector>
+
+#include "d3q19.cuh"
+#include "dense.cuh"
+#include "grid.h"
+#include "sparse.cuh"
+
+namespace lbm {
+
+struct BatchCase {
+  int kind;  // 0 dense, 1 sparse (block edge 8)
+  int nx, ny, nz, px, py, pz;
+  int64_t N;                 // dense voxels / sparse slots
+  const uint32_t* wmask;     // dense wall mask (null: walls only at box sides)
+  const uint8_t* flags;      // sparse slot flags
+  const int32_t* nbr;        // sparse neighbour table
+  const uint8_t* blk_walls;  // sparse per-block wall bit
+  void* buf[2];
+  int cur0;  // buffer holding the state before step parity 0
+  float omega;
+};
+
+constexpr int BT = 256;  // threads per CTA = voxels per work item
+
+template <int S, int COLL>
+__global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restrict__ cases,
+                                                        const int32_t* __restrict__ item_case,
+                                                        const int32_t* __restrict__ item_local,
+                                                        int64_t n_items, int parity) {
+  using T = typename Codec<S>::T;
+  __shared__ int32_t snbr[27];
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const BatchCase& C = cases[item_case[it]];
+    const int64_t t = item_local[it];
+    const int in = parity ^ C.cur0;
+    const T* __restrict__ fin = (const T*)C.buf[in];
+    T* __restrict__ fout = (T*)C.buf[in ^ 1];
+    float g[Q];
+    if (C.kind == 0) {
+      const int64_t v = t * BT + threadIdx.x;
+      if (v < C.N) {
+        DenseArgs a{};
+        a.nx = C.nx;
+        a.ny = C.ny;
+        a.nz = C.nz;
+        a.N = C.N;
+        a.px = C.px;
+        a.py = C.py;
+        a.pz = C.pz;
+        const int x = (int)(v % C.nx);
+        const int y = (int)((v / C.nx) % C.ny);
+        const int z = (int)(v / ((int64_t)C.nx * C.ny));
+        uint32_t wm = C.wmask ? C.wmask[v] : 0u;
+        if (!(wm & (WM_SKIP | WM_REG))) {
+          pull_all<S>(fin, a, x, y, z, v, wm, g);
+          collide<COLL>(g, C.omega);
+          static_for<Q>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            fout[(int64_t)I * C.N + v] = Codec<S>::template store<I>(g[I]);
+          });
+        }
+      }
+    } else {
+      const int64_t b = t >> 1;
+      const int l = (int)(t & 1) * BT + threadIdx.x;
+      if (threadIdx.x < 27) snbr[threadIdx.x] = C.nbr[b * 27 + threadIdx.x];
+      __syncthreads();
+      const bool walls = C.blk_walls[b] != 0;
+      const bool upd = !walls || type_updated(flag_type(C.flags[b * 512 + l]));
+      if (upd) {
+        sparse_pull_voxel<S, 8>(fin, snbr, C.flags, b, l, walls, g);
+        collide<COLL>(g, C.omega);
+        static_for<Q>([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          fout[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
+        });
+      }
+    }
+    __syncthreads();  // the neighbour list is reused by the next item
+  }
+}
+
+template <int S, int COLL>
+static void launch_step(const BatchCase* cases, const int32_t* ic, const int32_t* il,
+                        int64_t n_items, int grid, int parity, cudaStream_t s) {
+  batch_step_kernel<S, COLL><<<grid, BT, 0, s>>>(cases, ic, il, n_items, parity);
+}
+
+using StepFn = void (*)(const BatchCase*, const int32_t*, const int32_t*, int64_t, int, int,
+                        cudaStream_t);
+
+static StepFn step_fn(int storage, int collision) {
+  const bool bgk = collision == C_BGK;
+  switch (storage) {
+    case S_F32: return bgk ? launch_step<S_F32, C_BGK> : launch_step<S_F32, C_REG>;
+    case S_F16: return bgk ? launch_step<S_F16, C_BGK> : launch_step<S_F16, C_REG>;
+    default: return bgk ? launch_step<S_BF16, C_BGK> : launch_step<S_BF16, C_REG>;
+  }
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+  std::vector<lbm_grid*> grids;
+  std::vector<BatchCase> cases_h;
+  BatchCase* cases_d = nullptr;
+  int32_t* item_case_d = nullptr;
+  int32_t* item_local_d = nullptr;
+  int64_t n_items = 0;
+  int64_t n_updated = 0;
+  int storage = 0, collision = 0;
+  int n_sm = 1;
+  int ctas_per_sm = 4;
+  cudaStream_t cap = nullptr;                 // capture stream (non-blocking)
+  std::map<int, cudaGraphExec_t> graphs;      // steps -> instantiated graph
+  StepFn fn = nullptr;
+
+  int grid_size() const { return n_sm * ctas_per_sm; }
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+};
+
+static void batch_free(lbm_batch* b) {
+  if (!b) return;
+  b->drop_graphs();
+  cudaFree(b->cases_d);
+  cudaFree(b->item_case_d);
+  cudaFree(b->item_local_d);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+// Re-upload descriptors if a case advanced on its own since the last upload.
+static lbm_status sync_descriptors(lbm_batch* b, cudaStream_t s) {
+  bool dirty = false;
+  for (size_t c = 0; c < b->grids.size(); ++c) {
+    const int cur = b->grids[c]->g.lv[0].cur;
+    if (b->cases_h[c].cur0 != cur) {
+      b->cases_h[c].cur0 = cur;
+      dirty = true;
+    }
+  }
+  if (dirty)
+    LBM_CUDA(cudaMemcpyAsync(b->cases_d, b->cases_h.data(), b->cases_h.size() * sizeof(BatchCase),
+                             cudaMemcpyHostToDevice, s));
+  return LBM_OK;
+}
+
+static void advance_bookkeeping(lbm_batch* b, int n) {
+  for (auto* h : b->grids) {
+    Level& L = h->g.lv[0];
+    if (n & 1) L.cur ^= 1;
+    h->g.steps_done += n;
+  }
+}
+
+extern "C" {
+
+lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out) {
+  set_error("");
+  if (!out || !cases || n_cases <= 0) return fail(LBM_ERR_INVALID, "bad batch arguments");
+  *out = nullptr;
+  lbm_batch* b = new lbm_batch();
+  std::vector<int32_t> ic, il;
+  for (int c = 0; c < n_cases; ++c) {
+    lbm_grid* h = cases[c];
+    if (!h) {
+      batch_free(b);
+      return fail(LBM_ERR_INVALID, "NULL case");
+    }
+    const Grid& g = h->g;
+    const Level& L = g.lv[0];
+    if (c == 0) {
+      b->storage = g.phys.storage;
+      b->collision = g.phys.collision;
+    }
+    const char* why = nullptr;
+    if (g.kind == 2) why = "multi-resolution grids cannot join a batch";
+    else if (g.phys.storage != b->storage || g.phys.collision != b->collision)
+      why = "all cases need the same storage and collision";
+    else if (L.n_reg > 0) why = "cases with regularized boundaries cannot join a batch";
+    else if (g.kind == 1 && L.E != 8) why = "sparse cases need 8^3 blocks";
+    if (why) {
+      batch_free(b);
+      return fail(LBM_ERR_UNSUPPORTED, why);
+    }
+    BatchCase d{};
+    d.kind = g.kind;
+    d.nx = L.nx;
+    d.ny = L.ny;
+    d.nz = L.nz;
+    d.px = g.phys.periodic[0];
+    d.py = g.phys.periodic[1];
+    d.pz = g.phys.periodic[2];
+    d.N = L.n_slots;
+    d.wmask = L.wmask_d;
+    d.flags = L.flags_d;
+    d.nbr = L.nbr_d;
+    d.blk_walls = L.blk_walls_d;
+    d.buf[0] = L.f[0];
+    d.buf[1] = L.f[1];
+    d.cur0 = L.cur;
+    d.omega = (float)(1.0 / g.phys.tau);
+    b->cases_h.push_back(d);
+    const int64_t items = g.kind == 0 ? (L.n_slots + BT - 1) / BT : L.n_blocks * 2;
+    for (int64_t t = 0; t < items; ++t) {
+      ic.push_back(c);
+      il.push_back((int32_t)t);
+    }
+    b->n_updated += L.n_updated;
+    b->grids.push_back(h);
+  }
+  b->n_items = (int64_t)ic.size();
+  b->fn = step_fn(b->storage, b->collision);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaMalloc(&b->cases_d, b->cases_h.size() * sizeof(BatchCase));
+  if (e == cudaSuccess) e = cudaMalloc(&b->item_case_d, ic.size() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&b->item_local_d, il.size() * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->cases_d, b->cases_h.data(), b->cases_h.size() * sizeof(BatchCase),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->item_case_d, ic.data(), ic.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->item_local_d, il.data(), il.size() * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e, "lbm_batch_create");
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+  cudaDeviceSynchronize();
+  batch_free(b);
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch* b, int64_t* n_updated, int64_t* n_items,
+                          int* ctas_per_sm) {
+  if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+  if (n_updated) *n_updated = b->n_updated;
+  if (n_items) *n_items = b->n_items;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n_steps, void* stream) {
+  if (!b || n_steps < 0) return fail(LBM_ERR_INVALID, "bad batch_step arguments");
+  if (n_steps == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  lbm_status st = sync_descriptors(b, s);
+  if (st) return st;
+  auto it = b->graphs.find(n_steps);
+  if (it == b->graphs.end()) {
+    // capture n_steps persistent launches once; parity k & 1 per step
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    LBM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < n_steps; ++k)
+      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, b->grid_size(), k & 1, b->cap);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+    it = b->graphs.emplace(n_steps, exec).first;
+  }
+  LBM_CUDA(cudaGraphLaunch(it->second, s));
+  advance_bookkeeping(b, n_steps);
+  return sync_descriptors(b, s);
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int n_steps, int* chosen, double* ms_per_step) {
+  if (!b || n_steps <= 0) return fail(LBM_ERR_INVALID, "bad batch_autotune arguments");
+  const int cand[6] = {1, 2, 3, 4, 6, 8};
+  cudaStream_t s = b->cap;
+  lbm_status st = sync_descriptors(b, s);
+  if (st) return st;
+  // save every case's state
+  size_t total = 0;
+  for (auto* h : b->grids) total += h->g.lv[0].pop_bytes;
+  void* save = nullptr;
+  LBM_CUDA(cudaMalloc(&save, total));
+  size_t off = 0;
+  for (auto* h : b->grids) {
+    const Level& L = h->g.lv[0];
+    cudaMemcpyAsync((char*)save + off, L.f[L.cur], L.pop_bytes, cudaMemcpyDeviceToDevice, s);
+    off += L.pop_bytes;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e30;
+  int best_k = b->ctas_per_sm;
+  for (int c = 0; c < 6; ++c) {
+    const int grid = b->n_sm * cand[c];
+    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 0, s);  // warm-up
+    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 1, s);
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < n_steps; ++k)
+      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, k & 1, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_per_step) ms_per_step[c] = ms / n_steps;
+    if (ms / n_steps < best) {
+      best = ms / n_steps;
+      best_k = cand[c];
+    }
+  }
+  // restore: states back into the buffers the descriptors name as current
+  off = 0;
+  for (auto* h : b->grids) {
+    const Level& L = h->g.lv[0];
+    cudaMemcpyAsync(L.f[L.cur], (char*)save + off, L.pop_bytes, cudaMemcpyDeviceToDevice, s);
+    off += L.pop_bytes;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(save);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "batch autotune");
+  if (best_k != b->ctas_per_sm) {
+    b->ctas_per_sm = best_k;
+    b->drop_graphs();
+  }
+  if (chosen) *chosen = best_k;
+  return LBM_OK;
+}
+
+}  // extern "C"

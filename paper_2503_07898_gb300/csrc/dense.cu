@@ -17,75 +17,11 @@
 //   dense_monolithic<S,COLL> the paper's naive kernel (Sec. 4): every voxel,
 //                            per-voxel branch on its flag, boundary values
 //                            read from a full-domain array
+#include "dense.cuh"
 #include "d3q19.cuh"
 #include "grid.h"
 
 namespace lbm {
-
-constexpr uint32_t WM_REG = 1u << 30;   // voxel belongs to the boundary group
-constexpr uint32_t WM_SKIP = 1u << 31;  // voxel not updated
-
-struct DenseArgs {
-  const void* fin;
-  void* fout;
-  int nx, ny, nz;
-  int64_t N;
-  int64_t vend;  // interior: process v < vend
-  int px, py, pz;
-  const uint32_t* wmask;  // null: walls only at non-periodic box sides
-  const uint8_t* flags;
-  const float4* bc;       // boundary: compact per list entry; monolithic: per voxel
-  const int32_t* list;    // boundary voxel ids (null: contiguous from v0)
-  int64_t v0, nlist;
-  float omega;
-};
-
-// Pull population I of voxel (x, y, z) with halfway bounce-back.
-template <int S, int I>
-__device__ __forceinline__ float pull_dense(const typename Codec<S>::T* __restrict__ fin,
-                                            const DenseArgs& a, int x, int y, int z, int64_t v,
-                                            uint32_t wm) {
-  int xs = x - cx(I), ys = y - cy(I), zs = z - cz(I);
-  bool wall = false;
-  if constexpr (cx(I) != 0) {
-    if (xs < 0 || xs >= a.nx) {
-      if (a.px) xs += xs < 0 ? a.nx : -a.nx; else wall = true;
-    }
-  }
-  if constexpr (cy(I) != 0) {
-    if (ys < 0 || ys >= a.ny) {
-      if (a.py) ys += ys < 0 ? a.ny : -a.ny; else wall = true;
-    }
-  }
-  if constexpr (cz(I) != 0) {
-    if (zs < 0 || zs >= a.nz) {
-      if (a.pz) zs += zs < 0 ? a.nz : -a.nz; else wall = true;
-    }
-  }
-  if constexpr (I != 0) wall = wall || ((wm >> I) & 1u);
-  const int64_t src = wall ? (int64_t)opp(I) * a.N + v
-                           : (int64_t)I * a.N + xs + (int64_t)a.nx * (ys + (int64_t)a.ny * zs);
-  return Codec<S>::template load<I>(fin[src]);
-}
-
-template <int S>
-__device__ __forceinline__ void pull_all(const typename Codec<S>::T* __restrict__ fin,
-                                         const DenseArgs& a, int x, int y, int z, int64_t v,
-                                         uint32_t wm, float g[Q]) {
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    g[I] = pull_dense<S, I>(fin, a, x, y, z, v, wm);
-  });
-}
-
-template <int S>
-__device__ __forceinline__ void store_all(typename Codec<S>::T* __restrict__ fout,
-                                          const DenseArgs& a, int64_t v, const float g[Q]) {
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    fout[(int64_t)I * a.N + v] = Codec<S>::template store<I>(g[I]);
-  });
-}
 
 // Lean pull for rows whose y and z neighbours are all inside the box (no
 // wrap, no wall): one precomputed offset per direction, x edges handled by

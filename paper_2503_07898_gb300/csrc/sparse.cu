@@ -30,6 +30,7 @@
 #include "d3q19.cuh"
 #include "grid.h"
 #include "layout.h"
+#include "sparse.cuh"
 
 namespace lbm {
 
@@ -257,23 +258,7 @@ __global__ void __launch_bounds__(SP_THREADS, MODE == MODE_INTERIOR ? 4 : 1)
   }
   const T* __restrict__ fin = (const T*)a.fin;
   float g[Q];
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
-    const int dx = sx < 0 ? -1 : (sx >= E ? 1 : 0);
-    const int dy = sy < 0 ? -1 : (sy >= E ? 1 : 0);
-    const int dz = sz < 0 ? -1 : (sz >= E ? 1 : 0);
-    int64_t nb = b;
-    if (dx | dy | dz) nb = snbr[lb * 27 + (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
-    sx -= dx * E;
-    sy -= dy * E;
-    sz -= dz * E;
-    const int ls = sx + E * (sy + E * sz);
-    bool wall = nb < 0;
-    if (walls && !wall) wall = type_wall(flag_type(a.flags[nb * E3 + ls]));
-    const int64_t src = wall ? (b * Q + opp(I)) * E3 + l : (nb * Q + I) * E3 + ls;
-    g[I] = Codec<S>::template load<I>(fin[src]);
-  });
+  sparse_pull_voxel<S, E>(fin, snbr + lb * 27, a.flags, b, l, walls, g);
   if constexpr (MODE == MODE_INTERIOR) {
     collide<COLL>(g, a.omega);
   } else {

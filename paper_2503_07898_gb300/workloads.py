@@ -159,3 +159,29 @@ def turbulence(n, seed=7898, u_rms=0.03, kmax=None, dims=None):
     u -= u.mean(axis=(1, 2, 3), keepdims=True)
     u *= u_rms / np.sqrt(np.mean(u * u))
     return np.ones((nz, ny, nx)), u
+
+
+def batch_cases(n_cases=128, seed=7898, lmin=32, lmax=160, max_solid=0.20, tau=(0.52, 0.8),
+                u0=0.02):
+    """Serving-style batch: independent periodic cases, every edge drawn
+    uniformly in [lmin, lmax] and rounded to a multiple of 8, even cases dense
+    and odd cases 8^3 block-sparse, random solid spheres (or boxes) up to a
+    drawn solid fraction in [0, max_solid], tau drawn in `tau`, a 2D
+    Taylor-Green start of amplitude u0 (batch_case_fields).  Returns a list
+    of dicts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n_cases):
+        dims = tuple(int(8 * max(1, round(int(rng.integers(lmin, lmax + 1)) / 8))) for _ in range(3))
+        frac = float(rng.uniform(0.0, max_solid))
+        nx, ny, nz = dims
+        flags = random_obstacles((nz, ny, nx), seed=seed * 1000 + c, solid_fraction=frac,
+                                 kind="spheres" if c % 4 < 2 else "boxes")
+        out.append({"kind": "dense" if c % 2 == 0 else "sparse", "dims": dims, "flags": flags,
+                    "tau": float(rng.uniform(*tau)), "u0": u0, "solid_fraction": frac})
+    return out
+
+
+def batch_case_fields(case):
+    """Initial (rho, u) of a batch case (2D Taylor-Green of amplitude u0)."""
+    return taylor_green_2d(0, u0=case["u0"], dims=case["dims"])
