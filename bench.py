@@ -141,6 +141,99 @@ def run_reference(args, rank, world):
 
 # --------------------------------------------------------------------- GPU
 
+def _time_steps(torch, lbm, step, stream, n):
+    """Device time of n calls of step() on stream, in ms."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(n)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
+    """GLUPS of the other layouts of the method on their full-size inputs
+    (context lines of the same metric; each timed after 3 warm-up steps)."""
+    out = {}
+    if "sparse" in which:
+        flags, bc = wl.sphere_channel()
+        t = flags & 7
+        bcl = np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
+        res = {}
+        for name, kw in (("disaggregated_f32", dict(storage="f32")),
+                         ("monolithic_f32", dict(storage="f32", schedule="monolithic")),
+                         ("disaggregated_f16", dict(storage="f16"))):
+            g = lbm.lbm_grid_create_sparse(flags.shape[::-1], 8, flags,
+                                           lbm.physics(0.52, **kw), stream=stream)
+            lbm.lbm_set_boundary(g, 0, None, bcl)
+            lbm.lbm_init_equilibrium(g, 0, None, None)
+            n_upd = lbm.lbm_get_info(g)["n_updated"][0]
+            lbm.lbm_step(g, 3, stream)
+            ms = _time_steps(torch, lbm, lambda n: lbm.lbm_step(g, n, stream), stream, steps)
+            bpu = 152 if kw["storage"] == "f32" else 76
+            glups = n_upd * steps / (ms * 1e-3) / 1e9
+            res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
+            lbm.lbm_grid_destroy(g)
+        out["sphere_channel_512x256x256_sparse8"] = res
+    if "multires" in which:
+        lmap = wl.multires_slab_map()
+        res = {}
+        rng = np.random.default_rng(0)
+        theta = np.concatenate([rng.standard_normal(1024) * 0.35, np.zeros(64),
+                                rng.standard_normal(4096) * 0.18, np.zeros(64),
+                                rng.standard_normal(64) * 1e-3, np.zeros(1)]).astype(np.float32)
+        for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
+                         ("fused_f16", dict(storage="f16")),
+                         ("fused_f32_learned_closure", dict(closure=1))):
+            g = lbm.lbm_grid_create_multires((256, 256, 256), 3, lmap,
+                                             lbm.physics(0.52, periodic=(1, 1, 1), **kw),
+                                             stream=stream)
+            if kw.get("closure"):
+                lbm.lbm_closure_load(g, theta)
+            info = lbm.lbm_get_info(g)
+            ups = sum(n * 2 ** (2 - l) for l, n in enumerate(info["n_updated"]))
+            for l in range(3):
+                lbm.lbm_init_equilibrium(g, l, None, None)
+            lbm.lbm_step(g, 3, stream)
+            ms = _time_steps(torch, lbm, lambda n: lbm.lbm_step(g, n, stream), stream,
+                             max(1, steps // 4))
+            glups = ups * max(1, steps // 4) / (ms * 1e-3) / 1e9
+            bpu = 76 if kw.get("storage") == "f16" else 152
+            res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
+            lbm.lbm_grid_destroy(g)
+        res["updates_per_coarsest_step"] = ups
+        out["turbulence_256_3level"] = res
+    if "batch" in which:
+        cases = wl.batch_cases()
+        grids = []
+        for c in cases:
+            phys = lbm.physics(c["tau"], storage="f16", periodic=(1, 1, 1))
+            if c["kind"] == "dense":
+                g = lbm.lbm_grid_create_dense(c["dims"], phys, stream=stream)
+                lbm.lbm_set_boundary(g, 0, c["flags"])
+            else:
+                g = lbm.lbm_grid_create_sparse(c["dims"], 8, c["flags"], phys, stream=stream)
+            rho, u = wl.batch_case_fields(c)
+            lbm.lbm_init_equilibrium(g, 0, rho, u)
+            grids.append(g)
+        b = lbm.lbm_batch_create(grids)
+        k, _ = lbm.lbm_batch_autotune(b, 4)
+        info = lbm.lbm_batch_info(b)
+        lbm.lbm_batch_step(b, steps, stream)        # captures the graph
+        torch.cuda.synchronize()
+        ms = _time_steps(torch, lbm, lambda n: lbm.lbm_batch_step(b, n, stream), stream, steps)
+        glups = info["n_updated"] * steps / (ms * 1e-3) / 1e9
+        out["serving_batch_128_f16"] = {"GLUPS": round(glups, 3),
+                                        "roofline_frac": round(glups * 76 / peak, 4),
+                                        "updated_voxels": info["n_updated"],
+                                        "ctas_per_sm": k, "launches_per_step": 1}
+        del b
+        for g in grids:
+            lbm.lbm_grid_destroy(g)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -239,6 +332,13 @@ def run_ours(args, rank, world, local_rank):
                                                      / (vms * 1e-3) / 1e9 / peak, 4)}
             lbm.lbm_grid_destroy(gv)
 
+    workloads = {}
+    if args.workloads != "none" and rank == 0:
+        which = ("sparse", "multires", "batch") if args.workloads == "all" else tuple(
+            args.workloads.split(","))
+        workloads = measure_workloads(torch, lbm, wl, stream, peaks()[0], min(args.steps, 100),
+                                      which)
+
     # end to end through the C ABI with pinned host buffers: init from host
     # (rho, u), K steps, moments back to host
     nv = n ** 3
@@ -295,6 +395,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(),
             "variants": variants,
+            "workloads": workloads,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -316,6 +417,8 @@ def main():
     ap.add_argument("--variant", default="auto", choices=["auto", "vec16", "scalar", "vec8"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workloads", default="all",
+                    help="all | none | comma list of sparse,multires,batch")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
