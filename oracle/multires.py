@@ -34,11 +34,20 @@ at the finest resolution is a permutation and averaging keeps the sum of the
 exactly in a periodic box.  There is no rescaling of non-equilibrium parts
 between levels.
 
+Learned closure (optional, not in the paper): on every level l >= 1 each
+owned voxel collides with tau_eff = max(tau_l + d_tau, 1/2 + 1e-3), where
+d_tau is the closure network (oracle/closure.py) applied to the features of
+the populations the voxel pulled this step (after explosion / coalescence)
+and tau_l; level 0 keeps tau_0.  The network parameters are used as given
+(FP64), so a caller that wants the storage precision of the weights rounds
+them first.
+
 State: f[l] is a (19, nz_l, ny_l, nx_l) array over the whole level-l virtual
 box, zero where level l does not own the region.  The box is periodic.
 """
 import numpy as np
 
+from . import closure as cl
 from . import lattice as L
 from . import lbm
 
@@ -69,8 +78,9 @@ class MultiRes:
     """Multi-resolution grid: level_map (Mz, My, Mx) gives the owning level of
     every cube of `cell` finest voxels; cell must be a multiple of 2^(L-1)."""
 
-    def __init__(self, level_map, n_levels, cell, tau0, collision="bgk"):
+    def __init__(self, level_map, n_levels, cell, tau0, collision="bgk", theta=None):
         level_map = np.asarray(level_map, dtype=np.int64)
+        self.theta = None if theta is None else np.asarray(theta, dtype=np.float64)
         assert cell % (2 ** (n_levels - 1)) == 0
         self.L = n_levels
         self.tau0 = tau0
@@ -130,8 +140,14 @@ class MultiRes:
                 coal = subcell_mean(shift(held, c))
                 val = np.where(has_finer, coal, val)
             g[i] = val
+        tau = tau_of_level(self.tau0, lv)
+        if self.theta is not None and lv > 0:
+            mine = own == lv
+            d_tau, _ = cl.forward(self.theta, cl.features(g[:, mine], tau))
+            tau = np.full(own.shape, tau)
+            tau[mine] = np.maximum(tau[mine] + d_tau, cl.TAU_MIN)
         with np.errstate(invalid="ignore", divide="ignore"):   # unowned voxels hold zeros
-            fnew, _, _ = lbm.collide(g, tau_of_level(self.tau0, lv), self.collision)
+            fnew, _, _ = lbm.collide(g, tau, self.collision)
         self.f[lv] = np.where(own[None] == lv, fnew, 0.0)
 
     def step(self):

@@ -161,3 +161,75 @@ def test_closure_gain_over_plain_coarse_level(lbm):
     print(f"coarse-level velocity L2 vs filtered fine run: plain {errs[0]:.4f}, "
           f"learned closure {errs[1]:.4f} (gain {100 * (1 - errs[1] / errs[0]):.2f} %)")
     assert errs[1] < errs[0]
+
+
+def storage_weights(theta):
+    """The parameters as the collision kernels hold them: W1, W2, W3 rounded
+    to BF16 (nearest even), biases FP32."""
+    th = np.asarray(theta, np.float32)
+    bits = th.view(np.uint32).astype(np.uint64)
+    rounded = (((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16) << 16).astype(np.uint32)
+    bf = rounded.view(np.float32).astype(np.float64)
+    out = th.astype(np.float64)
+    for sl in (slice(0, 1024), slice(1088, 5184), slice(5248, 5312)):
+        out[sl] = bf[sl]
+    return out
+
+
+@pytest.mark.parametrize("collision", ["bgk", "reg"])
+def test_multires_step_with_closure_matches_oracle(lbm, collision):
+    """The closure fused into the multi-resolution collision (levels 1 and 2
+    of a coarse - middle - fine - middle hierarchy) against the FP64 oracle
+    running the same BF16-rounded network.  Tolerance: the FP32 bar plus the
+    oracle's own response to a 2e-2 relative change of d_tau (the BF16
+    network's bound against the FP64 one)."""
+    from cases import F32_RTOL
+    from oracle import multires as omr
+    lmap = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
+    tau0, steps = 0.56, 3
+    dims = (32, 32, 128)
+    fields = []
+    for lv in range(3):
+        nx, ny, nz = (d >> lv for d in dims)
+        fields.append(wl.random_fields((nz, ny, nx), seed=120 + lv, u_amp=0.02))
+    # weights on the scale of the features of this state, d_tau ~ 1e-2
+    rho, u = fields[1]
+    X = ocl.features(olbm.init_equilibrium(rho, u), omr.tau_of_level(tau0, 1)).reshape(-1, 16)
+    sd = X.std(axis=0)
+    sd[sd < 1e-9] = 1.0
+    theta = he_init(121, scale_out=0.05)
+    theta[:1024] = (theta[:1024].reshape(64, 16) / sd).ravel()
+    theta = theta.astype(np.float32)
+    th = storage_weights(theta)
+
+    def oracle_run(t):
+        o = omr.MultiRes(lmap, 3, 32, tau0, collision, theta=t)
+        for lv, (r, v) in enumerate(fields):
+            o.init_equilibrium(lv, r, v)
+        o.run(steps)
+        return o
+
+    o = oracle_run(th)
+    th_eps = th.copy()
+    th_eps[5248:] *= 1 + 2e-2
+    o_eps = oracle_run(th_eps)
+    g = lbm.lbm_grid_create_multires(dims, 3, lmap, lbm.physics(
+        tau0, collision, periodic=(1, 1, 1), closure=1))
+    lbm.lbm_closure_load(g, theta)
+    for lv, (r, v) in enumerate(fields):
+        lbm.lbm_init_equilibrium(g, lv, r, v)
+    lbm.lbm_step(g, steps)
+    worst = sens = 0.0
+    for lv in range(3):
+        m = o.own[lv] == lv
+        ref = o.f[lv][:, m]
+        got = lbm.lbm_get_populations_f64(g, lv)[:, m]
+        worst = max(worst, float(np.max(np.abs(got - ref) / np.abs(ref))))
+        sens = max(sens, float(np.max(np.abs(o_eps.f[lv][:, m] - ref) / np.abs(ref))))
+    base = oracle_run(None)
+    effect = max(float(np.max(np.abs(base.f[lv][:, o.own[lv] == lv] - o.f[lv][:, o.own[lv] == lv])
+                              / np.abs(o.f[lv][:, o.own[lv] == lv]))) for lv in (1, 2))
+    print(f"closure effect {effect:.3e}, GPU vs oracle {worst:.3e}, "
+          f"tolerance {F32_RTOL + sens:.3e}")
+    assert effect > 10 * (F32_RTOL + sens)      # the closure visibly changes the flow
+    assert worst <= F32_RTOL + sens

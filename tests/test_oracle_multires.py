@@ -9,6 +9,7 @@ rate of a Taylor-Green vortex crossing a level jump.
 import numpy as np
 import pytest
 
+from oracle import closure as ocl
 from oracle import lattice as L
 from oracle import lbm as olbm
 from oracle import multires as mr
@@ -138,3 +139,69 @@ def test_taylor_green_across_level_jump():
     # rescaling) damps faster, within a bounded band
     assert np.all(np.abs(ratio[0] - 1) < 0.25) and np.all(np.abs(ratio[1] - 1) < 0.25)
     assert np.all(np.isfinite(g.conservation()))
+
+
+# ---------------------------------------------------------------- closure
+
+def _net(b3=0.0):
+    return np.concatenate([np.zeros(ocl.N_PARAMS - 1), [b3]])
+
+
+def _plain(rho, u, tau, n):
+    return olbm.run(olbm.init_equilibrium(rho, u), np.zeros(rho.shape, np.uint8), tau, n,
+                    periodic=(True, True, True))
+
+
+def test_closure_zero_network_changes_nothing():
+    ref = three_level(0.58)
+    init_random(ref, 53)
+    ref.run(3)
+    g = mr.MultiRes(np.array([2, 1, 0, 1]).reshape(4, 1, 1), 3, 8, 0.58, theta=_net())
+    init_random(g, 53)
+    g.run(3)
+    for a, b in zip(ref.f, g.f):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("b3,level", [(0.03, 2), (-0.004, 1), (0.03, 0), (-1.0, 2)])
+def test_closure_constant_output_shifts_tau_of_coarse_levels(b3, level):
+    """A network with constant output b3 on a grid owned by one level: levels
+    >= 1 run the plain oracle at max(tau_l + b3, 1/2 + 1e-3), level 0 at tau_0."""
+    tau0 = 0.56
+    g = mr.MultiRes(np.full((2, 1, 1), level), 3, 8, tau0, theta=_net(b3))
+    nx, ny, nz = g.dims(level)
+    rho, u = wl.random_fields((nz, ny, nx), seed=54 + level)
+    g.init_equilibrium(level, rho, u)
+    g.run(2)
+    tau_l = mr.tau_of_level(tau0, level)
+    tau = tau_l if level == 0 else max(tau_l + b3, 0.5 + 1e-3)
+    ref = _plain(rho, u, tau, 2 ** (2 - level) * 2)
+    assert np.max(np.abs(g.f[level] - ref)) < 1e-15
+
+
+def test_closure_sees_tau_of_its_level():
+    """Network d_tau = relu(relu(feature 15)) = tau_l: level 1 then relaxes
+    with 2 tau_1."""
+    th = ocl.unpack(_net())
+    th["W1"][0, 15] = 1.0
+    th["W2"][0, 0] = 1.0
+    th["W3"][0] = 1.0
+    g = mr.MultiRes(np.full((2, 1, 1), 1), 2, 8, 0.6, theta=ocl.pack(th))
+    nx, ny, nz = g.dims(1)
+    rho, u = wl.random_fields((nz, ny, nx), seed=56)
+    g.init_equilibrium(1, rho, u)
+    g.run(3)
+    ref = _plain(rho, u, 2 * mr.tau_of_level(0.6, 1), 3)
+    assert np.max(np.abs(g.f[1] - ref)) < 1e-15
+
+
+def test_closure_keeps_volume_weighted_conservation():
+    rng = np.random.default_rng(57)
+    th = rng.standard_normal(ocl.N_PARAMS) * 0.05
+    g = mr.MultiRes(np.array([2, 1, 0, 1]).reshape(4, 1, 1), 3, 8, 0.6, theta=th)
+    init_random(g, 58)
+    m0 = g.conservation()
+    g.run(3)
+    m1 = g.conservation()
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
+    assert np.all(np.abs(m1[1:] - m0[1:]) < 1e-12 * m0[0])
