@@ -156,6 +156,12 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
     """GLUPS of the other layouts of the method on their full-size inputs
     (context lines of the same metric; each timed after 3 warm-up steps)."""
     out = {}
+    # a closure network of the trained one's size and scale (random weights:
+    # the cost of inference does not depend on their values)
+    rng = np.random.default_rng(0)
+    theta = np.concatenate([rng.standard_normal(1024) * 0.35, np.zeros(64),
+                            rng.standard_normal(4096) * 0.18, np.zeros(64),
+                            rng.standard_normal(64) * 1e-3, np.zeros(1)]).astype(np.float32)
     if "sparse" in which:
         flags, bc = wl.sphere_channel()
         t = flags & 7
@@ -179,10 +185,6 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
     if "multires" in which:
         lmap = wl.multires_slab_map()
         res = {}
-        rng = np.random.default_rng(0)
-        theta = np.concatenate([rng.standard_normal(1024) * 0.35, np.zeros(64),
-                                rng.standard_normal(4096) * 0.18, np.zeros(64),
-                                rng.standard_normal(64) * 1e-3, np.zeros(1)]).astype(np.float32)
         for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
                          ("fused_f16", dict(storage="f16")),
                          ("fused_f32_learned_closure", dict(closure=1))):
@@ -228,6 +230,17 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
                                         "roofline_frac": round(glups * 76 / peak, 4),
                                         "updated_voxels": info["n_updated"],
                                         "ctas_per_sm": k, "launches_per_step": 1}
+        # the learned closure on the cases whose largest edge is <= 64
+        lbm.lbm_batch_closure_load(b, theta, 64)
+        n_cl = sum(1 for c in cases if max(c["dims"]) <= 64)
+        k, _ = lbm.lbm_batch_autotune(b, 4)
+        lbm.lbm_batch_step(b, steps, stream)
+        torch.cuda.synchronize()
+        ms = _time_steps(torch, lbm, lambda n: lbm.lbm_batch_step(b, n, stream), stream, steps)
+        glups = info["n_updated"] * steps / (ms * 1e-3) / 1e9
+        out["serving_batch_128_f16_learned_closure"] = {
+            "GLUPS": round(glups, 3), "roofline_frac": round(glups * 76 / peak, 4),
+            "closure_cases": n_cl, "max_edge": 64, "ctas_per_sm": k, "launches_per_step": 1}
         del b
         for g in grids:
             lbm.lbm_grid_destroy(g)

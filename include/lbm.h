@@ -302,8 +302,10 @@ lbm_status lbm_closure_load(lbm_grid* g, const float* theta, size_t n);
  * (dense: consecutive voxel ids; sparse: half blocks), the steps of one
  * lbm_batch_step call captured once into a CUDA graph and replayed.
  * Cases keep their own state, walls and tau; they must share storage and
- * collision and have no regularized voxels.  A case may still be used on its
- * own (lbm_get_moments, lbm_step, ...) between batch steps. */
+ * collision, have no regularized voxels and fewer than 2^31 / 19 voxels
+ * (slots) each; otherwise lbm_batch_create returns LBM_ERR_UNSUPPORTED.  A
+ * case may still be used on its own (lbm_get_moments, lbm_step, ...) between
+ * batch steps. */
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out);
 lbm_status lbm_batch_destroy(lbm_batch* b);
@@ -314,6 +316,14 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps, void* stream);
  * 8 CTAs per SM from the current states (restored afterwards), keeps the
  * fastest; *chosen gets it, ms_per_step (6 doubles or NULL) the timings. */
 lbm_status lbm_batch_autotune(lbm_batch* b, int n_steps, int* chosen, double* ms_per_step);
+/* Learned closure on the small cases of a batch, the same network and
+ * parameter layout as lbm_closure_load: every case whose largest edge is at
+ * most max_edge collides with tau_eff = max(tau + d_tau, 1/2 + 1e-3) on each
+ * fluid voxel, d_tau the network evaluated on the features of the voxel's
+ * pulled populations and the case's tau (BF16 weights on tensor cores, FP32
+ * accumulation).  theta: host, n = 5313 FP32, copied.  max_edge <= 0 turns
+ * the closure off (theta may then be NULL).  Captured graphs are dropped. */
+lbm_status lbm_batch_closure_load(lbm_batch* b, const float* theta, size_t n, int max_edge);
 lbm_status lbm_batch_info(const lbm_batch* b, int64_t* n_updated, int64_t* n_items,
                           int* ctas_per_sm);
 

@@ -16,7 +16,9 @@ network
     parameters, flattened in this order: W1 (64 x 16, row j = unit j),
     b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1)  -> 5313 values
 collision with the closure
-    tau_eff = max(tau + d_tau, 1/2 + 1e-3)
+    tau_eff = max(tau + d_tau, 1/2 + 1e-3); `step` is one single-resolution
+    time step with it on every fluid voxel (the multi-resolution oracle applies
+    it on levels >= 1)
 training data
     box-filter a fine periodic run by r^3 (mean of the populations), stream
     the filtered populations one coarse step (the values a coarse voxel
@@ -190,3 +192,28 @@ def fold_normalisation(theta, mu, sd, y_mean, y_sd):
     p["W3"] = p["W3"] * y_sd
     p["b3"] = p["b3"] * y_sd + y_mean
     return pack(p)
+
+
+def step(f, flags, tau, theta, collision="bgk", periodic=(False, False, False)):
+    """One time step of a single-resolution grid with the closure on every
+    fluid voxel: pull with halfway bounce-back (as oracle.lbm.step), features
+    of the pulled populations and tau, tau_eff = max(tau + d_tau, 1/2 + 1e-3),
+    collision with tau_eff.  Regularized boundary voxels are not supported."""
+    from . import lbm
+    types = lbm.flag_type(flags)
+    if np.any((types == lbm.VELOCITY) | (types == lbm.PRESSURE)):
+        raise ValueError("the closure step has no regularized boundaries")
+    g = lbm.stream_with_walls(f, flags, periodic)
+    fluid = types == lbm.FLUID
+    d_tau, _ = forward(theta, features(g[:, fluid], tau))
+    tau_eff = np.full(flags.shape, float(tau))
+    tau_eff[fluid] = np.maximum(tau + d_tau, TAU_MIN)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        f_new, _, _ = lbm.collide(g, tau_eff, collision)
+    return np.where(fluid[None], f_new, 0.0)
+
+
+def run(f, flags, tau, theta, n_steps, **kw):
+    for _ in range(n_steps):
+        f = step(f, flags, tau, theta, **kw)
+    return f

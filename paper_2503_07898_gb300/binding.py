@@ -103,6 +103,7 @@ def load():
         "lbm_batch_step": [vp, I, vp],
         "lbm_batch_autotune": [vp, I, P(I), P(C.c_double)],
         "lbm_batch_info": [vp, P(C.c_int64), P(C.c_int64), P(I)],
+        "lbm_batch_closure_load": [vp, vp, C.c_size_t, I],
         "lbm_profile": [vp, I],
         "lbm_profile_read": [vp, P(lbm_kernel_stat), I, P(I)],
     }
@@ -479,6 +480,17 @@ def lbm_batch_info(batch):
     _check(load().lbm_batch_info(batch.ptr, C.byref(nu), C.byref(ni), C.byref(k)),
            "lbm_batch_info")
     return {"n_updated": nu.value, "n_items": ni.value, "ctas_per_sm": k.value}
+
+
+def lbm_batch_closure_load(batch, theta, max_edge):
+    """Closure on every case whose largest edge is <= max_edge (0: off)."""
+    if theta is None:
+        _check(load().lbm_batch_closure_load(batch.ptr, None, 0, int(max_edge)),
+               "lbm_batch_closure_load")
+        return
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(load().lbm_batch_closure_load(batch.ptr, C.c_void_p(th.ctypes.data), th.size,
+                                         int(max_edge)), "lbm_batch_closure_load")
 
 
 def lbm_profile(grid, enable):

@@ -8,9 +8,11 @@
 // step over the whole batch is a single launch whatever the number of cases.
 // A sequence of steps is captured once into a CUDA graph and replayed.  The
 // persistent grid size (CTAs per SM) is the tuning knob of lbm_batch_autotune.
+#include <algorithm>
 #include <map>
 #include <vector>
 
+#include "closure.cuh"
 #include "d3q19.cuh"
 #include "dense.cuh"
 #include "grid.h"
@@ -29,17 +31,25 @@ struct BatchCase {
   void* buf[2];
   int cur0;  // buffer holding the state before step parity 0
   float omega;
+  float tau;
+  int closure;  // learned closure on this case (lbm_batch_closure_load)
 };
 
 constexpr int BT = 256;  // threads per CTA = voxels per work item
 
-template <int S, int COLL>
+template <int S, int COLL, bool CLOSURE>
 __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restrict__ cases,
                                                         const int32_t* __restrict__ item_case,
                                                         const int32_t* __restrict__ item_local,
-                                                        int64_t n_items, int parity) {
+                                                        int64_t n_items, int parity,
+                                                        const ClosureParams* __restrict__ cp) {
   using T = typename Codec<S>::T;
   __shared__ int32_t snbr[27];
+  extern __shared__ __align__(16) unsigned char batch_dyn_smem[];
+  if constexpr (CLOSURE) {
+    closure_load_smem(reinterpret_cast<ClosureCta*>(batch_dyn_smem)->w, cp);
+    __syncthreads();
+  }
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const BatchCase& C = cases[item_case[it]];
     const int64_t t = item_local[it];
@@ -47,9 +57,22 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
     const T* __restrict__ fin = (const T*)C.buf[in];
     T* __restrict__ fout = (T*)C.buf[in ^ 1];
     float g[Q];
+    bool act;
+    int64_t obase;  // output index of population 0; population I adds I * ostride
+    int ostride;
     if (C.kind == 0) {
-      const int64_t v = t * BT + threadIdx.x;
-      if (v < C.N) {
+      // case sizes are below 2^31 / 19 voxels (checked at creation): 32-bit
+      // voxel ids and offsets
+      const int v = (int)t * BT + threadIdx.x;
+      uint32_t wm = 0u;
+      act = v < C.N;
+      if (act && C.wmask) {
+        wm = C.wmask[v];
+        act = !(wm & (WM_SKIP | WM_REG));
+      }
+      obase = v;
+      ostride = (int)C.N;
+      if (act) {
         DenseArgs a{};
         a.nx = C.nx;
         a.ny = C.ny;
@@ -58,55 +81,76 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
         a.px = C.px;
         a.py = C.py;
         a.pz = C.pz;
-        const int x = (int)(v % C.nx);
-        const int y = (int)((v / C.nx) % C.ny);
-        const int z = (int)(v / ((int64_t)C.nx * C.ny));
-        uint32_t wm = C.wmask ? C.wmask[v] : 0u;
-        if (!(wm & (WM_SKIP | WM_REG))) {
+        const int row = v / C.nx;
+        const int x = v - row * C.nx;
+        const int z = row / C.ny;
+        const int y = row - z * C.ny;
+        if (y > 0 && y < C.ny - 1 && z > 0 && z < C.nz - 1) {
+          if (wm) pull_row_interior<S, int, true>(fin, a, x, v, wm, g);
+          else pull_row_interior<S, int, false>(fin, a, x, v, 0u, g);
+        } else {
           pull_all<S>(fin, a, x, y, z, v, wm, g);
-          collide<COLL>(g, C.omega);
-          static_for<Q>([&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            fout[(int64_t)I * C.N + v] = Codec<S>::template store<I>(g[I]);
-          });
         }
       }
     } else {
-      const int64_t b = t >> 1;
+      const int b = (int)(t >> 1);
       const int l = (int)(t & 1) * BT + threadIdx.x;
-      if (threadIdx.x < 27) snbr[threadIdx.x] = C.nbr[b * 27 + threadIdx.x];
+      if (threadIdx.x < 27) snbr[threadIdx.x] = C.nbr[(int64_t)b * 27 + threadIdx.x];
       __syncthreads();
       const bool walls = C.blk_walls[b] != 0;
-      const bool upd = !walls || type_updated(flag_type(C.flags[b * 512 + l]));
-      if (upd) {
-        sparse_pull_voxel<S, 8>(fin, snbr, C.flags, b, l, walls, g);
-        collide<COLL>(g, C.omega);
-        static_for<Q>([&](auto ic) {
-          constexpr int I = decltype(ic)::value;
-          fout[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
-        });
+      act = !walls || type_updated(flag_type(C.flags[(int64_t)b * 512 + l]));
+      obase = (int64_t)b * (Q * 512) + l;
+      ostride = 512;
+      if (act) sparse_pull_voxel<S, 8>(fin, snbr, C.flags, b, l, walls, g);
+    }
+    float omega = C.omega;
+    if constexpr (CLOSURE) {
+      if (C.closure) {  // uniform per item: every lane of every warp takes part
+        if (!act) {
+#pragma unroll
+          for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state, finite features
+        }
+        ClosureCta* sm = reinterpret_cast<ClosureCta*>(batch_dyn_smem);
+        float x[MLP_IN];
+        closure_features(g, C.tau, x);
+        const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
+        omega = 1.f / fmaxf(C.tau + dtau, TAU_MIN);
       }
     }
-    __syncthreads();  // the neighbour list is reused by the next item
+    if (act) {
+      collide<COLL>(g, omega);
+      static_for<Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        fout[obase + I * ostride] = Codec<S>::template store<I>(g[I]);
+      });
+    }
+    __syncthreads();  // the neighbour list and the staging tiles are reused
   }
 }
 
-template <int S, int COLL>
+template <int S, int COLL, bool CLOSURE>
 static void launch_step(const BatchCase* cases, const int32_t* ic, const int32_t* il,
-                        int64_t n_items, int grid, int parity, cudaStream_t s) {
-  batch_step_kernel<S, COLL><<<grid, BT, 0, s>>>(cases, ic, il, n_items, parity);
+                        int64_t n_items, int grid, int parity, const ClosureParams* cp,
+                        cudaStream_t s) {
+  const size_t smem = CLOSURE ? sizeof(ClosureCta) : 0;
+  batch_step_kernel<S, COLL, CLOSURE><<<grid, BT, smem, s>>>(cases, ic, il, n_items, parity, cp);
 }
 
 using StepFn = void (*)(const BatchCase*, const int32_t*, const int32_t*, int64_t, int, int,
-                        cudaStream_t);
+                        const ClosureParams*, cudaStream_t);
 
-static StepFn step_fn(int storage, int collision) {
+template <bool CL>
+static StepFn step_fn_t(int storage, int collision) {
   const bool bgk = collision == C_BGK;
   switch (storage) {
-    case S_F32: return bgk ? launch_step<S_F32, C_BGK> : launch_step<S_F32, C_REG>;
-    case S_F16: return bgk ? launch_step<S_F16, C_BGK> : launch_step<S_F16, C_REG>;
-    default: return bgk ? launch_step<S_BF16, C_BGK> : launch_step<S_BF16, C_REG>;
+    case S_F32: return bgk ? launch_step<S_F32, C_BGK, CL> : launch_step<S_F32, C_REG, CL>;
+    case S_F16: return bgk ? launch_step<S_F16, C_BGK, CL> : launch_step<S_F16, C_REG, CL>;
+    default: return bgk ? launch_step<S_BF16, C_BGK, CL> : launch_step<S_BF16, C_REG, CL>;
   }
+}
+
+static StepFn step_fn(int storage, int collision, bool closure) {
+  return closure ? step_fn_t<true>(storage, collision) : step_fn_t<false>(storage, collision);
 }
 
 }  // namespace lbm
@@ -124,6 +168,8 @@ struct lbm_batch {
   int storage = 0, collision = 0;
   int n_sm = 1;
   int ctas_per_sm = 4;
+  ClosureParams* cp_d = nullptr;              // learned closure weights (device)
+  bool closure = false;                       // some case runs the closure
   cudaStream_t cap = nullptr;                 // capture stream (non-blocking)
   std::map<int, cudaGraphExec_t> graphs;      // steps -> instantiated graph
   StepFn fn = nullptr;
@@ -141,6 +187,7 @@ static void batch_free(lbm_batch* b) {
   cudaFree(b->cases_d);
   cudaFree(b->item_case_d);
   cudaFree(b->item_local_d);
+  cudaFree(b->cp_d);
   if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
 }
@@ -195,6 +242,7 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
       why = "all cases need the same storage and collision";
     else if (L.n_reg > 0) why = "cases with regularized boundaries cannot join a batch";
     else if (g.kind == 1 && L.E != 8) why = "sparse cases need 8^3 blocks";
+    else if (L.n_slots * Q >= ((int64_t)1 << 31)) why = "case too large for a batch (19 N >= 2^31)";
     if (why) {
       batch_free(b);
       return fail(LBM_ERR_UNSUPPORTED, why);
@@ -216,6 +264,8 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
     d.buf[1] = L.f[1];
     d.cur0 = L.cur;
     d.omega = (float)(1.0 / g.phys.tau);
+    d.tau = (float)g.phys.tau;
+    d.closure = 0;
     b->cases_h.push_back(d);
     const int64_t items = g.kind == 0 ? (L.n_slots + BT - 1) / BT : L.n_blocks * 2;
     for (int64_t t = 0; t < items; ++t) {
@@ -226,7 +276,7 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
     b->grids.push_back(h);
   }
   b->n_items = (int64_t)ic.size();
-  b->fn = step_fn(b->storage, b->collision);
+  b->fn = step_fn(b->storage, b->collision, false);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -263,6 +313,33 @@ lbm_status lbm_batch_info(const lbm_batch* b, int64_t* n_updated, int64_t* n_ite
   return LBM_OK;
 }
 
+lbm_status lbm_batch_closure_load(lbm_batch* b, const float* theta, size_t n, int max_edge) {
+  set_error("");
+  if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+  if (max_edge > 0 && !theta) return fail(LBM_ERR_INVALID, "NULL weights");
+  if (max_edge > 0 && n != (size_t)MLP_PARAMS)
+    return fail(LBM_ERR_INVALID, "closure weights must have 5313 values");
+  cudaStream_t s = b->cap;
+  if (max_edge > 0) {
+    ClosureParams cp;
+    closure_params_from_fp32(theta, &cp);
+    if (!b->cp_d) LBM_CUDA(cudaMalloc(&b->cp_d, sizeof(ClosureParams)));
+    LBM_CUDA(cudaMemcpyAsync(b->cp_d, &cp, sizeof(cp), cudaMemcpyHostToDevice, s));
+  }
+  bool any = false;
+  for (auto& d : b->cases_h) {
+    d.closure = max_edge > 0 && std::max(d.nx, std::max(d.ny, d.nz)) <= max_edge;
+    any = any || d.closure;
+  }
+  LBM_CUDA(cudaMemcpyAsync(b->cases_d, b->cases_h.data(), b->cases_h.size() * sizeof(BatchCase),
+                           cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaStreamSynchronize(s));
+  b->closure = any;
+  b->fn = step_fn(b->storage, b->collision, any);
+  b->drop_graphs();
+  return LBM_OK;
+}
+
 lbm_status lbm_batch_step(lbm_batch* b, int n_steps, void* stream) {
   if (!b || n_steps < 0) return fail(LBM_ERR_INVALID, "bad batch_step arguments");
   if (n_steps == 0) return LBM_OK;
@@ -276,7 +353,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps, void* stream) {
     cudaGraphExec_t exec = nullptr;
     LBM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < n_steps; ++k)
-      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, b->grid_size(), k & 1, b->cap);
+      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, b->grid_size(), k & 1,
+            b->cp_d, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
@@ -312,11 +390,11 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int n_steps, int* chosen, double* ms
   int best_k = b->ctas_per_sm;
   for (int c = 0; c < 6; ++c) {
     const int grid = b->n_sm * cand[c];
-    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 0, s);  // warm-up
-    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 1, s);
+    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 0, b->cp_d, s);  // warm-up
+    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 1, b->cp_d, s);
     cudaEventRecord(e0, s);
     for (int k = 0; k < n_steps; ++k)
-      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, k & 1, s);
+      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, k & 1, b->cp_d, s);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms = 0.f;

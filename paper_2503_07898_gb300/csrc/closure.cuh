@@ -62,6 +62,13 @@ struct ClosureSmem {
   float b3;
 };
 
+// Shared memory of a 256-thread CTA running the closure: network weights and
+// per-warp feature staging (dynamic, so plain kernel variants stay without it).
+struct ClosureCta {
+  ClosureSmem w;
+  __nv_bfloat16 stage[8][32 * FSTAGE];
+};
+
 __device__ __forceinline__ void closure_load_smem(ClosureSmem& sm, const ClosureParams* p) {
   for (int i = threadIdx.x; i < MLP_H * MLP_IN; i += blockDim.x)
     sm.w1[(i / MLP_IN) * W1S + i % MLP_IN] = p->w1[i];

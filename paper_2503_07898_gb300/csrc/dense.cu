@@ -23,25 +23,6 @@
 
 namespace lbm {
 
-// Lean pull for rows whose y and z neighbours are all inside the box (no
-// wrap, no wall): one precomputed offset per direction, x edges handled by
-// predicated selects.  IDX is int32_t when 19 N fits in 31 bits.
-template <int S, class IDX>
-__device__ __forceinline__ void pull_row_interior(const typename Codec<S>::T* __restrict__ fin,
-                                                  const DenseArgs& a, int x, IDX v, float g[Q]) {
-  const IDX N = (IDX)a.N, nx = (IDX)a.nx, plane = (IDX)a.nx * (IDX)a.ny;
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    IDX src = (IDX)I * N + v - ((IDX)cx(I) + (IDX)cy(I) * nx + (IDX)cz(I) * plane);
-    if constexpr (cx(I) > 0) {
-      if (x == 0) src = a.px ? src + nx : (IDX)opp(I) * N + v;
-    } else if constexpr (cx(I) < 0) {
-      if (x == a.nx - 1) src = a.px ? src - nx : (IDX)opp(I) * N + v;
-    }
-    g[I] = Codec<S>::template load<I>(fin[src]);
-  });
-}
-
 template <int S, int COLL, class IDX>
 __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
   using T = typename Codec<S>::T;
@@ -52,16 +33,17 @@ __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
   const int64_t v = x + (int64_t)a.nx * (y + (int64_t)a.ny * z);
   if (v >= a.vend) return;
   float g[Q];
+  uint32_t wm = 0;
+  if (a.wmask) {
+    wm = a.wmask[v];
+    if (wm & (WM_SKIP | WM_REG)) return;
+  }
   // warp-uniform choice: a warp holds one (y, z) row
-  const bool lean = !a.wmask && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1;
+  const bool lean = y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1;
   if (lean) {
-    pull_row_interior<S, IDX>((const T*)a.fin, a, x, (IDX)v, g);
+    if (wm) pull_row_interior<S, IDX, true>((const T*)a.fin, a, x, (IDX)v, wm, g);
+    else pull_row_interior<S, IDX, false>((const T*)a.fin, a, x, (IDX)v, 0u, g);
   } else {
-    uint32_t wm = 0;
-    if (a.wmask) {
-      wm = a.wmask[v];
-      if (wm & (WM_SKIP | WM_REG)) return;
-    }
     pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
   }
   collide<COLL>(g, a.omega);

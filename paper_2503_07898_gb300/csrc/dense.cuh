@@ -62,6 +62,30 @@ __device__ __forceinline__ void pull_all(const typename Codec<S>::T* __restrict_
   });
 }
 
+// Lean pull for rows whose y and z neighbours are all inside the box (no
+// wrap, no box-side wall in y or z): one precomputed offset per direction,
+// x edges handled by predicated selects, wall-mask bits (WM) by one bit test
+// per direction.  IDX is int32_t when 19 N fits in 31 bits.
+template <int S, class IDX, bool WM>
+__device__ __forceinline__ void pull_row_interior(const typename Codec<S>::T* __restrict__ fin,
+                                                  const DenseArgs& a, int x, IDX v, uint32_t wm,
+                                                  float g[Q]) {
+  const IDX N = (IDX)a.N, nx = (IDX)a.nx, plane = (IDX)a.nx * (IDX)a.ny;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    IDX src = (IDX)I * N + v - ((IDX)cx(I) + (IDX)cy(I) * nx + (IDX)cz(I) * plane);
+    if constexpr (cx(I) > 0) {
+      if (x == 0) src = a.px ? src + nx : (IDX)opp(I) * N + v;
+    } else if constexpr (cx(I) < 0) {
+      if (x == a.nx - 1) src = a.px ? src - nx : (IDX)opp(I) * N + v;
+    }
+    if constexpr (WM && I != 0) {
+      if ((wm >> I) & 1u) src = (IDX)opp(I) * N + v;
+    }
+    g[I] = Codec<S>::template load<I>(fin[src]);
+  });
+}
+
 template <int S>
 __device__ __forceinline__ void store_all(typename Codec<S>::T* __restrict__ fout,
                                           const DenseArgs& a, int64_t v, const float g[Q]) {

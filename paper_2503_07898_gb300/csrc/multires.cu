@@ -265,13 +265,6 @@ template <> struct TmpCodec<S_F32> {
   template <int I> __device__ static __forceinline__ T store(float s) { return s; }
 };
 
-// Shared memory of the closure variant: network weights and per-warp
-// feature staging (dynamic, so the plain variants stay without it).
-struct ClosureCta {
-  ClosureSmem w;
-  __nv_bfloat16 stage[8][32 * FSTAGE];
-};
-
 template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
 __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;

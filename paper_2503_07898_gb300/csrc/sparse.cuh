@@ -1,37 +1,76 @@
-// sparse.cuh - block-sparse pull of one voxel, shared by the sparse kernels
-// and the batched persistent step (internal).
+// sparse.cuh - block-sparse pull of one voxel, shared by the sparse kernels,
+// the multi-resolution uniform blocks and the batched persistent step
+// (internal).
 #pragma once
 #include "d3q19.cuh"
 
 namespace lbm {
 
 // Pull the 19 populations of voxel l of block b (block edge E) with halfway
-// bounce-back.  nbr27: the block's 27 neighbour ids (-1 = none), usually in
-// shared memory; walls: the block or its halo holds a wall voxel, so source
-// flags are read; flags: per-slot flag bytes.
+// bounce-back.  nbr27: the block's 27 neighbour ids, entry (dx+1) + 3 (dy+1)
+// + 9 (dz+1), entry 13 = b itself, -1 = none; usually in shared memory.
+// walls: the block or one of its 26 neighbours holds a wall voxel, or a
+// neighbour is missing, so sources are checked against their flags; a block
+// without it pulls with no test at all.  flags: per-slot flag bytes.
+//
+// Address arithmetic is hoisted out of the 19 pulls: a voxel can only leave
+// its block across the faces it lies on, so the (at most) six blocks a pull
+// can enter — one per face and one per edge between two of them; D3Q19 has
+// no corner velocities — are looked up once, and the source coordinate
+// wrapped into the source block is one of three precomputed values per axis.
+// Each pull then costs a few selects and one 32 x 32 -> 64-bit multiply-add.
+template <int S, int E, bool WALLS>
+__device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* __restrict__ fin,
+                                                    const int32_t* nbr27,
+                                                    const uint8_t* __restrict__ flags, int b,
+                                                    int l, float g[Q]) {
+  using T = typename Codec<S>::T;
+  constexpr int E3 = E * E * E, M = E - 1;
+  const int lx = l & M, ly = (l / E) & M, lz = l / (E * E);
+  const int ex = lx == 0 ? -1 : (lx == M ? 1 : 0);
+  const int ey = ly == 0 ? -1 : (ly == M ? 1 : 0);
+  const int ez = lz == 0 ? -1 : (lz == M ? 1 : 0);
+  const int nX = nbr27[13 + ex], nY = nbr27[13 + 3 * ey], nZ = nbr27[13 + 9 * ez];
+  const int nXY = nbr27[13 + ex + 3 * ey], nXZ = nbr27[13 + ex + 9 * ez];
+  const int nYZ = nbr27[13 + 3 * ey + 9 * ez];
+  // source coordinate inside its block for c = +1, -1 (pre-scaled by the
+  // axis stride for y and z)
+  const int xp = (lx - 1) & M, xn = (lx + 1) & M;
+  const int yp = ((ly - 1) & M) * E, yn = ((ly + 1) & M) * E, y0 = ly * E;
+  const int zp = ((lz - 1) & M) * E * E, zn = ((lz + 1) & M) * E * E, z0 = lz * E * E;
+  const T* __restrict__ self = fin + (int64_t)b * (Q * E3) + l;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+    const bool kx = X != 0 && ex == -X;  // the pull crosses the x face
+    const bool ky = Y != 0 && ey == -Y;
+    const bool kz = Z != 0 && ez == -Z;
+    int nb = b;
+    if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : b);
+    else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : b);
+    else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : b);
+    else if constexpr (X != 0) nb = kx ? nX : b;
+    else if constexpr (Y != 0) nb = ky ? nY : b;
+    else if constexpr (Z != 0) nb = kz ? nZ : b;
+    const int ls = (X > 0 ? xp : (X < 0 ? xn : lx)) + (Y > 0 ? yp : (Y < 0 ? yn : y0)) +
+                   (Z > 0 ? zp : (Z < 0 ? zn : z0));
+    if constexpr (!WALLS) {
+      g[I] = Codec<S>::template load<I>(fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)]);
+    } else {
+      bool wall = nb < 0;
+      if (!wall) wall = type_wall(flag_type(flags[(int64_t)nb * E3 + ls]));
+      g[I] = Codec<S>::template load<I>(wall ? self[opp(I) * E3]
+                                             : fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)]);
+    }
+  });
+}
+
 template <int S, int E>
 __device__ __forceinline__ void sparse_pull_voxel(const typename Codec<S>::T* __restrict__ fin,
                                                   const int32_t* nbr27, const uint8_t* flags,
                                                   int64_t b, int l, bool walls, float g[Q]) {
-  constexpr int E3 = E * E * E;
-  const int lx = l % E, ly = (l / E) % E, lz = l / (E * E);
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
-    const int dx = sx < 0 ? -1 : (sx >= E ? 1 : 0);
-    const int dy = sy < 0 ? -1 : (sy >= E ? 1 : 0);
-    const int dz = sz < 0 ? -1 : (sz >= E ? 1 : 0);
-    int64_t nb = b;
-    if (dx | dy | dz) nb = nbr27[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
-    sx -= dx * E;
-    sy -= dy * E;
-    sz -= dz * E;
-    const int ls = sx + E * (sy + E * sz);
-    bool wall = nb < 0;
-    if (walls && !wall) wall = type_wall(flag_type(flags[nb * E3 + ls]));
-    const int64_t src = wall ? (b * Q + opp(I)) * E3 + l : (nb * Q + I) * E3 + ls;
-    g[I] = Codec<S>::template load<I>(fin[src]);
-  });
+  if (walls) sparse_pull_voxel_t<S, E, true>(fin, nbr27, flags, (int)b, l, g);
+  else sparse_pull_voxel_t<S, E, false>(fin, nbr27, flags, (int)b, l, g);
 }
 
 }  // namespace lbm

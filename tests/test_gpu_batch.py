@@ -101,3 +101,69 @@ def test_full_serving_batch_conserves_mass(lbm):
     lbm.lbm_batch_step(b, 10)
     m1 = np.array([lbm.lbm_conservation(g)[0] for g in grids])
     assert np.max(np.abs(m1 / m0 - 1)) <= 1e-5
+
+
+def test_batch_closure_matches_oracle(lbm):
+    """Closure on the cases whose largest edge is <= 24 (one dense, one
+    sparse), the other two plain, in one batch; each case against the FP64
+    oracle after 6 steps.  Closure cases: the oracle's closure step on the
+    BF16-rounded network, tolerance the FP32 bar plus the oracle's response to
+    a 2e-2 relative change of d_tau (the BF16 network's bound); plain cases:
+    the FP32 bar."""
+    from test_gpu_closure import he_init, storage_weights
+    from oracle import closure as ocl
+    from oracle import lbm as olbm
+    cases = wl.batch_cases(n_cases=4, seed=38, lmin=16, lmax=32, max_solid=0.15)
+    on = [max(c["dims"]) <= 24 for c in cases]
+    assert on == [True, False, False, True]
+    steps = 6
+    grids, fields = [], []
+    for k, c in enumerate(cases):
+        nx, ny, nz = c["dims"]
+        rho, u = wl.random_fields((nz, ny, nx), seed=130 + k, u_amp=0.02)
+        phys = lbm.physics(c["tau"], periodic=(1, 1, 1))
+        if c["kind"] == "dense":
+            g = lbm.lbm_grid_create_dense(c["dims"], phys)
+            lbm.lbm_set_boundary(g, 0, c["flags"])
+        else:
+            g = lbm.lbm_grid_create_sparse(c["dims"], 8, c["flags"], phys)
+        lbm.lbm_init_equilibrium(g, 0, rho, u)
+        grids.append(g)
+        fields.append((rho, u))
+    # network on the scale of this state's features, d_tau ~ 1e-2
+    f0 = olbm.init_equilibrium(*fields[0], cases[0]["flags"])
+    X = ocl.features(olbm.stream_with_walls(f0, cases[0]["flags"], (True,) * 3)[
+        :, (cases[0]["flags"] & 7) == 0], cases[0]["tau"])
+    sd = X.std(axis=0)
+    sd[sd < 1e-9] = 1.0
+    theta = he_init(131, scale_out=0.05)
+    theta[:1024] = (theta[:1024].reshape(64, 16) / sd).ravel()
+    theta = theta.astype(np.float32)
+    th = storage_weights(theta)
+    th_eps = th.copy()
+    th_eps[5248:] *= 1 + 2e-2
+    b = lbm.lbm_batch_create(grids)
+    lbm.lbm_batch_closure_load(b, theta, 24)
+    lbm.lbm_batch_step(b, steps)
+    per = (True, True, True)
+    for c, g, (rho, u), cl_on in zip(cases, grids, fields, on):
+        f0 = olbm.init_equilibrium(rho, u, c["flags"])
+        got = lbm.lbm_get_populations_f64(g, 0)
+        if cl_on:
+            ref = ocl.run(f0, c["flags"], c["tau"], th, steps, periodic=per)
+            ref_eps = ocl.run(f0, c["flags"], c["tau"], th_eps, steps, periodic=per)
+            plain = olbm.run(f0, c["flags"], c["tau"], steps, periodic=per)
+            tol = F32_RTOL + max_rel_err(ref_eps, ref, c["flags"])
+            effect = max_rel_err(plain, ref, c["flags"])
+            err = max_rel_err(got, ref, c["flags"])
+            print(f"{c['kind']} closure case: effect {effect:.3e}, GPU vs oracle {err:.3e}, "
+                  f"tolerance {tol:.3e}")
+            assert effect > 10 * tol
+            assert err <= tol
+        else:
+            ref = olbm.run(f0, c["flags"], c["tau"], steps, periodic=per)
+            assert max_rel_err(got, ref, c["flags"]) <= F32_RTOL
+    # switching the closure off restores the plain kernel
+    lbm.lbm_batch_closure_load(b, None, 0)
+    assert lbm.lbm_batch_info(b)["n_items"] > 0
+    lbm.lbm_batch_step(b, 1)

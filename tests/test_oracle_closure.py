@@ -1,11 +1,14 @@
 """Pins of the learned-closure oracle (oracle/closure.py): the network's
 gradient against finite differences, a hand-built network, Adam's first step,
 the features on inputs whose moments are known, and the training target's
-invariances."""
+invariances; the single-grid closure step against plain steps it must
+reduce to."""
 import numpy as np
+import pytest
 
 from oracle import closure as cl
 from oracle import lattice as L
+from oracle import lbm as olbm
 from paper_2503_07898_gb300 import workloads as wl
 
 
@@ -134,3 +137,61 @@ def test_coarse_pulled_uniform_flow_is_stationary():
     f = L.equilibrium(rho, u)
     assert np.allclose(cl.coarse_pulled(f, 2), L.equilibrium(rho[:4, :4, :4], u[:, :4, :4, :4]),
                        atol=1e-15)
+
+
+# ------------------------------------------------- single-grid closure step
+
+def _obstacle_box(seed, shape=(10, 9, 12)):
+    flags = wl.random_obstacles(shape, seed=seed, solid_fraction=0.1)
+    rho, u = wl.random_fields(shape, seed=seed + 1)
+    return flags, olbm.init_equilibrium(rho, u, flags)
+
+
+def _const_net(b3):
+    return np.concatenate([np.zeros(cl.N_PARAMS - 1), [b3]])
+
+
+@pytest.mark.parametrize("b3", [0.0, 0.04, -0.05, -1.0])
+def test_closure_step_with_constant_network_is_plain_step(b3):
+    """Constant output b3: the plain oracle step at max(tau + b3, 1/2 + 1e-3),
+    walls, obstacles and periodic axes included."""
+    flags, f0 = _obstacle_box(200)
+    per = (True, False, True)
+    got = cl.run(f0, flags, 0.58, _const_net(b3), 3, periodic=per)
+    ref = olbm.run(f0, flags, max(0.58 + b3, 0.5 + 1e-3), 3, periodic=per)
+    assert np.max(np.abs(got - ref)) < 1e-15
+
+
+def test_closure_step_feeds_tau_and_pulled_moments():
+    """d_tau = relu(relu(feature 15)) = tau relaxes with 2 tau; a network
+    reading u_x (feature 1) gives tau_eff = tau + 2 relu(u_x) of the pulled
+    populations, checked voxel by voxel against a hand evaluation."""
+    flags, f0 = _obstacle_box(201)
+    p = cl.unpack(_const_net(0.0))
+    p["W1"][0, 15] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][0] = 1.0
+    got = cl.step(f0, flags, 0.6, cl.pack(p), periodic=(True, True, True))
+    ref = olbm.step(f0, flags, 1.2, periodic=(True, True, True))
+    assert np.max(np.abs(got - ref)) < 1e-15
+    p = cl.unpack(_const_net(0.0))
+    p["W1"][0, 1] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["W3"][0] = 2.0
+    got = cl.step(f0, flags, 0.6, cl.pack(p), periodic=(True, True, True))
+    g = olbm.stream_with_walls(f0, flags, (True, True, True))
+    fluid = olbm.flag_type(flags) == olbm.FLUID
+    for z, y, x in zip(*np.nonzero(fluid)):
+        gv = g[:, z, y, x]
+        ux = float(L.C[:, 0] @ gv) / gv.sum()
+        fv, _, _ = olbm.collide(gv, 0.6 + 2 * max(ux, 0.0))
+        assert np.max(np.abs(got[:, z, y, x] - fv)) < 1e-15
+
+
+def test_closure_step_conserves_mass_in_a_walled_box():
+    flags, f0 = _obstacle_box(202)
+    rng = np.random.default_rng(203)
+    th = rng.standard_normal(cl.N_PARAMS) * 0.05
+    f1 = cl.run(f0, flags, 0.6, th, 5, periodic=(False, False, False))
+    m0, m1 = f0.sum(), f1.sum()
+    assert abs(m1 - m0) / m0 < 1e-13
