@@ -152,7 +152,7 @@ def _time_steps(torch, lbm, step, stream, n):
     return e0.elapsed_time(e1)
 
 
-def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
+def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
     """GLUPS of the other layouts of the method on their full-size inputs
     (context lines of the same metric; each timed after 3 warm-up steps)."""
     out = {}
@@ -168,6 +168,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
         bcl = np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
         res = {}
         for name, kw in (("disaggregated_f32", dict(storage="f32")),
+                         ("disaggregated_bitmask_f32", dict(storage="f32", schedule="bitmask")),
                          ("monolithic_f32", dict(storage="f32", schedule="monolithic")),
                          ("disaggregated_f16", dict(storage="f16"))):
             g = lbm.lbm_grid_create_sparse(flags.shape[::-1], 8, flags,
@@ -207,7 +208,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
         res["updates_per_coarsest_step"] = ups
         out["turbulence_256_3level"] = res
     if "batch" in which:
-        cases = wl.batch_cases()
+        cases = wl.batch_cases(n_cases=n_batch)
         grids = []
         for c in cases:
             phys = lbm.physics(c["tau"], storage="f16", periodic=(1, 1, 1))
@@ -226,7 +227,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
         torch.cuda.synchronize()
         ms = _time_steps(torch, lbm, lambda n: lbm.lbm_batch_step(b, n, stream), stream, steps)
         glups = info["n_updated"] * steps / (ms * 1e-3) / 1e9
-        out["serving_batch_128_f16"] = {"GLUPS": round(glups, 3),
+        out[f"serving_batch_{n_batch}_f16"] = {"GLUPS": round(glups, 3),
                                         "roofline_frac": round(glups * 76 / peak, 4),
                                         "updated_voxels": info["n_updated"],
                                         "ctas_per_sm": k, "launches_per_step": 1}
@@ -238,13 +239,77 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which):
         torch.cuda.synchronize()
         ms = _time_steps(torch, lbm, lambda n: lbm.lbm_batch_step(b, n, stream), stream, steps)
         glups = info["n_updated"] * steps / (ms * 1e-3) / 1e9
-        out["serving_batch_128_f16_learned_closure"] = {
+        out[f"serving_batch_{n_batch}_f16_learned_closure"] = {
             "GLUPS": round(glups, 3), "roofline_frac": round(glups * 76 / peak, 4),
             "closure_cases": n_cl, "max_edge": 64, "ctas_per_sm": k, "launches_per_step": 1}
         del b
         for g in grids:
             lbm.lbm_grid_destroy(g)
     return out
+
+
+def closure_quality(torch, lbm, wl, N=64, r=4, tau_f=0.504, T=192, kmax=16, urms=0.03):
+    """Error of the learned closure, through the library's own dataset and
+    training kernels: fine N^3 decaying turbulence at tau_f (two seeds,
+    snapshots every 16 steps) gives the training set of a level r times
+    coarser; the trained network then runs on that coarse level of a 3-level
+    grid (tau_2 = 1/2 + (tau_f - 1/2) / r) started from the box-filtered fine
+    field of a third seed.  Reported: velocity L2 against the box-filtered
+    fine run after T fine steps, with and without the closure."""
+    def box(a):
+        *lead, nz, ny, nx = a.shape
+        return a.reshape(*lead, nz // r, r, ny // r, r, nx // r, r).mean(axis=(-5, -3, -1))
+
+    tau_c = 0.5 + (tau_f - 0.5) / r
+    nc = (N // r) ** 3
+    feats, targs = [], []
+    t0 = time.time()
+    for seed in (11, 12):
+        rho, u = wl.turbulence(N, seed=seed, u_rms=urms, kmax=kmax)
+        g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau_f, periodic=(1, 1, 1)))
+        lbm.lbm_init_equilibrium(g, 0, rho, u)
+        for _ in range(T // 16):
+            lbm.lbm_step(g, 16)
+            F = torch.empty((nc, 16), dtype=torch.float32, device="cuda")
+            Y = torch.empty(nc, dtype=torch.float32, device="cuda")
+            lbm.lbm_closure_dataset(g, r, tau_c, F, Y)
+            feats.append(F)
+            targs.append(Y)
+        lbm.lbm_grid_destroy(g)
+    X = torch.cat(feats).contiguous()
+    Y = torch.cat(targs).contiguous()
+    rng = np.random.default_rng(0)
+    th0 = np.concatenate([rng.standard_normal(64 * 16) * np.sqrt(2 / 16), np.zeros(64),
+                          rng.standard_normal(64 * 64) * np.sqrt(2 / 64), np.zeros(64),
+                          rng.standard_normal(64) * np.sqrt(1 / 64), np.zeros(1)])
+    th = torch.from_numpy(th0.astype(np.float32)).cuda()
+    loss = lbm.lbm_closure_train(X, Y, 4000, 4096, 1e-3, 1, th)
+    theta = th.cpu().numpy()
+    rho0, u0 = wl.turbulence(N, seed=23, u_rms=urms, kmax=kmax)
+    g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau_f, periodic=(1, 1, 1)))
+    lbm.lbm_init_equilibrium(g, 0, rho0, u0)
+    lbm.lbm_step(g, T)
+    _, uf = lbm.lbm_get_moments(g, 0)
+    lbm.lbm_grid_destroy(g)
+    ub = box(uf)
+    lmap = np.full((N // 32,) * 3, 2, np.uint8)
+    errs = {}
+    for closure in (0, 1):
+        gc = lbm.lbm_grid_create_multires((N,) * 3, 3, lmap,
+                                          lbm.physics(tau_f, periodic=(1, 1, 1), closure=closure))
+        if closure:
+            lbm.lbm_closure_load(gc, theta)
+        lbm.lbm_init_equilibrium(gc, 2, box(rho0), box(u0))
+        lbm.lbm_step(gc, T // r)
+        _, uc = lbm.lbm_get_moments(gc, 2)
+        lbm.lbm_grid_destroy(gc)
+        errs[closure] = float(np.sqrt(((uc - ub) ** 2).sum() / (ub ** 2).sum()))
+    return {"case": f"decaying turbulence, fine {N}^3 tau {tau_f} u_rms {urms} vs the level "
+                    f"{r}x coarser (tau {tau_c}) after {T} fine steps",
+            "training_samples": int(Y.numel()), "final_loss": float(f"{loss:.4e}"),
+            "velocity_l2_plain": round(errs[0], 5), "velocity_l2_closure": round(errs[1], 5),
+            "gain_pct": round(100 * (1 - errs[1] / errs[0]), 2),
+            "seconds": round(time.time() - t0, 1)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -321,6 +386,23 @@ def run_ours(args, rank, world, local_rank):
     # schedule / storage variants on the same workload (context lines)
     variants = {}
     if not args.no_variants:
+        # velocity error of each variant against an FP32 disaggregated run of
+        # the same steps (FP32 itself matches the FP64 oracle to 1e-5 in the
+        # parity tests): L2 = sqrt(sum |u - u_f32|^2 / sum |u_f32|^2) over the
+        # updated voxels, computed on the device
+        kv = min(args.steps, 200)
+        gr = lbm.lbm_grid_create_dense(dims, lbm.physics(tau), stream=stream)
+        lbm.lbm_set_boundary(gr, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
+        lbm.lbm_init_equilibrium(gr, 0, None, None)
+        lbm.lbm_step(gr, 20 + kv, stream)
+        torch.cuda.synchronize()
+        rho_d = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+        u_ref = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+        u_var = torch.empty_like(u_ref)
+        lbm.lbm_get_moments(gr, 0, rho_d, u_ref)
+        lbm.lbm_grid_destroy(gr)
+        upd = torch.from_numpy(((flags & 7) == 0) | ((flags & 7) == 2)).cuda()
+        u_den = float((u_ref[:, upd] ** 2).sum())
         for name, kw in (("monolithic_f32", dict(storage="f32", schedule="monolithic")),
                          ("disaggregated_f16", dict(storage="f16", schedule="disaggregated")),
                          ("disaggregated_bf16", dict(storage="bf16", schedule="disaggregated"))):
@@ -332,7 +414,6 @@ def run_ours(args, rank, world, local_rank):
             lbm.lbm_autotune(gv, 20)
             lbm.lbm_step(gv, 20, stream)
             torch.cuda.synchronize()
-            kv = min(args.steps, 200)
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
@@ -340,17 +421,24 @@ def run_ours(args, rank, world, local_rank):
             a1.record(stream)
             a1.synchronize()
             vms = a0.elapsed_time(a1)
+            lbm.lbm_get_moments(gv, 0, rho_d, u_var)
+            l2 = (float(((u_var - u_ref)[:, upd] ** 2).sum()) / u_den) ** 0.5
             variants[name] = {"GLUPS": round(n_upd * kv / (vms * 1e-3) / 1e9, 3),
                               "roofline_frac": round(n_upd * kv * BYTES_PER_UPDATE[kw["storage"]]
-                                                     / (vms * 1e-3) / 1e9 / peak, 4)}
+                                                     / (vms * 1e-3) / 1e9 / peak, 4),
+                              "velocity_l2_vs_f32": float(f"{l2:.3e}"),
+                              "after_steps": 20 + kv}
             lbm.lbm_grid_destroy(gv)
+        del rho_d, u_ref, u_var
 
     workloads = {}
     if args.workloads != "none" and rank == 0:
-        which = ("sparse", "multires", "batch") if args.workloads == "all" else tuple(
+        which = ("sparse", "multires", "batch", "closure") if args.workloads == "all" else tuple(
             args.workloads.split(","))
         workloads = measure_workloads(torch, lbm, wl, stream, peaks()[0], min(args.steps, 100),
-                                      which)
+                                      which, args.batch_cases)
+        if "closure" in which:
+            workloads["learned_closure_quality"] = closure_quality(torch, lbm, wl)
 
     # end to end through the C ABI with pinned host buffers: init from host
     # (rho, u), K steps, moments back to host
@@ -430,8 +518,10 @@ def main():
     ap.add_argument("--variant", default="auto", choices=["auto", "vec16", "scalar", "vec8"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-cases", type=int, default=128,
+                    help="cases of the serving-batch workload (its first n of the 128)")
     ap.add_argument("--workloads", default="all",
-                    help="all | none | comma list of sparse,multires,batch")
+                    help="all | none | comma list of sparse,multires,batch,closure")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

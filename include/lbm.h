@@ -63,11 +63,20 @@ typedef enum {
 enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_REG = 1 };
 enum { LBM_STORAGE_F32 = 0, LBM_STORAGE_F16 = 1, LBM_STORAGE_BF16 = 2 };
 /* Kernel schedule.  DISAGGREGATED: one lean kernel per voxel group (the
- * paper's design).  MONOLITHIC: one kernel with per-voxel branches over every
+ * paper's design; on block-sparse grids its memory-based grouping, Sec. 4:
+ * boundary blocks stored first, then the rest, each kernel over its own
+ * contiguous range).  MONOLITHIC: one kernel with per-voxel branches over every
  * voxel (the paper's "naive" kernel, Sec. 4 and Table 2); for multi-resolution
  * grids it selects the unfused collide / stream pair on every block (the
- * baseline of Sec. 6.3). */
-enum { LBM_SCHEDULE_DISAGGREGATED = 0, LBM_SCHEDULE_MONOLITHIC = 1 };
+ * baseline of Sec. 6.3).  BITMASK (block-sparse grids only, chosen at
+ * creation): the bitmask-based grouping of Sec. 4 and Table 2 — every block
+ * in Morton order whatever its group, a per-block bit marks the boundary
+ * blocks, both group kernels run over all blocks and skip the other group's,
+ * and boundary values are reached through a per-slot index into a compact
+ * buffer (indirect indexing).  A grid created with BITMASK may switch only
+ * to MONOLITHIC and back; a grid created otherwise cannot switch to BITMASK
+ * (LBM_ERR_UNSUPPORTED): the block order is fixed at creation. */
+enum { LBM_SCHEDULE_DISAGGREGATED = 0, LBM_SCHEDULE_MONOLITHIC = 1, LBM_SCHEDULE_BITMASK = 2 };
 
 typedef struct {
   double tau;        /* BGK relaxation time of the finest level, > 0.5        */
@@ -182,7 +191,9 @@ lbm_status lbm_init_equilibrium(lbm_grid* g, int level, const double* rho,
                                 const double* u, int device_ptrs);
 
 /* Advance n_steps time steps (coarsest steps on a multi-resolution grid) on
- * `stream`.  Asynchronous; device errors are latched. */
+ * `stream`.  Asynchronous; device errors are latched.  LBM_ERR_INVALID when
+ * the grid has regularized voxels whose boundary values were never given
+ * (lbm_set_boundary). */
 lbm_status lbm_step(lbm_grid* g, int n_steps, void* stream);
 
 /* Density and velocity of the stored state in FP64, virtual-box order, NaN on
@@ -209,7 +220,12 @@ enum {
   LBM_LAYOUT_NBR = 2,          /* int32  n_blocks x 27, -1 = none              */
   LBM_LAYOUT_BLOCK_MAP = 3,    /* int32  virtual block grid -> block id or -1  */
   LBM_LAYOUT_XNBR_COARSE = 4,  /* int32  n_blocks x 27 (multi-res)             */
-  LBM_LAYOUT_XNBR_FINE = 5     /* int32  n_blocks x 27 x 8 (multi-res)         */
+  LBM_LAYOUT_XNBR_FINE = 5,    /* int32  n_blocks x 27 x 8 (multi-res)         */
+  LBM_LAYOUT_BOUNDARY_BITS = 6,/* uint32 ceil(n_blocks / 32): bit b % 32 of word
+                                  b / 32 = block b is a boundary block (BITMASK) */
+  LBM_LAYOUT_BC_INDEX = 7      /* int32  n_blocks x E^3: rank of the slot's
+                                  regularized voxel in flag-scan order, or -1
+                                  (BITMASK)                                     */
 };
 /* Copy one host-side layout table (for bit-exact checks).  bytes must equal
  * the table's size; lbm_layout_bytes reports it. */

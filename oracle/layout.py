@@ -12,6 +12,11 @@ boundary / non-boundary block split, but gives no ordering):
 * numbering (memory-based grouping, Sec. 4): boundary blocks first, then
   non-boundary blocks; inside each group ascending Morton code of the block
   coordinate with x in the lowest bit (bit 3k = x_k, 3k+1 = y_k, 3k+2 = z_k);
+* numbering (bitmask-based grouping, Sec. 4): every block in ascending
+  Morton code, whatever its group; a per-block bit marks the boundary blocks
+  (bit b % 32 of 32-bit word b // 32), and the boundary values are reached
+  through a per-slot index (-1 or the rank of the regularized voxel in
+  flag-scan order, x fastest) into a compact buffer;
 * nbr[b][k], k = (dx+1) + 3(dy+1) + 9(dz+1), is the id of the block at
   (bx+dx, by+dy, bz+dz) (wrapped on periodic axes) or -1.
 
@@ -34,11 +39,13 @@ def morton_code(bx, by, bz, bits=10):
     return code
 
 
-def block_tables(flags, block_edge=8, periodic=(False, False, False)):
-    """Return dict(coords (n,3) int32, n_boundary, nbr (n,27) int32, map dict).
+def block_tables(flags, block_edge=8, periodic=(False, False, False), grouping="memory"):
+    """Return dict(coords (n,3) int32, n_boundary, nbr (n,27) int32, ...).
 
     ``flags`` has shape (nz, ny, nx); the box is padded with type 7 (not in
-    domain) up to a whole number of blocks.
+    domain) up to a whole number of blocks.  grouping "memory" or "bitmask";
+    the latter also returns boundary_bits (uint32 words) and bc_index (int32
+    per slot, slot = b * B^3 + lx + B (ly + B lz)).
     """
     nz, ny, nx = flags.shape
     B = block_edge
@@ -53,7 +60,12 @@ def block_tables(flags, block_edge=8, periodic=(False, False, False)):
                     is_b = bool(np.isin(t, REGULARIZED_TYPES).any())
                     active.append((bx, by, bz))
                     boundary.append(is_b)
-    keys = [(0 if isb else 1, morton_code(*c)) for c, isb in zip(active, boundary)]
+    if grouping == "memory":
+        keys = [(0 if isb else 1, morton_code(*c)) for c, isb in zip(active, boundary)]
+    elif grouping == "bitmask":
+        keys = [morton_code(*c) for c in active]
+    else:
+        raise ValueError(grouping)
     order = sorted(range(len(active)), key=lambda i: keys[i])
     coords = np.array([active[i] for i in order], dtype=np.int32).reshape(-1, 3)
     n_boundary = int(sum(boundary))
@@ -75,8 +87,25 @@ def block_tables(flags, block_edge=8, periodic=(False, False, False)):
                                 ok = False
                     if ok:
                         nbr[b, k] = index.get(tuple(q), -1)
-    return {"coords": coords, "n_boundary": n_boundary, "nbr": nbr,
-            "dims_blocks": dims_b}
+    out = {"coords": coords, "n_boundary": n_boundary, "nbr": nbr, "dims_blocks": dims_b}
+    if grouping == "bitmask":
+        is_b = [boundary[i] for i in order]
+        words = np.zeros((len(coords) + 31) // 32, dtype=np.uint32)
+        for b, v in enumerate(is_b):
+            if v:
+                words[b // 32] |= np.uint32(1 << (b % 32))
+        bc_index = np.full(len(coords) * B ** 3, -1, dtype=np.int32)
+        rank = 0
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    if types[z, y, x] in REGULARIZED_TYPES:
+                        b = index[(x // B, y // B, z // B)]
+                        bc_index[b * B ** 3 + (x % B) + B * ((y % B) + B * (z % B))] = rank
+                        rank += 1
+        out["boundary_bits"] = words
+        out["bc_index"] = bc_index
+    return out
 
 
 def multires_tables(level_map, n_levels, cell, block_edge=8):

@@ -25,6 +25,8 @@ LBM_STORAGE_F32, LBM_STORAGE_F16, LBM_STORAGE_BF16 = 0, 1, 2
 LBM_SCHEDULE_DISAGGREGATED, LBM_SCHEDULE_MONOLITHIC = 0, 1
 LBM_LAYOUT_FLAGS, LBM_LAYOUT_BLOCK_COORDS, LBM_LAYOUT_NBR = 0, 1, 2
 LBM_LAYOUT_BLOCK_MAP, LBM_LAYOUT_XNBR_COARSE, LBM_LAYOUT_XNBR_FINE = 3, 4, 5
+LBM_LAYOUT_BOUNDARY_BITS, LBM_LAYOUT_BC_INDEX = 6, 7
+SCHEDULES = {"disaggregated": 0, "monolithic": 1, "bitmask": 2}
 
 
 class lbm_physics(C.Structure):
@@ -188,8 +190,7 @@ def physics(tau, collision="bgk", storage="f32", periodic=(0, 0, 0), schedule="d
     p.closure = int(closure)
     for a in range(3):
         p.periodic[a] = int(bool(periodic[a]))
-    p.schedule = ({"disaggregated": 0, "monolithic": 1}[schedule] if isinstance(schedule, str)
-                  else int(schedule))
+    p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     return p
 
 
@@ -275,7 +276,7 @@ def lbm_get_info(grid):
 
 
 def lbm_set_schedule(grid, schedule):
-    s = {"disaggregated": 0, "monolithic": 1}[schedule] if isinstance(schedule, str) else schedule
+    s = SCHEDULES[schedule] if isinstance(schedule, str) else schedule
     _check(load().lbm_set_schedule(grid.ptr, int(s)), "lbm_set_schedule")
 
 
@@ -368,7 +369,8 @@ def lbm_get_layout(grid, level, what):
     n = C.c_size_t()
     lib = load()
     _check(lib.lbm_layout_bytes(grid.ptr, int(level), int(what), C.byref(n)), "lbm_layout_bytes")
-    dtype = np.uint8 if what == LBM_LAYOUT_FLAGS else np.int32
+    dtype = (np.uint8 if what == LBM_LAYOUT_FLAGS
+             else np.uint32 if what == LBM_LAYOUT_BOUNDARY_BITS else np.int32)
     out = np.empty(n.value // np.dtype(dtype).itemsize, dtype)
     _check(lib.lbm_get_layout(grid.ptr, int(level), int(what), C.c_void_p(out.ctypes.data),
                               n.value), "lbm_get_layout")

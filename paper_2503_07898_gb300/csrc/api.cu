@@ -104,12 +104,25 @@ static void free_level(Grid& g, Level& L) {
   g.dfree(L.nbr_d, s);
   g.dfree(L.bmap_d, s);
   g.dfree(L.blk_walls_d, s);
+  g.dfree(L.bnd_bits_d, s);
+  g.dfree(L.bc_idx_d, s);
+  g.dfree(L.bc_cmp_d, s);
   L = Level();
 }
 
 static void free_grid(Grid& g) {
   cudaStreamSynchronize(g.stream);
   prof_clear(g);
+  for (int l = 0; l < 4; ++l) {
+    if (g.mr_aux[l]) {
+      cudaStreamSynchronize(g.mr_aux[l]);
+      cudaStreamDestroy(g.mr_aux[l]);
+    }
+    if (g.mr_fork[l]) cudaEventDestroy(g.mr_fork[l]);
+    if (g.mr_join[l]) cudaEventDestroy(g.mr_join[l]);
+    g.mr_aux[l] = nullptr;
+    g.mr_fork[l] = g.mr_join[l] = nullptr;
+  }
   for (int l = 0; l < 4; ++l) free_level(g, g.lv[l]);
   g.dfree(g.status_d, g.stream);
   g.dfree(g.partials_d, g.stream);
@@ -130,7 +143,8 @@ static lbm_status check_physics(const lbm_physics* p) {
     return fail(LBM_ERR_INVALID, "unknown collision");
   if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16)
     return fail(LBM_ERR_INVALID, "unknown storage");
-  if (p->schedule != LBM_SCHEDULE_DISAGGREGATED && p->schedule != LBM_SCHEDULE_MONOLITHIC)
+  if (p->schedule != LBM_SCHEDULE_DISAGGREGATED && p->schedule != LBM_SCHEDULE_MONOLITHIC &&
+      p->schedule != LBM_SCHEDULE_BITMASK)
     return fail(LBM_ERR_INVALID, "unknown schedule");
   if (p->closure != 0 && p->closure != 1) return fail(LBM_ERR_INVALID, "closure must be 0 or 1");
   return LBM_OK;
@@ -302,6 +316,8 @@ lbm_status lbm_grid_create_dense(const int dims[3], const lbm_physics* phys,
   if ((double)dims[0] * dims[1] * dims[2] * Q >= 9.0e18)
     return fail(LBM_ERR_INVALID, "grid too large");
   if (phys && phys->closure) return fail(LBM_ERR_UNSUPPORTED, "the closure runs on multi-resolution grids");
+  if (phys && phys->schedule == LBM_SCHEDULE_BITMASK)
+    return fail(LBM_ERR_UNSUPPORTED, "bitmask grouping is a block-sparse layout");
   Grid* gp = nullptr;
   lbm_status st = begin(out, phys, alloc, stream, gp);
   if (st) return st;
@@ -361,6 +377,8 @@ lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
                                     const lbm_allocator* alloc, void* stream, lbm_grid** out) {
   set_error("");
   if (!finest_dims || !level_map) return fail(LBM_ERR_INVALID, "NULL argument");
+  if (phys && phys->schedule == LBM_SCHEDULE_BITMASK)
+    return fail(LBM_ERR_UNSUPPORTED, "bitmask grouping is a block-sparse layout");
   Grid* gp = nullptr;
   lbm_status st = begin(out, phys, alloc, stream, gp);
   if (st) return st;
@@ -431,8 +449,14 @@ lbm_status lbm_get_info(const lbm_grid* h, lbm_info* out) {
 
 lbm_status lbm_set_schedule(lbm_grid* h, int schedule) {
   if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
-  if (schedule != LBM_SCHEDULE_DISAGGREGATED && schedule != LBM_SCHEDULE_MONOLITHIC)
+  if (schedule != LBM_SCHEDULE_DISAGGREGATED && schedule != LBM_SCHEDULE_MONOLITHIC &&
+      schedule != LBM_SCHEDULE_BITMASK)
     return fail(LBM_ERR_INVALID, "unknown schedule");
+  // the block order is fixed at creation: a bitmask-grouped grid has no
+  // contiguous boundary group, a memory-grouped one no boundary bits
+  const bool bm = h->g.kind == 1 && h->g.lv[0].bitmask;
+  if ((schedule == LBM_SCHEDULE_BITMASK && !bm) || (schedule == LBM_SCHEDULE_DISAGGREGATED && bm))
+    return fail(LBM_ERR_UNSUPPORTED, "the grouping (block order) is chosen at grid creation");
   h->g.phys.schedule = schedule;
   return LBM_OK;
 }
@@ -557,6 +581,9 @@ lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
   if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
   if (n_steps < 0) return fail(LBM_ERR_INVALID, "n_steps < 0");
   Grid& g = h->g;
+  for (int l = 0; l < g.n_levels; ++l)
+    if (g.lv[l].n_reg > 0 && g.lv[l].bc_h.size() != (size_t)g.lv[l].n_reg * 4)
+      return fail(LBM_ERR_INVALID, "regularized voxels have no boundary values (lbm_set_boundary)");
   cudaStream_t s = stream ? (cudaStream_t)stream : g.stream;
   g.stream = s;
   if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
@@ -680,6 +707,14 @@ lbm_status lbm_layout_bytes(const lbm_grid* h, int level, int what, size_t* byte
       if (g.kind != 2) break;
       *bytes = L.xnbr_fine_h.size() * 4;
       return LBM_OK;
+    case LBM_LAYOUT_BOUNDARY_BITS:
+      if (!L.bitmask) break;
+      *bytes = L.bnd_bits_h.size() * 4;
+      return LBM_OK;
+    case LBM_LAYOUT_BC_INDEX:
+      if (!L.bitmask) break;
+      *bytes = L.bc_idx_h.size() * 4;
+      return LBM_OK;
     default: break;
   }
   return fail(LBM_ERR_UNSUPPORTED, "layout table not available for this grid");
@@ -696,7 +731,9 @@ lbm_status lbm_get_layout(const lbm_grid* h, int level, int what, void* dst, siz
                     : what == LBM_LAYOUT_NBR ? (const void*)L.nbr_h.data()
                     : what == LBM_LAYOUT_BLOCK_MAP ? (const void*)L.bmap_h.data()
                     : what == LBM_LAYOUT_XNBR_COARSE ? (const void*)L.xnbr_coarse_h.data()
-                                                     : (const void*)L.xnbr_fine_h.data();
+                    : what == LBM_LAYOUT_XNBR_FINE ? (const void*)L.xnbr_fine_h.data()
+                    : what == LBM_LAYOUT_BOUNDARY_BITS ? (const void*)L.bnd_bits_h.data()
+                                                       : (const void*)L.bc_idx_h.data();
   if (need) std::memcpy(dst, src, need);
   return LBM_OK;
 }

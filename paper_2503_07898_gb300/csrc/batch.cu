@@ -8,6 +8,10 @@
 // step over the whole batch is a single launch whatever the number of cases.
 // A sequence of steps is captured once into a CUDA graph and replayed.  The
 // persistent grid size (CTAs per SM) is the tuning knob of lbm_batch_autotune.
+// Cases running the learned closure are listed after all the others and
+// stepped by a second persistent launch of the closure kernel variant, so
+// its larger register and shared-memory footprint costs the other cases
+// nothing.
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -24,7 +28,8 @@ struct BatchCase {
   int kind;  // 0 dense, 1 sparse (block edge 8)
   int nx, ny, nz, px, py, pz;
   int64_t N;                 // dense voxels / sparse slots
-  const uint32_t* wmask;     // dense wall mask (null: walls only at box sides)
+  const uint32_t* wmask;     // per-voxel (dense) or per-slot (sparse) wall mask; dense: null
+                             // when walls are only at box sides
   const uint8_t* flags;      // sparse slot flags
   const int32_t* nbr;        // sparse neighbour table
   const uint8_t* blk_walls;  // sparse per-block wall bit
@@ -44,7 +49,6 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
                                                         int64_t n_items, int parity,
                                                         const ClosureParams* __restrict__ cp) {
   using T = typename Codec<S>::T;
-  __shared__ int32_t snbr[27];
   extern __shared__ __align__(16) unsigned char batch_dyn_smem[];
   if constexpr (CLOSURE) {
     closure_load_smem(reinterpret_cast<ClosureCta*>(batch_dyn_smem)->w, cp);
@@ -95,13 +99,13 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
     } else {
       const int b = (int)(t >> 1);
       const int l = (int)(t & 1) * BT + threadIdx.x;
-      if (threadIdx.x < 27) snbr[threadIdx.x] = C.nbr[(int64_t)b * 27 + threadIdx.x];
-      __syncthreads();
       const bool walls = C.blk_walls[b] != 0;
-      act = !walls || type_updated(flag_type(C.flags[(int64_t)b * 512 + l]));
+      uint32_t wm = 0u;
+      if (walls) wm = C.wmask[(int64_t)b * 512 + l];
+      act = !(wm & WM_SKIP);
       obase = (int64_t)b * (Q * 512) + l;
       ostride = 512;
-      if (act) sparse_pull_voxel<S, 8>(fin, snbr, C.flags, b, l, walls, g);
+      if (act) sparse_pull_voxel<S, 8>(fin, C.nbr + (int64_t)b * 27, wm, b, l, walls, g);
     }
     float omega = C.omega;
     if constexpr (CLOSURE) {
@@ -124,7 +128,6 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
         fout[obase + I * ostride] = Codec<S>::template store<I>(g[I]);
       });
     }
-    __syncthreads();  // the neighbour list and the staging tiles are reused
   }
 }
 
@@ -164,6 +167,8 @@ struct lbm_batch {
   int32_t* item_case_d = nullptr;
   int32_t* item_local_d = nullptr;
   int64_t n_items = 0;
+  int64_t n_plain = 0;                        // items of cases without the closure (listed first)
+  std::vector<int32_t> items_per_case;
   int64_t n_updated = 0;
   int storage = 0, collision = 0;
   int n_sm = 1;
@@ -172,9 +177,17 @@ struct lbm_batch {
   bool closure = false;                       // some case runs the closure
   cudaStream_t cap = nullptr;                 // capture stream (non-blocking)
   std::map<int, cudaGraphExec_t> graphs;      // steps -> instantiated graph
-  StepFn fn = nullptr;
+  StepFn fn = nullptr;      // plain kernel
+  StepFn fn_cl = nullptr;   // closure kernel (items n_plain .. n_items)
 
   int grid_size() const { return n_sm * ctas_per_sm; }
+  // one step: plain items, then the closure items (if any)
+  void launch(int grid, int parity, cudaStream_t s) const {
+    if (n_plain > 0) fn(cases_d, item_case_d, item_local_d, n_plain, grid, parity, cp_d, s);
+    if (n_items > n_plain)
+      fn_cl(cases_d, item_case_d + n_plain, item_local_d + n_plain, n_items - n_plain, grid,
+            parity, cp_d, s);
+  }
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
@@ -272,11 +285,14 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
       ic.push_back(c);
       il.push_back((int32_t)t);
     }
+    b->items_per_case.push_back((int32_t)items);
     b->n_updated += L.n_updated;
     b->grids.push_back(h);
   }
   b->n_items = (int64_t)ic.size();
+  b->n_plain = b->n_items;
   b->fn = step_fn(b->storage, b->collision, false);
+  b->fn_cl = step_fn(b->storage, b->collision, true);
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -326,16 +342,28 @@ lbm_status lbm_batch_closure_load(lbm_batch* b, const float* theta, size_t n, in
     if (!b->cp_d) LBM_CUDA(cudaMalloc(&b->cp_d, sizeof(ClosureParams)));
     LBM_CUDA(cudaMemcpyAsync(b->cp_d, &cp, sizeof(cp), cudaMemcpyHostToDevice, s));
   }
-  bool any = false;
-  for (auto& d : b->cases_h) {
-    d.closure = max_edge > 0 && std::max(d.nx, std::max(d.ny, d.nz)) <= max_edge;
-    any = any || d.closure;
-  }
+  // the work list: items of plain cases first, then those of closure cases
+  std::vector<int32_t> ic, il;
+  for (int pass = 0; pass < 2; ++pass)
+    for (size_t c = 0; c < b->cases_h.size(); ++c) {
+      BatchCase& d = b->cases_h[c];
+      d.closure = max_edge > 0 && std::max(d.nx, std::max(d.ny, d.nz)) <= max_edge;
+      if (d.closure != pass) continue;
+      for (int32_t t = 0; t < b->items_per_case[c]; ++t) {
+        ic.push_back((int32_t)c);
+        il.push_back(t);
+      }
+    }
+  if (ic.size() != (size_t)b->n_items) return fail(LBM_ERR_INTERNAL, "batch work list size");
+  int64_t n_plain = 0;
+  while (n_plain < b->n_items && !b->cases_h[(size_t)ic[(size_t)n_plain]].closure) ++n_plain;
   LBM_CUDA(cudaMemcpyAsync(b->cases_d, b->cases_h.data(), b->cases_h.size() * sizeof(BatchCase),
                            cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaMemcpyAsync(b->item_case_d, ic.data(), ic.size() * 4, cudaMemcpyHostToDevice, s));
+  LBM_CUDA(cudaMemcpyAsync(b->item_local_d, il.data(), il.size() * 4, cudaMemcpyHostToDevice, s));
   LBM_CUDA(cudaStreamSynchronize(s));
-  b->closure = any;
-  b->fn = step_fn(b->storage, b->collision, any);
+  b->n_plain = n_plain;
+  b->closure = n_plain < b->n_items;
   b->drop_graphs();
   return LBM_OK;
 }
@@ -353,8 +381,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int n_steps, void* stream) {
     cudaGraphExec_t exec = nullptr;
     LBM_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < n_steps; ++k)
-      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, b->grid_size(), k & 1,
-            b->cp_d, b->cap);
+      b->launch(b->grid_size(), k & 1, b->cap);
     cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
@@ -390,11 +417,11 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int n_steps, int* chosen, double* ms
   int best_k = b->ctas_per_sm;
   for (int c = 0; c < 6; ++c) {
     const int grid = b->n_sm * cand[c];
-    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 0, b->cp_d, s);  // warm-up
-    b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, 1, b->cp_d, s);
+    b->launch(grid, 0, s);  // warm-up
+    b->launch(grid, 1, s);
     cudaEventRecord(e0, s);
     for (int k = 0; k < n_steps; ++k)
-      b->fn(b->cases_d, b->item_case_d, b->item_local_d, b->n_items, grid, k & 1, b->cp_d, s);
+      b->launch(grid, k & 1, s);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms = 0.f;

@@ -183,13 +183,26 @@ __device__ __forceinline__ void collide(float s[Q], float omega) {
   const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
   const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
   if constexpr (COLL == C_BGK) {
+    // The pair (i, opp(i)) = (i, i + 1) shares the even part of the shifted
+    // equilibrium: E = sym +- asym with sym = w (drho + rho (9/2 (c.u)^2 -
+    // 3/2 u.u)) and asym = 3 w rho c.u, c = c_i; w rho, w drho and 3 w rho
+    // are formed once per weight class.  e sums exactly the E values used,
+    // so the rest population closes the mass as in the unpaired form.
+    const float rf = rho * (1.f / 18.f), df = drho * (1.f / 18.f), af = rho * (3.f / 18.f);
+    const float rd = rho * (1.f / 36.f), dd = drho * (1.f / 36.f), ad = rho * (3.f / 36.f);
     float e = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const float E = eq_s(i, drho, rho, ux, uy, uz, usq15);
-      e += E;
-      s[i] = s[i] + omega * (E - s[i]);
-    }
+    static_for<(Q - 1) / 2>([&](auto pc) {
+      constexpr int i = 2 * decltype(pc)::value + 1, o = i + 1;
+      constexpr bool face = i < 7;
+      const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
+      const float t = 4.5f * cu * cu - usq15;
+      const float sym = face ? fmaf(rf, t, df) : fmaf(rd, t, dd);
+      const float asym = (face ? af : ad) * cu;
+      const float Ei = sym + asym, Eo = sym - asym;
+      e += Ei + Eo;
+      s[i] = s[i] + omega * (Ei - s[i]);
+      s[o] = s[o] + omega * (Eo - s[o]);
+    });
     s[0] = s[0] + omega * ((drho - e) - s[0]);
   } else {
     float pxx, pyy, pzz, pxy, pxz, pyz;

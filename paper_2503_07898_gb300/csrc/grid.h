@@ -32,7 +32,8 @@ struct Level {
   int E = 0;                  // block edge (0 = dense)
   int nbx = 0, nby = 0, nbz = 0;  // virtual block grid
   int64_t n_blocks = 0;       // active blocks (sparse)
-  int64_t n_b = 0;            // boundary blocks, stored first (sparse)
+  int64_t n_b = 0;            // boundary blocks, stored first (sparse, memory grouping)
+  bool bitmask = false;       // sparse: bitmask grouping (all blocks in Morton order)
   int64_t n_slots = 0;        // dense: voxels; sparse: n_blocks * E^3
   int64_t n_updated = 0;      // fluid + regularized voxels
   int64_t n_upd_b = 0;        // updated voxels inside boundary blocks (sparse)
@@ -57,6 +58,8 @@ struct Level {
   std::vector<int32_t> nbr_h;         // n_blocks x 27
   std::vector<int32_t> bmap_h;        // virtual block grid -> id
   std::vector<float> bc_h;            // 4 per regularized voxel, flag-scan order
+  std::vector<uint32_t> bnd_bits_h;   // bitmask grouping: bit b = block b is a boundary block
+  std::vector<int32_t> bc_idx_h;      // bitmask grouping: per slot, rank in bc_h or -1
 
   // device tables
   uint8_t* flags_d = nullptr;    // dense: N (null when all fluid); sparse: n_slots
@@ -67,6 +70,9 @@ struct Level {
   int32_t* nbr_d = nullptr;
   int32_t* bmap_d = nullptr;
   uint8_t* blk_walls_d = nullptr; // sparse: 1 if block or its halo has a wall voxel
+  uint32_t* bnd_bits_d = nullptr; // bitmask grouping: boundary block bits
+  int32_t* bc_idx_d = nullptr;    // bitmask grouping: per-slot index into bc_cmp_d
+  float4* bc_cmp_d = nullptr;     // bitmask grouping: BC values, one per regularized voxel
 
   int variant = VARIANT_SCALAR;   // kernel variant (VARIANT_*), set by lbm_set_variant / autotune
 
@@ -95,6 +101,12 @@ struct Grid {
   int n_partials = 0;
   double* sums_d = nullptr;      // 4 doubles
   int64_t steps_done = 0;
+
+  // multi-resolution: a second stream per level for the G_i launch, which
+  // overlaps the finer substeps and the G_c launch of its level
+  cudaStream_t mr_aux[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t mr_fork[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t mr_join[4] = {nullptr, nullptr, nullptr, nullptr};
 
   // learned closure (multi-resolution levels >= 1)
   void* closure_d = nullptr;     // ClosureParams on the device

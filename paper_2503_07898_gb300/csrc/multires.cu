@@ -269,39 +269,60 @@ template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
 __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;
   const int64_t b = a.b0 + blockIdx.x / 2;
-  __shared__ int32_t snbr[27];
   extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
   if (b >= a.b1) return;  // uniform per CTA
-  if (threadIdx.x < 27) snbr[threadIdx.x] = a.nbr[b * 27 + threadIdx.x];
-  if constexpr (CLOSURE) closure_load_smem(reinterpret_cast<ClosureCta*>(mr_dyn_smem)->w, a.cp);
-  __syncthreads();
+  if constexpr (CLOSURE) {
+    closure_load_smem(reinterpret_cast<ClosureCta*>(mr_dyn_smem)->w, a.cp);
+    __syncthreads();
+  }
+  const int32_t* __restrict__ nbr = a.nbr + b * 27;
   const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
   const int gx = a.coords[b * 3] * 8 + lx, gy = a.coords[b * 3 + 1] * 8 + ly,
             gz = a.coords[b * 3 + 2] * 8 + lz;
   const int jmp = a.jump[b];
   const T* __restrict__ cur = (const T*)a.cur;
+  // same-level pulls: the blocks a pull can enter are looked up once per
+  // voxel (as in the sparse pull); a missing one means another level
+  const int ex = lx == 0 ? -1 : (lx == 7 ? 1 : 0);
+  const int ey = ly == 0 ? -1 : (ly == 7 ? 1 : 0);
+  const int ez = lz == 0 ? -1 : (lz == 7 ? 1 : 0);
+  const int bb = (int)b;
+  const int nX = __ldg(nbr + 13 + ex), nY = __ldg(nbr + 13 + 3 * ey);
+  const int nZ = __ldg(nbr + 13 + 9 * ez);
+  const int nXY = __ldg(nbr + 13 + ex + 3 * ey), nXZ = __ldg(nbr + 13 + ex + 9 * ez);
+  const int nYZ = __ldg(nbr + 13 + 3 * ey + 9 * ez);
+  const int xp = (lx - 1) & 7, xn = (lx + 1) & 7;
+  const int yp = ((ly - 1) & 7) * 8, yn = ((ly + 1) & 7) * 8, y0 = ly * 8;
+  const int zp = ((lz - 1) & 7) * 64, zn = ((lz + 1) & 7) * 64, z0 = lz * 64;
   float g[Q];
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
-    int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
-    const int dx = sx < 0 ? -1 : (sx > 7 ? 1 : 0);
-    const int dy = sy < 0 ? -1 : (sy > 7 ? 1 : 0);
-    const int dz = sz < 0 ? -1 : (sz > 7 ? 1 : 0);
-    const int64_t nb = (dx | dy | dz) ? (int64_t)snbr[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] : b;
+    constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+    const bool kx = X != 0 && ex == -X;
+    const bool ky = Y != 0 && ey == -Y;
+    const bool kz = Z != 0 && ez == -Z;
+    int nb = bb;
+    if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : bb);
+    else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : bb);
+    else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : bb);
+    else if constexpr (X != 0) nb = kx ? nX : bb;
+    else if constexpr (Y != 0) nb = ky ? nY : bb;
+    else if constexpr (Z != 0) nb = kz ? nZ : bb;
     bool plain = nb >= 0;
-    if constexpr ((cx(I) != 0) + (cy(I) != 0) + (cz(I) != 0) == 2) {
+    if constexpr ((X != 0) + (Y != 0) + (Z != 0) == 2) {
       // a coarse voxel's subcells also trace through the two face neighbours
       // of a 2D-diagonal direction; all of them must be on this level
       if (plain && jmp == 1) {
-        if (dx && snbr[(dx + 1) + 3 + 9] < 0) plain = false;
-        if (dy && snbr[1 + 3 * (dy + 1) + 9] < 0) plain = false;
-        if (dz && snbr[1 + 3 + 9 * (dz + 1)] < 0) plain = false;
+        if (kx && nX < 0) plain = false;
+        if (ky && nY < 0) plain = false;
+        if (kz && nZ < 0) plain = false;
       }
     }
     if (plain) {
-      const int ls = (sx - 8 * dx) + 8 * ((sy - 8 * dy) + 8 * (sz - 8 * dz));
-      g[I] = Codec<S>::template load<I>(cur[(nb * Q + I) * 512 + ls]);
+      const int ls = (X > 0 ? xp : (X < 0 ? xn : lx)) + (Y > 0 ? yp : (Y < 0 ? yn : y0)) +
+                     (Z > 0 ? zp : (Z < 0 ? zn : z0));
+      g[I] = Codec<S>::template load<I>(cur[(int64_t)nb * (Q * 512) + (I * 512 + ls)]);
     } else if (jmp == 2) {
       g[I] = explosion<S, I>(a, gx, gy, gz);
     } else {
@@ -408,8 +429,15 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
     a.co = view(W);
     a.ccur = W.f[W.cur];
   }
-  // G_i blocks need no cross-level data: launched before the finer substeps
-  if (!unfused && V.n_blocks > V.n_c) {
+  // G_i blocks need no cross-level data and share no output with the rest of
+  // this substep: launched first, on the level's second stream, they overlap
+  // the finer substeps and this level's G_c launch; joined before returning
+  const bool fork = !unfused && V.n_blocks > V.n_c;
+  const cudaStream_t s_main = s;
+  if (fork) {
+    LBM_CUDA(cudaEventRecord(g.mr_fork[l], s_main));
+    LBM_CUDA(cudaStreamWaitEvent(g.mr_aux[l], g.mr_fork[l], 0));
+    s = g.mr_aux[l];
     if (closure) {
       MrArgs ai = a;
       ai.b0 = V.n_c;
@@ -423,6 +451,8 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
                                 (V.n_blocks - V.n_c) * 512);
       if (st) return st;
     }
+    LBM_CUDA(cudaEventRecord(g.mr_join[l], s));
+    s = s_main;
   }
   if (l > 0) {
     if ((st = mr_advance<S, COLL>(g, l - 1, 1, s))) return st;
@@ -459,6 +489,7 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
     prof_end(g, s, pr);
   }
   LBM_CUDA(cudaGetLastError());
+  if (fork) LBM_CUDA(cudaStreamWaitEvent(s, g.mr_join[l], 0));
   V.cur = nx;
   return LBM_OK;
 }
@@ -477,6 +508,11 @@ lbm_status multires_step(Grid& g, cudaStream_t s) {
         if (!V.tmp) return fail(LBM_ERR_OOM, "unfused scratch allocation failed");
       }
     }
+  }
+  for (int l = 0; l < g.n_levels; ++l) {
+    if (!g.mr_aux[l]) LBM_CUDA(cudaStreamCreateWithFlags(&g.mr_aux[l], cudaStreamNonBlocking));
+    if (!g.mr_fork[l]) LBM_CUDA(cudaEventCreateWithFlags(&g.mr_fork[l], cudaEventDisableTiming));
+    if (!g.mr_join[l]) LBM_CUDA(cudaEventCreateWithFlags(&g.mr_join[l], cudaEventDisableTiming));
   }
   const bool bgk = g.phys.collision == C_BGK;
   switch (g.phys.storage) {

@@ -18,9 +18,8 @@
 // MODE_MONOLITHIC is the paper's naive single kernel: every block, per-voxel
 // branches, boundary values read from a full-domain array.
 //
-// Each CTA stages the 27-entry neighbour list of its block(s) in shared
-// memory; a pull that leaves the block reads the neighbour block through it
-// (-1 = no block: bounce-back).  A per-block bit (blk_walls) marks blocks
+// A pull that leaves the block reads the neighbour block through the
+// block's row of the 27-entry neighbour table (-1 = no block: bounce-back).  A per-block bit (blk_walls) marks blocks
 // that hold or touch a wall voxel or a missing neighbour; only those read
 // voxel flags, so uniform fluid blocks stream with no metadata traffic.
 #include <algorithm>
@@ -81,15 +80,23 @@ lbm_status sparse_build(Grid& g, Level& L) {
   std::vector<int64_t> ids;
   for (int64_t vb = 0; vb < nvb; ++vb)
     if (act[(size_t)vb]) ids.push_back(vb);
+  // memory grouping: boundary blocks first; bitmask grouping: Morton only
+  L.bitmask = g.phys.schedule == LBM_SCHEDULE_BITMASK;
   auto key = [&](int64_t vb) {
     const uint32_t bx = (uint32_t)(vb % L.nbx), by = (uint32_t)((vb / L.nbx) % L.nby),
                    bz = (uint32_t)(vb / ((int64_t)L.nbx * L.nby));
-    return ((uint64_t)(bnd[(size_t)vb] ? 0 : 1) << 32) | morton3(bx, by, bz);
+    const uint64_t grp = L.bitmask ? 0 : (bnd[(size_t)vb] ? 0 : 1);
+    return (grp << 32) | morton3(bx, by, bz);
   };
   std::sort(ids.begin(), ids.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
   L.n_blocks = (int64_t)ids.size();
   L.n_b = 0;
   for (int64_t vb : ids) L.n_b += bnd[(size_t)vb] ? 1 : 0;
+  auto is_bnd = [&](int64_t b) { return bnd[(size_t)ids[(size_t)b]] != 0; };
+  L.bnd_bits_h.assign(L.bitmask ? (size_t)((L.n_blocks + 31) / 32) : 0, 0u);
+  if (L.bitmask)
+    for (int64_t b = 0; b < L.n_blocks; ++b)
+      if (is_bnd(b)) L.bnd_bits_h[(size_t)(b / 32)] |= 1u << (b % 32);
   L.bmap_h.assign((size_t)nvb, -1);
   L.coords_h.resize((size_t)L.n_blocks * 3);
   for (int64_t b = 0; b < L.n_blocks; ++b) {
@@ -138,7 +145,7 @@ lbm_status sparse_build(Grid& g, Level& L) {
         sf[(size_t)(b * E3 + l)] = f;
         if (type_updated(flag_type(f))) {
           ++n_upd;
-          if (b < L.n_b) ++n_upd_b;
+          if (is_bnd(b)) ++n_upd_b;
         }
         if (type_regularized(flag_type(f))) ++n_reg;
       }
@@ -147,15 +154,54 @@ lbm_status sparse_build(Grid& g, Level& L) {
   L.n_updated = n_upd;
   L.n_upd_b = n_upd_b;
   L.n_reg = n_reg;
-  // stash the per-slot flags and wall bits until upload
+  // per-slot wall mask of the blocks that pull with checks (walls bit or
+  // boundary group): bit i = the source of population i bounces back (missing
+  // block or wall voxel), bit 30 = regularized voxel, bit 31 = not updated.
+  // One coalesced 32-bit load then replaces a flag load per population.
+  std::vector<uint32_t> wm((size_t)L.n_slots, 0u);
+  for (int64_t b = 0; b < L.n_blocks; ++b) {
+    if (!bw[(size_t)b] && !is_bnd(b)) continue;
+    for (int l = 0; l < E3; ++l) {
+      const int t = flag_type(sf[(size_t)(b * E3 + l)]);
+      uint32_t m = 0;
+      if (!type_updated(t)) m |= 1u << 31;
+      if (type_regularized(t)) m |= 1u << 30;
+      const int lc[3] = {l % E, (l / E) % E, l / (E * E)};
+      for (int i = 1; i < Q; ++i) {
+        int sc[3] = {lc[0] - cx(i), lc[1] - cy(i), lc[2] - cz(i)};
+        int d[3];
+        for (int a = 0; a < 3; ++a) {
+          d[a] = sc[a] < 0 ? -1 : (sc[a] >= E ? 1 : 0);
+          sc[a] -= d[a] * E;
+        }
+        const int32_t nb = L.nbr_h[(size_t)b * 27 + (d[0] + 1) + 3 * (d[1] + 1) + 9 * (d[2] + 1)];
+        const bool wall =
+            nb < 0 || type_wall(flag_type(sf[(size_t)((int64_t)nb * E3 + sc[0] + E * (sc[1] + E * sc[2]))]));
+        if (wall) m |= 1u << i;
+      }
+      wm[(size_t)(b * E3 + l)] = m;
+    }
+  }
+  // stash the per-slot flags, masks and wall bits until upload
   L.bc_h.clear();
   g.dfree(L.flags_d, g.stream);
   g.dfree(L.blk_walls_d, g.stream);
+  g.dfree(L.wmask_d, g.stream);
   L.flags_d = (uint8_t*)g.dalloc(sf.size(), g.stream);
   L.blk_walls_d = (uint8_t*)g.dalloc(bw.size() ? bw.size() : 1, g.stream);
-  if (!L.flags_d || !L.blk_walls_d) return fail(LBM_ERR_OOM, "device allocation failed");
+  L.wmask_d = (uint32_t*)g.dalloc(wm.size() * 4 + 4, g.stream);
+  if (!L.flags_d || !L.blk_walls_d || !L.wmask_d) return fail(LBM_ERR_OOM, "device allocation failed");
   LBM_CUDA(cudaMemcpy(L.flags_d, sf.data(), sf.size(), cudaMemcpyHostToDevice));
   if (!bw.empty()) LBM_CUDA(cudaMemcpy(L.blk_walls_d, bw.data(), bw.size(), cudaMemcpyHostToDevice));
+  if (!wm.empty()) LBM_CUDA(cudaMemcpy(L.wmask_d, wm.data(), wm.size() * 4, cudaMemcpyHostToDevice));
+  if (L.bitmask) {
+    g.dfree(L.bnd_bits_d, g.stream);
+    L.bnd_bits_d = (uint32_t*)g.dalloc(L.bnd_bits_h.size() * 4 + 4, g.stream);
+    if (!L.bnd_bits_d) return fail(LBM_ERR_OOM, "device allocation failed");
+    if (!L.bnd_bits_h.empty())
+      LBM_CUDA(cudaMemcpy(L.bnd_bits_d, L.bnd_bits_h.data(), L.bnd_bits_h.size() * 4,
+                          cudaMemcpyHostToDevice));
+  }
   return LBM_OK;
 }
 
@@ -192,6 +238,30 @@ lbm_status sparse_set_bc(Grid& g, Level& L, const float* bc_values, const float*
     return fail(LBM_ERR_INVALID, "regularized voxels need bc_values or default_bc");
   const int64_t E3 = (int64_t)L.E * L.E * L.E;
   L.bc_h.assign((size_t)L.n_reg * 4, 0.f);
+  if (L.bitmask) {
+    // indirect indexing: a per-slot rank into one compact value per
+    // regularized voxel (flag-scan order)
+    L.bc_idx_h.assign((size_t)L.n_slots, -1);
+    std::vector<float4> cmp((size_t)L.n_reg);
+    for_each_reg(L, [&](int64_t slot, int64_t k) {
+      const float* v = bc_values ? bc_values + k * 4 : def_bc;
+      for (int c = 0; c < 4; ++c) L.bc_h[(size_t)k * 4 + c] = v[c];
+      cmp[(size_t)k] = make_float4(v[0], v[1], v[2], v[3]);
+      L.bc_idx_h[(size_t)slot] = (int32_t)k;
+    });
+    g.dfree(L.bc_idx_d, g.stream);
+    g.dfree(L.bc_cmp_d, g.stream);
+    g.dfree(L.bc_full_d, g.stream);
+    L.bc_full_d = nullptr;
+    L.bc_idx_d = (int32_t*)g.dalloc(L.bc_idx_h.size() * 4 + 4, g.stream);
+    L.bc_cmp_d = (float4*)g.dalloc(cmp.size() * sizeof(float4) + 16, g.stream);
+    if (!L.bc_idx_d || !L.bc_cmp_d) return fail(LBM_ERR_OOM, "device allocation failed");
+    if (!L.bc_idx_h.empty())
+      LBM_CUDA(cudaMemcpy(L.bc_idx_d, L.bc_idx_h.data(), L.bc_idx_h.size() * 4, cudaMemcpyHostToDevice));
+    if (!cmp.empty())
+      LBM_CUDA(cudaMemcpy(L.bc_cmp_d, cmp.data(), cmp.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return LBM_OK;
+  }
   std::vector<float4> grp((size_t)(L.n_b * E3), make_float4(0.f, 0.f, 0.f, 1.f));
   for_each_reg(L, [&](int64_t slot, int64_t k) {
     const float* v = bc_values ? bc_values + k * 4 : def_bc;
@@ -216,7 +286,12 @@ void sparse_fill_bc_full(const Level& L, float4* full) {
 
 // ------------------------------------------------------------------ kernels
 
-enum { MODE_INTERIOR = 0, MODE_BOUNDARY = 1, MODE_MONOLITHIC = 2 };
+// INTERIOR / BOUNDARY: the two group kernels of the memory grouping, each
+// over its own contiguous block range; *_BM: the same kernels under the
+// bitmask grouping, launched over every block and returning at once on a
+// block of the other group; MONOLITHIC: the naive single kernel.
+enum { MODE_INTERIOR = 0, MODE_BOUNDARY = 1, MODE_MONOLITHIC = 2, MODE_INTERIOR_BM = 3,
+       MODE_BOUNDARY_BM = 4 };
 constexpr int SP_THREADS = 256;
 
 struct SparseArgs {
@@ -224,47 +299,50 @@ struct SparseArgs {
   void* fout;
   const int32_t* nbr;
   const uint8_t* flags;
+  const uint32_t* wmask;  // per-slot wall mask (blocks with walls, boundary group)
   const uint8_t* blk_walls;
   const float4* bc;
+  const uint32_t* bnd_bits;  // bitmask grouping: boundary block bits
+  const int32_t* bc_idx;     // bitmask grouping: per-slot index into bc_cmp
+  const float4* bc_cmp;      // bitmask grouping: compact BC values
   int64_t s0, s1;  // slot range [s0, s1), block aligned
   float omega;
 };
 
 template <int S, int E, int COLL, int MODE>
-__global__ void __launch_bounds__(SP_THREADS, MODE == MODE_INTERIOR ? 4 : 1)
+__global__ void __launch_bounds__(SP_THREADS,
+                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? 4 : 1)
     sparse_kernel(SparseArgs a) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E;
-  constexpr int BPC = SP_THREADS >= E3 ? SP_THREADS / E3 : 1;  // blocks touched per CTA
-  __shared__ int32_t snbr[BPC * 27];
-  const int64_t cta0 = a.s0 + (int64_t)blockIdx.x * SP_THREADS;
-  const int64_t b0 = cta0 / E3;
-  for (int t = threadIdx.x; t < BPC * 27; t += SP_THREADS) {
-    const int64_t bb = b0 + t / 27;
-    snbr[t] = bb * E3 < a.s1 ? a.nbr[bb * 27 + t % 27] : -1;
-  }
-  __syncthreads();
-  const int64_t slot = cta0 + threadIdx.x;
+  constexpr bool LEAN = MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM;
+  const int64_t slot = a.s0 + (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
   if (slot >= a.s1) return;
   const int64_t b = slot / E3;
   const int l = (int)(slot - b * E3);
-  const int lb = (int)(b - b0);
-  const int lx = l % E, ly = (l / E) % E, lz = l / (E * E);
-  const bool walls = MODE != MODE_INTERIOR || a.blk_walls[b];
-  uint8_t own = 0;
+  if constexpr (MODE == MODE_INTERIOR_BM || MODE == MODE_BOUNDARY_BM) {
+    const bool bnd = (a.bnd_bits[b >> 5] >> (b & 31)) & 1u;
+    if (bnd != (MODE == MODE_BOUNDARY_BM)) return;
+  }
+  const bool walls = !LEAN || a.blk_walls[b];
+  uint32_t wm = 0;
   if (walls) {
-    own = a.flags[slot];
-    if (!type_updated(flag_type(own))) return;
+    wm = a.wmask[slot];
+    if (wm & (1u << 31)) return;
   }
   const T* __restrict__ fin = (const T*)a.fin;
   float g[Q];
-  sparse_pull_voxel<S, E>(fin, snbr + lb * 27, a.flags, b, l, walls, g);
-  if constexpr (MODE == MODE_INTERIOR) {
+  sparse_pull_voxel<S, E>(fin, a.nbr + b * 27, wm, b, l, walls, g);
+  if constexpr (LEAN) {
     collide<COLL>(g, a.omega);
   } else {
-    const int t = flag_type(own);
-    if (type_regularized(t)) regularized_node(g, t, flag_normal(own), a.bc[slot], a.omega);
-    else collide<COLL>(g, a.omega);
+    if (wm & (1u << 30)) {
+      const uint8_t own = a.flags[slot];
+      const float4 bc = MODE == MODE_BOUNDARY_BM ? a.bc_cmp[a.bc_idx[slot]] : a.bc[slot];
+      regularized_node(g, flag_type(own), flag_normal(own), bc, a.omega);
+    } else {
+      collide<COLL>(g, a.omega);
+    }
   }
   T* __restrict__ fout = (T*)a.fout;
   static_for<Q>([&](auto ic) {
@@ -290,6 +368,7 @@ static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
   a.fout = L.f[L.cur ^ 1];
   a.nbr = L.nbr_d;
   a.flags = L.flags_d;
+  a.wmask = L.wmask_d;
   a.blk_walls = L.blk_walls_d;
   a.omega = (float)(1.0 / g.phys.tau);
   if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
@@ -297,6 +376,15 @@ static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
     a.s0 = 0;
     a.s1 = L.n_blocks * E3;
     launch_range<S, E, COLL, MODE_MONOLITHIC>(g, a, s, "sparse_monolithic", L.n_updated);
+  } else if (L.bitmask) {
+    a.bnd_bits = L.bnd_bits_d;
+    a.bc_idx = L.bc_idx_d;
+    a.bc_cmp = L.bc_cmp_d;
+    a.s0 = 0;
+    a.s1 = L.n_blocks * E3;
+    launch_range<S, E, COLL, MODE_BOUNDARY_BM>(g, a, s, "sparse_boundary_bitmask", L.n_upd_b);
+    launch_range<S, E, COLL, MODE_INTERIOR_BM>(g, a, s, "sparse_interior_bitmask",
+                                               L.n_updated - L.n_upd_b);
   } else {
     a.bc = L.bc_grp_d;
     a.s0 = 0;
@@ -319,6 +407,7 @@ static void uniform_range_t(Grid& g, Level& L, int64_t b0, int64_t b1, const voi
   a.fout = fout;
   a.nbr = L.nbr_d;
   a.flags = L.flags_d;
+  a.wmask = L.wmask_d;
   a.blk_walls = L.blk_walls_d;
   a.omega = omega;
   a.s0 = b0 * 512;

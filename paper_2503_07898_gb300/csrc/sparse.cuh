@@ -7,11 +7,14 @@
 namespace lbm {
 
 // Pull the 19 populations of voxel l of block b (block edge E) with halfway
-// bounce-back.  nbr27: the block's 27 neighbour ids, entry (dx+1) + 3 (dy+1)
-// + 9 (dz+1), entry 13 = b itself, -1 = none; usually in shared memory.
+// bounce-back.  nbr27: the block's row of the neighbour table in global
+// memory (27 ids, entry (dx+1) + 3 (dy+1) + 9 (dz+1), entry 13 = b itself,
+// -1 = none); each thread reads the six entries it needs through the
+// read-only cache, so a CTA starts pulling without a staging barrier.
 // walls: the block or one of its 26 neighbours holds a wall voxel, or a
-// neighbour is missing, so sources are checked against their flags; a block
-// without it pulls with no test at all.  flags: per-slot flag bytes.
+// neighbour is missing, so sources are checked against wm, the voxel's wall
+// mask (bit i = the source of population i bounces back); a block without
+// it pulls with no test at all.
 //
 // Address arithmetic is hoisted out of the 19 pulls: a voxel can only leave
 // its block across the faces it lies on, so the (at most) six blocks a pull
@@ -21,8 +24,7 @@ namespace lbm {
 // Each pull then costs a few selects and one 32 x 32 -> 64-bit multiply-add.
 template <int S, int E, bool WALLS>
 __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* __restrict__ fin,
-                                                    const int32_t* nbr27,
-                                                    const uint8_t* __restrict__ flags, int b,
+                                                    const int32_t* nbr27, uint32_t wm, int b,
                                                     int l, float g[Q]) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E, M = E - 1;
@@ -30,9 +32,10 @@ __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* 
   const int ex = lx == 0 ? -1 : (lx == M ? 1 : 0);
   const int ey = ly == 0 ? -1 : (ly == M ? 1 : 0);
   const int ez = lz == 0 ? -1 : (lz == M ? 1 : 0);
-  const int nX = nbr27[13 + ex], nY = nbr27[13 + 3 * ey], nZ = nbr27[13 + 9 * ez];
-  const int nXY = nbr27[13 + ex + 3 * ey], nXZ = nbr27[13 + ex + 9 * ez];
-  const int nYZ = nbr27[13 + 3 * ey + 9 * ez];
+  const int nX = __ldg(nbr27 + 13 + ex), nY = __ldg(nbr27 + 13 + 3 * ey);
+  const int nZ = __ldg(nbr27 + 13 + 9 * ez);
+  const int nXY = __ldg(nbr27 + 13 + ex + 3 * ey), nXZ = __ldg(nbr27 + 13 + ex + 9 * ez);
+  const int nYZ = __ldg(nbr27 + 13 + 3 * ey + 9 * ez);
   // source coordinate inside its block for c = +1, -1 (pre-scaled by the
   // axis stride for y and z)
   const int xp = (lx - 1) & M, xn = (lx + 1) & M;
@@ -57,8 +60,7 @@ __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* 
     if constexpr (!WALLS) {
       g[I] = Codec<S>::template load<I>(fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)]);
     } else {
-      bool wall = nb < 0;
-      if (!wall) wall = type_wall(flag_type(flags[(int64_t)nb * E3 + ls]));
+      const bool wall = (wm >> I) & 1u;
       g[I] = Codec<S>::template load<I>(wall ? self[opp(I) * E3]
                                              : fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)]);
     }
@@ -67,10 +69,10 @@ __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* 
 
 template <int S, int E>
 __device__ __forceinline__ void sparse_pull_voxel(const typename Codec<S>::T* __restrict__ fin,
-                                                  const int32_t* nbr27, const uint8_t* flags,
-                                                  int64_t b, int l, bool walls, float g[Q]) {
-  if (walls) sparse_pull_voxel_t<S, E, true>(fin, nbr27, flags, (int)b, l, g);
-  else sparse_pull_voxel_t<S, E, false>(fin, nbr27, flags, (int)b, l, g);
+                                                  const int32_t* nbr27, uint32_t wm, int64_t b,
+                                                  int l, bool walls, float g[Q]) {
+  if (walls) sparse_pull_voxel_t<S, E, true>(fin, nbr27, wm, (int)b, l, g);
+  else sparse_pull_voxel_t<S, E, false>(fin, nbr27, 0u, (int)b, l, g);
 }
 
 }  // namespace lbm

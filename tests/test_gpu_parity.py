@@ -104,7 +104,7 @@ def small_sphere_channel():
 
 
 @pytest.mark.parametrize("block_edge", [8, 4])
-@pytest.mark.parametrize("schedule", ["disaggregated", "monolithic"])
+@pytest.mark.parametrize("schedule", ["disaggregated", "monolithic", "bitmask"])
 def test_sparse_sphere_channel(lbm, block_edge, schedule):
     flags, bc = small_sphere_channel()
     rho, u = wl.random_fields(flags.shape, seed=26, u_amp=0.02)
@@ -127,6 +127,71 @@ def test_sparse_layout_bit_exact(lbm, block_edge):
     assert info["n_group_b"][0] == tab["n_boundary"]
     assert info["n_updated"][0] == int(updated_mask(flags).sum())
     assert lbm.lbm_get_layout(g, 0, lbm.LBM_LAYOUT_FLAGS).tobytes() == flags.tobytes()
+
+
+@pytest.mark.parametrize("block_edge", [8, 4])
+def test_sparse_bitmask_layout_bit_exact(lbm, block_edge):
+    """Bitmask grouping (Sec. 4, Table 2): Morton order over all blocks,
+    boundary bits and the per-slot index of the compact boundary values equal
+    the oracle's tables byte for byte."""
+    flags, bc = small_sphere_channel()
+    g = make_grid(lbm, "sparse", flags, bc, 0.56, schedule="bitmask", block_edge=block_edge)
+    tab = olayout.block_tables(flags, block_edge, grouping="bitmask")
+    coords = lbm.lbm_get_layout(g, 0, lbm.LBM_LAYOUT_BLOCK_COORDS).reshape(-1, 3)
+    nbr = lbm.lbm_get_layout(g, 0, lbm.LBM_LAYOUT_NBR).reshape(-1, 27)
+    assert coords.tobytes() == tab["coords"].tobytes()
+    assert nbr.tobytes() == tab["nbr"].tobytes()
+    bits = lbm.lbm_get_layout(g, 0, lbm.LBM_LAYOUT_BOUNDARY_BITS)
+    assert bits.tobytes() == tab["boundary_bits"].tobytes()
+    idx = lbm.lbm_get_layout(g, 0, lbm.LBM_LAYOUT_BC_INDEX)
+    assert idx.tobytes() == tab["bc_index"].tobytes()
+    assert lbm.lbm_get_info(g)["n_group_b"][0] == tab["n_boundary"] > 0
+
+
+def test_sparse_bitmask_equals_memory_grouping(lbm):
+    """Both groupings run the same per-voxel arithmetic: identical populations
+    after 60 steps (FP32 and FP16 storage)."""
+    flags, bc = small_sphere_channel()
+    rho, u = wl.random_fields(flags.shape, seed=27, u_amp=0.02)
+    for storage in ("f32", "f16"):
+        out = []
+        for schedule in ("disaggregated", "bitmask"):
+            g = make_grid(lbm, "sparse", flags, bc, 0.56, storage=storage, schedule=schedule)
+            out.append(gpu_run(lbm, g, rho, u, 60))
+        m = updated_mask(flags)
+        assert np.array_equal(out[0][:, m], out[1][:, m]), storage
+
+
+def test_grouping_is_fixed_at_creation(lbm):
+    flags, bc = small_sphere_channel()
+    gb = make_grid(lbm, "sparse", flags, bc, 0.56, schedule="bitmask")
+    lbm.lbm_set_schedule(gb, "monolithic")
+    lbm.lbm_set_schedule(gb, "bitmask")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_schedule(gb, "disaggregated")
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    gm = make_grid(lbm, "sparse", flags, bc, 0.56)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_schedule(gm, "bitmask")
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_grid_create_dense((16, 16, 16), lbm.physics(0.6, schedule="bitmask"))
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_grid_create_multires((32, 32, 32), 2, np.zeros((1, 1, 1), np.uint8),
+                                     lbm.physics(0.6, periodic=(1, 1, 1), schedule="bitmask"))
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_step_without_boundary_values_is_rejected(lbm):
+    """Regularized voxels with no boundary values: lbm_step refuses to run."""
+    flags, _ = small_sphere_channel()
+    nz, ny, nx = flags.shape
+    for schedule in ("disaggregated", "bitmask"):
+        g = lbm.lbm_grid_create_sparse((nx, ny, nz), 8, flags, lbm.physics(0.56, schedule=schedule))
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step(g, 1)
+        assert e.value.status == lbm.LBM_ERR_INVALID
 
 
 def test_sparse_periodic_equals_dense(lbm):

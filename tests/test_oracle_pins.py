@@ -296,6 +296,27 @@ def test_block_tables_hand_example():
     assert nbr[0, k(0, 0, 0)] == 0
 
 
+def test_block_tables_bitmask_grouping_hand_example():
+    """Bitmask grouping of the example above: every block in Morton order,
+    (1,1,0) marked by bit 3, its two regularized voxels indexed 0 and 1 in
+    flag-scan order, every other slot -1."""
+    flags = np.full((8, 16, 24), wl.OUTSIDE, np.uint8)
+    flags[:, 0:16, 0:16] = wl.FLUID
+    flags[5, 12, 12] = wl.flag(wl.VELOCITY, wl.NZ_P)
+    flags[6, 9, 10] = wl.flag(wl.PRESSURE, wl.NX_M)
+    t = layout.block_tables(flags, 8, grouping="bitmask")
+    assert [tuple(c) for c in t["coords"]] == [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0)]
+    assert t["n_boundary"] == 1
+    assert t["boundary_bits"].tolist() == [1 << 3]
+    idx = t["bc_index"]
+    # flag-scan order: (z=5, y=12, x=12) comes before (z=6, y=9, x=10)
+    assert idx[3 * 512 + 4 + 8 * (4 + 8 * 5)] == 0
+    assert idx[3 * 512 + 2 + 8 * (1 + 8 * 6)] == 1
+    assert int((idx >= 0).sum()) == 2
+    k = lambda dx, dy, dz: (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+    assert t["nbr"][0, k(1, 1, 0)] == 3 and t["nbr"][3, k(-1, 0, 0)] == 2
+
+
 def test_block_tables_neighbour_symmetry_and_sphere_counts():
     """Config-3 geometry: 22 767 active 8^3 blocks (34.7 % of 65 536), 716 of
     them boundary (inlet + outlet columns); nbr is an involution."""
