@@ -166,23 +166,34 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
         flags, bc = wl.sphere_channel()
         t = flags & 7
         bcl = np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
-        res = {}
-        for name, kw in (("disaggregated_f32", dict(storage="f32")),
-                         ("disaggregated_bitmask_f32", dict(storage="f32", schedule="bitmask")),
-                         ("monolithic_f32", dict(storage="f32", schedule="monolithic")),
-                         ("disaggregated_f16", dict(storage="f16"))):
-            g = lbm.lbm_grid_create_sparse(flags.shape[::-1], 8, flags,
-                                           lbm.physics(0.52, **kw), stream=stream)
-            lbm.lbm_set_boundary(g, 0, None, bcl)
-            lbm.lbm_init_equilibrium(g, 0, None, None)
-            n_upd = lbm.lbm_get_info(g)["n_updated"][0]
-            lbm.lbm_step(g, 3, stream)
-            ms = _time_steps(torch, lbm, lambda n: lbm.lbm_step(g, n, stream), stream, steps)
-            bpu = 152 if kw["storage"] == "f32" else 76
-            glups = n_upd * steps / (ms * 1e-3) / 1e9
-            res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
-            lbm.lbm_grid_destroy(g)
-        out["sphere_channel_512x256x256_sparse8"] = res
+        for key, q, cases in (
+                ("sphere_channel_512x256x256_sparse8", 19,
+                 (("disaggregated_f32", dict(storage="f32")),
+                  ("disaggregated_bitmask_f32", dict(storage="f32", schedule="bitmask")),
+                  ("monolithic_f32", dict(storage="f32", schedule="monolithic")),
+                  ("disaggregated_f16", dict(storage="f16")))),
+                # the paper's register-pressure configuration: D3Q27,
+                # block-sparse, regularized inflow / outflow (Sec. 6.2)
+                ("sphere_channel_512x256x256_sparse8_d3q27", 27,
+                 (("disaggregated_f32", dict(storage="f32")),
+                  ("disaggregated_bitmask_f32", dict(storage="f32", schedule="bitmask")),
+                  ("monolithic_f32", dict(storage="f32", schedule="monolithic"))))):
+            res = {}
+            for name, kw in cases:
+                g = lbm.lbm_grid_create_sparse(flags.shape[::-1], 8, flags,
+                                               lbm.physics(0.52, lattice=q, **kw), stream=stream)
+                lbm.lbm_set_boundary(g, 0, None, bcl)
+                lbm.lbm_init_equilibrium(g, 0, None, None)
+                n_upd = lbm.lbm_get_info(g)["n_updated"][0]
+                lbm.lbm_step(g, 3, stream)
+                ms = _time_steps(torch, lbm, lambda n: lbm.lbm_step(g, n, stream), stream, steps)
+                bpu = 2 * q * (4 if kw["storage"] == "f32" else 2)
+                glups = n_upd * steps / (ms * 1e-3) / 1e9
+                res[name] = {"GLUPS": round(glups, 3),
+                             "roofline_frac": round(glups * bpu / peak, 4),
+                             "bytes_per_update": bpu}
+                lbm.lbm_grid_destroy(g)
+            out[key] = res
     if "multires" in which:
         lmap = wl.multires_slab_map()
         res = {}
@@ -405,8 +416,11 @@ def run_ours(args, rank, world, local_rank):
         u_den = float((u_ref[:, upd] ** 2).sum())
         for name, kw in (("monolithic_f32", dict(storage="f32", schedule="monolithic")),
                          ("disaggregated_f16", dict(storage="f16", schedule="disaggregated")),
-                         ("disaggregated_bf16", dict(storage="bf16", schedule="disaggregated"))):
-            if kw["storage"] == args.storage and kw["schedule"] == args.schedule:
+                         ("disaggregated_bf16", dict(storage="bf16", schedule="disaggregated")),
+                         ("disaggregated_f32_d3q27", dict(storage="f32", schedule="disaggregated",
+                                                          lattice=27))):
+            q = kw.get("lattice", 19)
+            if kw["storage"] == args.storage and kw["schedule"] == args.schedule and q == 19:
                 continue
             gv = lbm.lbm_grid_create_dense(dims, lbm.physics(tau, **kw), stream=stream)
             lbm.lbm_set_boundary(gv, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
@@ -423,10 +437,12 @@ def run_ours(args, rank, world, local_rank):
             vms = a0.elapsed_time(a1)
             lbm.lbm_get_moments(gv, 0, rho_d, u_var)
             l2 = (float(((u_var - u_ref)[:, upd] ** 2).sum()) / u_den) ** 0.5
+            bpu = BYTES_PER_UPDATE[kw["storage"]] * q // 19
             variants[name] = {"GLUPS": round(n_upd * kv / (vms * 1e-3) / 1e9, 3),
-                              "roofline_frac": round(n_upd * kv * BYTES_PER_UPDATE[kw["storage"]]
-                                                     / (vms * 1e-3) / 1e9 / peak, 4),
-                              "velocity_l2_vs_f32": float(f"{l2:.3e}"),
+                              "roofline_frac": round(n_upd * kv * bpu / (vms * 1e-3) / 1e9 / peak, 4),
+                              "bytes_per_update": bpu,
+                              ("velocity_l2_vs_f32" if q == 19 else "velocity_l2_vs_d3q19_f32"):
+                                  float(f"{l2:.3e}"),
                               "after_steps": 20 + kv}
             lbm.lbm_grid_destroy(gv)
         del rho_d, u_ref, u_var

@@ -1,8 +1,8 @@
 """Brute-force sparse block tables (oracle).
 
-Reading of the sparse layout (Sec. 4 and Sec. 6.2; the paper names a
-block-sparse grid "commonly managed by space-filling curves" and the
-boundary / non-boundary block split, but gives no ordering):
+Reading of the sparse layout (Sec. 4 and Sec. 6.2; the paper orders blocks
+along a space-filling curve and splits boundary from non-boundary blocks,
+but names no curve and no ordering):
 
 * the virtual box is cut into cubic blocks of edge B (8 by default);
 * a block is active iff it holds at least one updated voxel (type fluid,

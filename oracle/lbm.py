@@ -1,7 +1,8 @@
-"""Plain FP64 D3Q19 lattice-Boltzmann step on a virtual box (oracle).
+"""Plain FP64 D3Q19 / D3Q27 lattice-Boltzmann step on a virtual box (oracle).
 
 State
-  f    : float64 array (19, nz, ny, nx), the stored post-collision
+  f    : float64 array (Q, nz, ny, nx), Q = 19 or 27 (the lattice is read
+         from this length), the stored post-collision
          populations f* of every voxel (x fastest).  Voxels that are not
          updated (solid, not in domain) hold 0.
   flags: uint8 array (nz, ny, nx).  Bits 0-2 = type
@@ -83,31 +84,33 @@ def _source_outside(shape, c, periodic):
 def stream_with_walls(f, flags, periodic):
     """Steps 1-2: pulled populations g with halfway bounce-back at walls.
 
-    Returns g of shape (19,) + box.  Rows of U at regularized nodes are
-    still the pulled (or bounced) values; ``regularized_boundary`` replaces
-    them.
+    Returns g of shape (Q,) + box (Q = 19 or 27, from f).  Rows of U at
+    regularized nodes are still the pulled (or bounced) values;
+    ``regularized_boundary`` replaces them.
     """
+    lat = L.lattice(f.shape[0])
     types = flag_type(flags)
     g = np.empty_like(f)
-    for i in range(L.Q):
-        cx, cy, cz = (int(v) for v in L.C[i])
+    for i in range(lat.Q):
+        cx, cy, cz = (int(v) for v in lat.C[i])
         src_val = _shift(f[i], cz, cy, cx)
         src_type = _shift(types, cz, cy, cx)
         wall = (src_type == SOLID) | (src_type == OUTSIDE)
         wall = wall | _source_outside(flags.shape, (cx, cy, cz), periodic)
-        g[i] = np.where(wall, f[L.OPP[i]], src_val)
+        g[i] = np.where(wall, f[lat.OPP[i]], src_val)
     return g
 
 
 def regularized_boundary(g_node, normal, bc_node, kind, tau):
     """Step 3 for a set of nodes sharing one normal.
 
-    g_node : (19, n) pulled populations; normal: int 0..5; bc_node: (4, n);
+    g_node : (Q, n) pulled populations; normal: int 0..5; bc_node: (4, n);
     kind   : VELOCITY or PRESSURE.
-    Returns (f_star (19, n), rho (n,), u (3, n)).
+    Returns (f_star (Q, n), rho (n,), u (3, n)).
     """
+    lat = L.lattice(g_node.shape[0])
     nvec = L.NORMALS[normal]
-    cn = L.C @ nvec                      # c_i . n for every i
+    cn = lat.C @ nvec                    # c_i . n for every i
     k0 = np.flatnonzero(cn == 0)
     kp = np.flatnonzero(cn > 0)
     unknown = np.flatnonzero(cn < 0)
@@ -120,45 +123,46 @@ def regularized_boundary(g_node, normal, bc_node, kind, tau):
         rho = bc_node[3].copy()
         un = s / rho - 1.0
         u = np.stack([un * nvec[0], un * nvec[1], un * nvec[2]]).astype(np.float64)
-    feq = L.equilibrium(rho, u)
+    feq = lat.equilibrium(rho, u)
     g = g_node.copy()
     for i in unknown:
-        j = L.OPP[i]
+        j = lat.OPP[i]
         g[i] = feq[i] + (g[j] - feq[j])
-    pi_neq = L.second_moment(g - feq)
-    fneq = L.regularized_neq(pi_neq)
+    pi_neq = lat.second_moment(g - feq)
+    fneq = lat.regularized_neq(pi_neq)
     f_star = feq + (1.0 - 1.0 / tau) * fneq
     return f_star, rho, u
 
 
 def collide(g, tau, collision="bgk", force=None):
-    """Step 4 on pulled populations g (19,) + S.  Returns (f*, rho, u).
+    """Step 4 on pulled populations g (Q,) + S.  Returns (f*, rho, u).
 
     ``force`` (3 floats) adds a constant body force with Guo's scheme
     (velocity shifted by F/2, source (1 - 1/(2 tau)) w_i [3(c_i - u) +
     9 (c_i.u) c_i].F); it exists only for the Poiseuille pin.
     """
+    lat = L.lattice(g.shape[0])
     rho = g.sum(axis=0)
-    Cf = L.C.astype(np.float64)
+    Cf = lat.C.astype(np.float64)
     j = np.stack([np.tensordot(Cf[:, a], g, axes=(0, 0)) for a in range(3)])
     if force is not None:
         j = j + 0.5 * np.asarray(force, dtype=np.float64).reshape((3,) + (1,) * rho.ndim)
     u = j / rho
-    feq = L.equilibrium(rho, u)
+    feq = lat.equilibrium(rho, u)
     if collision == "bgk":
         f_star = g - (g - feq) / tau
     elif collision == "reg":
-        f_star = feq + (1.0 - 1.0 / tau) * L.regularized_neq(L.second_moment(g - feq))
+        f_star = feq + (1.0 - 1.0 / tau) * lat.regularized_neq(lat.second_moment(g - feq))
     else:
         raise ValueError(collision)
     if force is not None:
         F = np.asarray(force, dtype=np.float64)
-        for i in range(L.Q):
+        for i in range(lat.Q):
             cu = Cf[i, 0] * u[0] + Cf[i, 1] * u[1] + Cf[i, 2] * u[2]
             src = 0.0
             for a in range(3):
                 src = src + (3.0 * (Cf[i, a] - u[a]) + 9.0 * cu * Cf[i, a]) * F[a]
-            f_star[i] = f_star[i] + (1.0 - 0.5 / tau) * L.W[i] * src
+            f_star[i] = f_star[i] + (1.0 - 0.5 / tau) * lat.W[i] * src
     return f_star, rho, u
 
 
@@ -195,9 +199,10 @@ def run(f, flags, tau, n_steps, **kw):
     return f
 
 
-def init_equilibrium(rho, u, flags=None):
-    """Initial state f* = f^eq(rho, u) in FP64 (0 on voxels not updated)."""
-    f = L.equilibrium(rho, u)
+def init_equilibrium(rho, u, flags=None, q=19):
+    """Initial state f* = f^eq(rho, u) of lattice(q) in FP64 (0 on voxels
+    not updated)."""
+    f = L.equilibrium(rho, u, q)
     if flags is not None:
         t = flag_type(flags)
         upd = (t == FLUID) | (t == VELOCITY) | (t == PRESSURE)
@@ -208,7 +213,7 @@ def init_equilibrium(rho, u, flags=None):
 def state_moments(f, flags=None):
     """Density and velocity of the stored state; NaN on voxels not updated."""
     rho = f.sum(axis=0)
-    Cf = L.C.astype(np.float64)
+    Cf = L.lattice(f.shape[0]).C.astype(np.float64)
     j = np.stack([np.tensordot(Cf[:, a], f, axes=(0, 0)) for a in range(3)])
     with np.errstate(invalid="ignore", divide="ignore"):
         u = j / rho
@@ -226,7 +231,7 @@ def conservation(f, flags=None):
         t = flag_type(flags)
         upd = (t == FLUID) | (t == VELOCITY) | (t == PRESSURE)
         f = np.where(upd[None], f, 0.0)
-    Cf = L.C.astype(np.float64)
+    Cf = L.lattice(f.shape[0]).C.astype(np.float64)
     m = f.sum()
     j = [float(np.tensordot(Cf[:, a], f, axes=(0, 0)).sum()) for a in range(3)]
     return np.array([m] + j)

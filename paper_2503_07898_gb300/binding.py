@@ -31,7 +31,8 @@ SCHEDULES = {"disaggregated": 0, "monolithic": 1, "bitmask": 2}
 
 class lbm_physics(C.Structure):
     _fields_ = [("tau", C.c_double), ("collision", C.c_int), ("storage", C.c_int),
-                ("closure", C.c_int), ("periodic", C.c_int * 3), ("schedule", C.c_int)]
+                ("closure", C.c_int), ("periodic", C.c_int * 3), ("schedule", C.c_int),
+                ("lattice", C.c_int)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -47,7 +48,7 @@ class lbm_info(C.Structure):
                 ("block_edge", C.c_int), ("n_updated", C.c_int64 * 4),
                 ("n_blocks", C.c_int64 * 4), ("n_group_b", C.c_int64 * 4),
                 ("n_regularized", C.c_int64), ("population_bytes", C.c_size_t * 4),
-                ("steps_done", C.c_int64)]
+                ("steps_done", C.c_int64), ("lattice", C.c_int)]
 
 
 class lbm_kernel_stat(C.Structure):
@@ -181,7 +182,7 @@ def _ptr(a, dtype):
 
 
 def physics(tau, collision="bgk", storage="f32", periodic=(0, 0, 0), schedule="disaggregated",
-            closure=0):
+            closure=0, lattice=19):
     p = lbm_physics()
     p.tau = float(tau)
     p.collision = {"bgk": 0, "reg": 1}[collision] if isinstance(collision, str) else int(collision)
@@ -191,6 +192,7 @@ def physics(tau, collision="bgk", storage="f32", periodic=(0, 0, 0), schedule="d
     for a in range(3):
         p.periodic[a] = int(bool(periodic[a]))
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    p.lattice = int(lattice)
     return p
 
 
@@ -272,7 +274,8 @@ def lbm_get_info(grid):
             "block_edge": info.block_edge, "n_updated": list(info.n_updated)[:L],
             "n_blocks": list(info.n_blocks)[:L], "n_group_b": list(info.n_group_b)[:L],
             "n_regularized": info.n_regularized,
-            "population_bytes": list(info.population_bytes)[:L], "steps_done": info.steps_done}
+            "population_bytes": list(info.population_bytes)[:L], "steps_done": info.steps_done,
+            "lattice": info.lattice}
 
 
 def lbm_set_schedule(grid, schedule):
@@ -359,7 +362,7 @@ def lbm_set_populations(grid, level, src):
 def lbm_get_populations_f64(grid, level=0, dst=None):
     nx, ny, nz = _box(grid, level)
     if dst is None:
-        dst = np.empty((19, nz, ny, nx), np.float64)
+        dst = np.empty((lbm_get_info(grid)["lattice"], nz, ny, nx), np.float64)
     p, d, _ = _ptr(dst, np.float64)
     _check(load().lbm_get_populations_f64(grid.ptr, int(level), p, d), "lbm_get_populations_f64")
     return dst

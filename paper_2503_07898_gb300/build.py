@@ -17,6 +17,11 @@ LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2"]
 SOURCES = ["api.cu", "dense.cu", "sparse.cu", "fields.cu", "multires.cu", "noalloc.cu", "closure.cu", "batch.cu"]
+# The lattice-dependent sources are compiled a second time for D3Q27 (their
+# code lands in namespace lbm::q27; the D3Q19 build in lbm::q19).
+LATTICE_SOURCES = ["dense.cu", "sparse.cu", "fields.cu"]
+UNITS = [(src, [], src.replace(".cu", ".o")) for src in SOURCES] + \
+        [(src, ["-DLBM_Q=27"], src.replace(".cu", "_q27.o")) for src in LATTICE_SOURCES]
 
 
 def _nvcc():
@@ -32,12 +37,13 @@ def _newest_header():
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 
-def _compile(nvcc, src, verbose):
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+def _compile(nvcc, unit, verbose):
+    src, defs, obj_name = unit
+    obj = os.path.join(BUILD, obj_name)
     s = os.path.join(CSRC, src)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(s), _newest_header()):
         return obj, ""
-    cmd = [nvcc] + ARCH + FLAGS + ["-c", s, "-o", obj]
+    cmd = [nvcc] + ARCH + FLAGS + defs + ["-c", s, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,8 +59,8 @@ def build(verbose=False, force=False):
     if force:
         for f in os.listdir(BUILD):
             os.remove(os.path.join(BUILD, f))
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, verbose), SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        results = list(ex.map(lambda u: _compile(nvcc, u, verbose), UNITS))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:

@@ -147,6 +147,10 @@ static lbm_status check_physics(const lbm_physics* p) {
       p->schedule != LBM_SCHEDULE_BITMASK)
     return fail(LBM_ERR_INVALID, "unknown schedule");
   if (p->closure != 0 && p->closure != 1) return fail(LBM_ERR_INVALID, "closure must be 0 or 1");
+  if (p->lattice != 0 && p->lattice != 19 && p->lattice != 27)
+    return fail(LBM_ERR_INVALID, "lattice must be 19 or 27");
+  if (p->lattice == 27 && p->closure)
+    return fail(LBM_ERR_UNSUPPORTED, "the closure runs on D3Q19 grids");
   return LBM_OK;
 }
 
@@ -168,7 +172,7 @@ static lbm_status alloc_common(Grid& g) {
 }
 
 static lbm_status alloc_populations(Grid& g, Level& L) {
-  L.pop_bytes = (size_t)Q * (size_t)L.n_slots * storage_bytes(g.phys.storage);
+  L.pop_bytes = (size_t)g.q * (size_t)L.n_slots * storage_bytes(g.phys.storage);
   for (int k = 0; k < L.nbuf; ++k) {
     L.f[k] = g.dalloc(L.pop_bytes, g.stream);
     if (!L.f[k]) return fail(LBM_ERR_OOM, "population buffer allocation failed");
@@ -189,6 +193,8 @@ static lbm_status begin(lbm_grid** out, const lbm_physics* phys, const lbm_alloc
   if (!h) return fail(LBM_ERR_OOM, "host allocation failed");
   gp = &h->g;
   gp->phys = *phys;
+  gp->q = phys->lattice == 27 ? 27 : 19;
+  gp->phys.lattice = gp->q;
   if (alloc) {
     gp->alloc = *alloc;
     gp->have_alloc = true;
@@ -240,34 +246,9 @@ static lbm_status dense_groups(Grid& g, Level& L, const float* bc_values, const 
   // per-voxel wall mask when walls are not only the box sides, or when the
   // boundary group is not the contiguous tail
   if (has_wall_voxel || (!regs.empty() && !L.dense_reg_tail)) {
-    std::vector<uint32_t> wm((size_t)N);
-    const int* per = g.phys.periodic;
-    for (int z = 0; z < L.nz; ++z)
-      for (int y = 0; y < L.ny; ++y)
-        for (int x = 0; x < L.nx; ++x) {
-          const int64_t v = x + (int64_t)L.nx * (y + (int64_t)L.ny * z);
-          const int t = flag_type(fl[v]);
-          uint32_t m = 0;
-          if (!type_updated(t)) m |= 1u << 31;
-          if (type_regularized(t)) m |= 1u << 30;
-          for (int i = 1; i < Q; ++i) {
-            int s[3] = {x - cx(i), y - cy(i), z - cz(i)};
-            const int n[3] = {L.nx, L.ny, L.nz};
-            bool wall = false;
-            for (int a = 0; a < 3; ++a) {
-              if (s[a] < 0 || s[a] >= n[a]) {
-                if (per[a]) s[a] = (s[a] + n[a]) % n[a];
-                else wall = true;
-              }
-            }
-            if (!wall) {
-              const int64_t sv = s[0] + (int64_t)L.nx * (s[1] + (int64_t)L.ny * s[2]);
-              wall = type_wall(flag_type(fl[sv]));
-            }
-            if (wall) m |= 1u << i;
-          }
-          wm[(size_t)v] = m;
-        }
+    std::vector<uint32_t> wm;
+    if (g.q == 27) q27::dense_wall_mask(g, L, wm);
+    else q19::dense_wall_mask(g, L, wm);
     if ((st = upload(g, &L.wmask_d, wm.data(), wm.size()))) return st;
   }
   if (!regs.empty()) {
@@ -313,7 +294,7 @@ lbm_status lbm_grid_create_dense(const int dims[3], const lbm_physics* phys,
   set_error("");
   if (!dims || dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0)
     return fail(LBM_ERR_INVALID, "dims must be positive");
-  if ((double)dims[0] * dims[1] * dims[2] * Q >= 9.0e18)
+  if ((double)dims[0] * dims[1] * dims[2] * 27 >= 9.0e18)
     return fail(LBM_ERR_INVALID, "grid too large");
   if (phys && phys->closure) return fail(LBM_ERR_UNSUPPORTED, "the closure runs on multi-resolution grids");
   if (phys && phys->schedule == LBM_SCHEDULE_BITMASK)
@@ -362,7 +343,8 @@ lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge, const uint8
   L.nz = dims[2];
   L.E = block_edge;
   L.flags_h.assign(flags, flags + (size_t)dims[0] * dims[1] * dims[2]);
-  if ((st = sparse_build(g, L)) || (st = alloc_common(g)) || (st = alloc_populations(g, L)) ||
+  if ((st = (g.q == 27 ? q27::sparse_build(g, L) : q19::sparse_build(g, L))) ||
+      (st = alloc_common(g)) || (st = alloc_populations(g, L)) ||
       (st = sparse_upload(g, L))) {
     free_grid(g);
     delete *out;
@@ -379,6 +361,8 @@ lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
   if (!finest_dims || !level_map) return fail(LBM_ERR_INVALID, "NULL argument");
   if (phys && phys->schedule == LBM_SCHEDULE_BITMASK)
     return fail(LBM_ERR_UNSUPPORTED, "bitmask grouping is a block-sparse layout");
+  if (phys && phys->lattice == 27)
+    return fail(LBM_ERR_UNSUPPORTED, "multi-resolution grids are D3Q19");
   Grid* gp = nullptr;
   lbm_status st = begin(out, phys, alloc, stream, gp);
   if (st) return st;
@@ -444,6 +428,7 @@ lbm_status lbm_get_info(const lbm_grid* h, lbm_info* out) {
     out->population_bytes[l] = g.lv[l].pop_bytes;
   }
   out->steps_done = g.steps_done;
+  out->lattice = g.q;
   return LBM_OK;
 }
 
@@ -561,7 +546,8 @@ lbm_status lbm_init_equilibrium(lbm_grid* h, int level, const double* rho, const
   const size_t n = (size_t)L.nx * L.ny * L.nz;
   cudaStream_t s = g.stream;
   if (device_ptrs) {
-    lbm_status st = launch_init_equilibrium(g, L, rho, u, s);
+    lbm_status st = g.q == 27 ? q27::launch_init_equilibrium(g, L, rho, u, s)
+                              : q19::launch_init_equilibrium(g, L, rho, u, s);
     if (st) return st;
     LBM_CUDA(cudaStreamSynchronize(s));
     return LBM_OK;
@@ -570,8 +556,10 @@ lbm_status lbm_init_equilibrium(lbm_grid* h, int level, const double* rho, const
   if (!dr.p || !du.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
   if (rho) LBM_CUDA(cudaMemcpyAsync(dr.p, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
   if (u) LBM_CUDA(cudaMemcpyAsync(du.p, u, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-  lbm_status st = launch_init_equilibrium(g, L, rho ? (double*)dr.p : nullptr,
-                                          u ? (double*)du.p : nullptr, s);
+  const double* rp = rho ? (const double*)dr.p : nullptr;
+  const double* up = u ? (const double*)du.p : nullptr;
+  lbm_status st = g.q == 27 ? q27::launch_init_equilibrium(g, L, rp, up, s)
+                            : q19::launch_init_equilibrium(g, L, rp, up, s);
   if (st) return st;
   LBM_CUDA(cudaStreamSynchronize(s));
   return LBM_OK;
@@ -593,8 +581,10 @@ lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
     }
   }
   for (int k = 0; k < n_steps; ++k) {
-    lbm_status st = g.kind == 0   ? dense_step(g, g.lv[0], s)
-                    : g.kind == 1 ? sparse_step(g, g.lv[0], s)
+    lbm_status st = g.kind == 0   ? (g.q == 27 ? q27::dense_step(g, g.lv[0], s)
+                                               : q19::dense_step(g, g.lv[0], s))
+                    : g.kind == 1 ? (g.q == 27 ? q27::sparse_step(g, g.lv[0], s)
+                                               : q19::sparse_step(g, g.lv[0], s))
                                   : multires_step(g, s);
     if (st) return st;
     ++g.steps_done;
@@ -626,13 +616,17 @@ lbm_status lbm_get_moments(lbm_grid* h, int level, double* rho, double* u, int d
   const size_t n = (size_t)L.nx * L.ny * L.nz;
   cudaStream_t s = g.stream;
   if (device_ptrs) {
-    if ((st = launch_moments(g, L, rho, u, s))) return st;
+    if ((st = g.q == 27 ? q27::launch_moments(g, L, rho, u, s)
+                        : q19::launch_moments(g, L, rho, u, s)))
+      return st;
     LBM_CUDA(cudaStreamSynchronize(s));
     return LBM_OK;
   }
   Scratch dr(g, rho ? n * sizeof(double) : 16, s), du(g, u ? 3 * n * sizeof(double) : 16, s);
   if (!dr.p || !du.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
-  if ((st = launch_moments(g, L, rho ? (double*)dr.p : nullptr, u ? (double*)du.p : nullptr, s)))
+  double* rp = rho ? (double*)dr.p : nullptr;
+  double* up = u ? (double*)du.p : nullptr;
+  if ((st = g.q == 27 ? q27::launch_moments(g, L, rp, up, s) : q19::launch_moments(g, L, rp, up, s)))
     return st;
   if (rho) LBM_CUDA(cudaMemcpyAsync(rho, dr.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (u) LBM_CUDA(cudaMemcpyAsync(u, du.p, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -674,16 +668,19 @@ lbm_status lbm_get_populations_f64(lbm_grid* h, int level, double* dst, int devi
   lbm_status st = lbm_sync(h);
   if (st) return st;
   Level& L = g.lv[level];
-  const size_t n = (size_t)L.nx * L.ny * L.nz * Q;
+  const size_t n = (size_t)L.nx * L.ny * L.nz * g.q;
   cudaStream_t s = g.stream;
   if (device_ptrs) {
-    if ((st = launch_decode_f64(g, L, dst, s))) return st;
+    if ((st = g.q == 27 ? q27::launch_decode_f64(g, L, dst, s) : q19::launch_decode_f64(g, L, dst, s)))
+      return st;
     LBM_CUDA(cudaStreamSynchronize(s));
     return LBM_OK;
   }
   Scratch d(g, n * sizeof(double), s);
   if (!d.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
-  if ((st = launch_decode_f64(g, L, (double*)d.p, s))) return st;
+  if ((st = g.q == 27 ? q27::launch_decode_f64(g, L, (double*)d.p, s)
+                      : q19::launch_decode_f64(g, L, (double*)d.p, s)))
+    return st;
   LBM_CUDA(cudaMemcpyAsync(dst, d.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
   LBM_CUDA(cudaStreamSynchronize(s));
   return LBM_OK;
@@ -775,7 +772,9 @@ lbm_status lbm_conservation(lbm_grid* h, double out[4]) {
   Grid& g = h->g;
   lbm_status st = lbm_sync(h);
   if (st) return st;
-  if ((st = launch_conservation(g, g.sums_d, g.stream))) return st;
+  if ((st = g.q == 27 ? q27::launch_conservation(g, g.sums_d, g.stream)
+                      : q19::launch_conservation(g, g.sums_d, g.stream)))
+    return st;
   LBM_CUDA(cudaMemcpyAsync(out, g.sums_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, g.stream));
   LBM_CUDA(cudaStreamSynchronize(g.stream));
   for (int k = 0; k < 4; ++k)

@@ -251,6 +251,7 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
     }
     const char* why = nullptr;
     if (g.kind == 2) why = "multi-resolution grids cannot join a batch";
+    else if (g.q != 19) why = "batches are D3Q19";
     else if (g.phys.storage != b->storage || g.phys.collision != b->collision)
       why = "all cases need the same storage and collision";
     else if (L.n_reg > 0) why = "cases with regularized boundaries cannot join a batch";

@@ -471,7 +471,8 @@ lbm_status lbm_closure_dataset(lbm_grid* h, int r, double tau_coarse, float* fea
   set_error("");
   if (!h || !feats || !targets || r < 1) return fail(LBM_ERR_INVALID, "bad closure_dataset arguments");
   Grid& g = h->g;
-  if (g.kind != 0) return fail(LBM_ERR_UNSUPPORTED, "closure datasets come from dense grids");
+  if (g.kind != 0 || g.q != 19)
+    return fail(LBM_ERR_UNSUPPORTED, "closure datasets come from dense D3Q19 grids");
   Level& L = g.lv[0];
   for (int a = 0; a < 3; ++a)
     if (!g.phys.periodic[a]) return fail(LBM_ERR_UNSUPPORTED, "closure datasets need a periodic box");

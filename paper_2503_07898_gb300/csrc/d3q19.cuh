@@ -1,11 +1,20 @@
-// d3q19.cuh - D3Q19 lattice, storage codecs and per-voxel update math
-// (device side of liblbm).
+// d3q19.cuh - D3Q19 / D3Q27 lattice, storage codecs and per-voxel update
+// math (device side of liblbm).
 //
-// The paper evolves populations f_i along the D3Q19 directions by a fused
+// The lattice is fixed per translation unit by LBM_Q (19 by default, 27 for
+// the second build of the lattice-dependent sources); everything that
+// depends on it lives in namespace lbm::q19 or lbm::q27, which the rest of
+// namespace lbm sees through a using-directive.  Velocity tables hold the
+// 27 directions of D3Q27, whose first 19 are D3Q19 in the same order; odd i
+// >= 1 has its opposite at i + 1.
+//
+// The paper evolves populations f_i along the D3Q19 or D3Q27 directions
+// (Sec. 6 uses both lattices) by a fused
 // collide-and-stream update with BGK collision (Sec. 6), halfway bounce-back
 // on obstacles (Sec. 6.2) and regularized inflow / outflow boundaries
-// (Sec. 6.2, "register-heavy", 3Q live populations).  It does not write the
-// formulas; this file uses the standard forms of the references it cites:
+// (Sec. 6.2: they keep 3Q populations live, hence many registers).  It does
+// not write the formulas; this file uses the standard forms of the
+// references it cites:
 //   f_i^eq   = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
 //   BGK      f* = g + omega (f^eq - g),                 omega = 1 / tau
 //   REG      f* = f^eq + (1 - omega) 9/2 w_i Q_i : Pi^neq
@@ -25,33 +34,37 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#ifndef LBM_Q
+#define LBM_Q 19
+#endif
+#if LBM_Q == 19
+#define LBM_LNS q19
+#elif LBM_Q == 27
+#define LBM_LNS q27
+#else
+#error "LBM_Q must be 19 or 27"
+#endif
+
 namespace lbm {
 
-constexpr int Q = 19;
 // Lattice tables as constexpr accessors, usable in host and device code
-// (unrolled loops fold them to immediates).
+// (unrolled loops fold them to immediates); index < Q of the lattice in use.
 __host__ __device__ constexpr int cx(int i) {
-  constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0,
+                         1, -1, 1, -1, 1, -1, -1, 1};
   return t[i];
 }
 __host__ __device__ constexpr int cy(int i) {
-  constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1,
+                         1, -1, 1, -1, -1, 1, 1, -1};
   return t[i];
 }
 __host__ __device__ constexpr int cz(int i) {
-  constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+  constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1,
+                         1, -1, -1, 1, 1, -1, 1, -1};
   return t[i];
 }
-__host__ __device__ constexpr int opp(int i) {
-  constexpr int t[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
-  return t[i];
-}
-__host__ __device__ constexpr float wf(int i) {
-  return i == 0 ? 1.f / 3.f : (i <= 6 ? 1.f / 18.f : 1.f / 36.f);
-}
-__host__ __device__ constexpr double wd(int i) {
-  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i & 1 ? i + 1 : i - 1); }
 
 // Flag byte.
 constexpr int T_FLUID = 0, T_SOLID = 1, T_VELOCITY = 2, T_PRESSURE = 3, T_OUTSIDE = 7;
@@ -65,23 +78,46 @@ __host__ __device__ inline bool type_regularized(int t) {
   return t == T_VELOCITY || t == T_PRESSURE;
 }
 
+// Compile-time loop: body(integral_constant<int, I>) for I = 0..N-1.
+template <int I> struct IC { static constexpr int value = I; };
+template <int N, int I = 0, class F> __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(IC<I>{});
+    static_for<N, I + 1>(f);
+  }
+}
+
+enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
+
+namespace LBM_LNS {
+
+constexpr int Q = LBM_Q;
+// weights: D3Q19 1/3, 1/18 (axis), 1/36 (edge); D3Q27 8/27, 2/27, 1/54,
+// 1/216 (corner)
+__host__ __device__ constexpr double wd(int i) {
+  return Q == 19 ? (i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0))
+                 : (i == 0 ? 8.0 / 27.0 : (i <= 6 ? 2.0 / 27.0 : (i <= 18 ? 1.0 / 54.0 : 1.0 / 216.0)));
+}
+__host__ __device__ constexpr float wf(int i) { return (float)wd(i); }
+
 // ------------------------------------------------------------ storage codecs
 // F32 stores f_i.  F16 / BF16 store s_i = f_i - w_i rounded to nearest even.
 // load<I> returns the shifted value s_i in FP32, store<I> takes it; abs_d
 // returns the absolute f_i in FP64 (moments, reductions).
-enum Storage { S_F32 = 0, S_F16 = 1, S_BF16 = 2 };
 
 template <int S> struct Codec;
 template <> struct Codec<S_F32> {
   using T = float;
   template <int I> __device__ static __forceinline__ float load(T v) { return v - wf(I); }
   template <int I> __device__ static __forceinline__ T store(float s) { return wf(I) + s; }
+  __device__ static __forceinline__ float load_rt(T v, int i) { return v - wf(i); }
   __device__ static __forceinline__ double abs_d(T v, int) { return (double)v; }
   __device__ static __forceinline__ T from_double(double f, int) { return (float)f; }
 };
 template <> struct Codec<S_F16> {
   using T = __half;
   template <int I> __device__ static __forceinline__ float load(T v) { return __half2float(v); }
+  __device__ static __forceinline__ float load_rt(T v, int) { return __half2float(v); }
   template <int I> __device__ static __forceinline__ T store(float s) { return __float2half_rn(s); }
   __device__ static __forceinline__ double abs_d(T v, int i) {
     return wd(i) + (double)__half2float(v);
@@ -95,6 +131,7 @@ template <> struct Codec<S_BF16> {
   template <int I> __device__ static __forceinline__ float load(T v) {
     return __bfloat162float(v);
   }
+  __device__ static __forceinline__ float load_rt(T v, int) { return __bfloat162float(v); }
   template <int I> __device__ static __forceinline__ T store(float s) {
     return __float2bfloat16_rn(s);
   }
@@ -105,15 +142,6 @@ template <> struct Codec<S_BF16> {
     return __double2bfloat16(f - wd(i));
   }
 };
-
-// Compile-time loop: body(integral_constant<int, I>) for I = 0..N-1.
-template <int I> struct IC { static constexpr int value = I; };
-template <int N, int I = 0, class F> __device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(IC<I>{});
-    static_for<N, I + 1>(f);
-  }
-}
 
 // ------------------------------------------------------------ collision
 // Every function below takes and returns shifted populations s_i = f_i - w_i.
@@ -186,18 +214,23 @@ __device__ __forceinline__ void collide(float s[Q], float omega) {
     // The pair (i, opp(i)) = (i, i + 1) shares the even part of the shifted
     // equilibrium: E = sym +- asym with sym = w (drho + rho (9/2 (c.u)^2 -
     // 3/2 u.u)) and asym = 3 w rho c.u, c = c_i; w rho, w drho and 3 w rho
-    // are formed once per weight class.  e sums exactly the E values used,
-    // so the rest population closes the mass as in the unpaired form.
-    const float rf = rho * (1.f / 18.f), df = drho * (1.f / 18.f), af = rho * (3.f / 18.f);
-    const float rd = rho * (1.f / 36.f), dd = drho * (1.f / 36.f), ad = rho * (3.f / 36.f);
+    // are formed once per weight class (axis, edge, corner).  e sums exactly
+    // the E values used, so the rest population closes the mass as in the
+    // unpaired form.
+    constexpr float W1 = wf(1), W2 = wf(7), W3 = Q == 27 ? wf(Q - 1) : 0.f;
+    constexpr float A1 = (float)(3.0 * wd(1)), A2 = (float)(3.0 * wd(7));
+    constexpr float A3 = Q == 27 ? (float)(3.0 * wd(Q - 1)) : 0.f;
+    const float r1 = rho * W1, d1 = drho * W1, a1 = rho * A1;
+    const float r2 = rho * W2, d2 = drho * W2, a2 = rho * A2;
+    const float r3 = rho * W3, d3 = drho * W3, a3 = rho * A3;
     float e = 0.f;
     static_for<(Q - 1) / 2>([&](auto pc) {
       constexpr int i = 2 * decltype(pc)::value + 1, o = i + 1;
-      constexpr bool face = i < 7;
+      constexpr int cls = i < 7 ? 1 : (i < 19 ? 2 : 3);
       const float cu = (float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz;
       const float t = 4.5f * cu * cu - usq15;
-      const float sym = face ? fmaf(rf, t, df) : fmaf(rd, t, dd);
-      const float asym = (face ? af : ad) * cu;
+      const float sym = cls == 1 ? fmaf(r1, t, d1) : (cls == 2 ? fmaf(r2, t, d2) : fmaf(r3, t, d3));
+      const float asym = (cls == 1 ? a1 : (cls == 2 ? a2 : a3)) * cu;
       const float Ei = sym + asym, Eo = sym - asym;
       e += Ei + Eo;
       s[i] = s[i] + omega * (Ei - s[i]);
@@ -298,4 +331,6 @@ __device__ __forceinline__ double feq_d(int i, double rho, double ux, double uy,
   return wd(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
 }
 
+}  // namespace LBM_LNS
+using namespace LBM_LNS;
 }  // namespace lbm

@@ -22,6 +22,7 @@
 #include "grid.h"
 
 namespace lbm {
+namespace LBM_LNS {
 
 template <int S, int COLL, class IDX>
 __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
@@ -277,6 +278,34 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
   return LBM_OK;
 }
 
+void dense_wall_mask(const Grid& g, const Level& L, std::vector<uint32_t>& wm) {
+  const int* per = g.phys.periodic;
+  const int n[3] = {L.nx, L.ny, L.nz};
+  wm.assign((size_t)L.n_slots, 0u);
+  for (int z = 0; z < L.nz; ++z)
+    for (int y = 0; y < L.ny; ++y)
+      for (int x = 0; x < L.nx; ++x) {
+        const int64_t v = x + (int64_t)L.nx * (y + (int64_t)L.ny * z);
+        const int t = flag_type(L.flags_h[(size_t)v]);
+        uint32_t m = 0;
+        if (!type_updated(t)) m |= WM_SKIP;
+        if (type_regularized(t)) m |= WM_REG;
+        for (int i = 1; i < Q; ++i) {
+          int sc[3] = {x - cx(i), y - cy(i), z - cz(i)};
+          bool wall = false;
+          for (int a = 0; a < 3; ++a)
+            if (sc[a] < 0 || sc[a] >= n[a]) {
+              if (per[a]) sc[a] = (sc[a] + n[a]) % n[a];
+              else wall = true;
+            }
+          if (!wall)
+            wall = type_wall(flag_type(L.flags_h[(size_t)(sc[0] + (int64_t)L.nx * (sc[1] + (int64_t)L.ny * sc[2]))]));
+          if (wall) m |= 1u << i;
+        }
+        wm[(size_t)v] = m;
+      }
+}
+
 lbm_status dense_step(Grid& g, Level& L, cudaStream_t s) {
   const int st = g.phys.storage, co = g.phys.collision;
   if (st == S_F32) return co == C_BGK ? dense_step_t<S_F32, C_BGK>(g, L, s)
@@ -286,4 +315,5 @@ lbm_status dense_step(Grid& g, Level& L, cudaStream_t s) {
   return co == C_BGK ? dense_step_t<S_BF16, C_BGK>(g, L, s) : dense_step_t<S_BF16, C_REG>(g, L, s);
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

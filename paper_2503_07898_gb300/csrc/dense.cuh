@@ -5,6 +5,7 @@
 #include "grid.h"
 
 namespace lbm {
+namespace LBM_LNS {
 
 constexpr uint32_t WM_REG = 1u << 30;   // voxel belongs to the boundary group
 constexpr uint32_t WM_SKIP = 1u << 31;  // voxel not updated
@@ -95,4 +96,5 @@ __device__ __forceinline__ void store_all(typename Codec<S>::T* __restrict__ fou
   });
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

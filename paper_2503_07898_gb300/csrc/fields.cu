@@ -3,12 +3,13 @@
 //
 // A voxel (x, y, z) of a level's virtual box maps to storage as
 //   dense : index(pop) = pop * N + v,                 v = x + nx (y + ny z)
-//   sparse: index(pop) = (b * 19 + pop) * E^3 + l,    b = block id from the
+//   sparse: index(pop) = (b * Q + pop) * E^3 + l,     b = block id from the
 //           virtual block map, l = lx + E (ly + E lz)
 #include "d3q19.cuh"
 #include "grid.h"
 
 namespace lbm {
+namespace LBM_LNS {
 
 struct LevelDev {
   int nx, ny, nz, E, nbx, nby, nbz;
@@ -282,4 +283,5 @@ lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s) {
   return LBM_OK;
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

@@ -89,6 +89,7 @@ struct ProfRec {
 
 struct Grid {
   int kind = 0;  // 0 dense, 1 sparse, 2 multires
+  int q = 19;    // lattice: 19 (D3Q19) or 27 (D3Q27)
   lbm_physics phys{};
   lbm_allocator alloc{};
   bool have_alloc = false;
@@ -127,19 +128,31 @@ void prof_end(Grid& g, cudaStream_t s, int rec);
 void prof_clear(Grid& g);
 
 // Kernel launchers (defined in the .cu files) -------------------------------
-lbm_status dense_step(Grid& g, Level& L, cudaStream_t s);
-lbm_status sparse_step(Grid& g, Level& L, cudaStream_t s);
-// sparse fused kernel over blocks [b0, b1) of L with relaxation omega (no walls)
-lbm_status sparse_uniform_range(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin,
-                                void* fout, float omega, cudaStream_t s, const char* name,
-                                int64_t units);
+// dense.cu, sparse.cu and fields.cu are built once per lattice, into
+// namespace q19 (D3Q19) and q27 (D3Q27); the host code picks by Grid::q.
+#define LBM_LATTICE_LAUNCHERS                                                              \
+  lbm_status dense_step(Grid& g, Level& L, cudaStream_t s);                                \
+  /* per-voxel wall mask of a dense level (bits 1..Q-1 wall sources, 30 regularized, */  \
+  /* 31 not updated) from L.flags_h */                                                    \
+  void dense_wall_mask(const Grid& g, const Level& L, std::vector<uint32_t>& wm);         \
+  lbm_status sparse_step(Grid& g, Level& L, cudaStream_t s);                               \
+  /* sparse fused kernel over blocks [b0, b1) of L with relaxation omega (no walls) */   \
+  lbm_status sparse_uniform_range(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin, \
+                                  void* fout, float omega, cudaStream_t s, const char* name,  \
+                                  int64_t units);                                             \
+  lbm_status launch_init_equilibrium(Grid& g, Level& L, const double* rho, const double* u,  \
+                                     cudaStream_t s);                                         \
+  lbm_status launch_moments(Grid& g, Level& L, double* rho, double* u, cudaStream_t s);     \
+  lbm_status launch_decode_f64(Grid& g, Level& L, double* dst, cudaStream_t s);             \
+  lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s);
+namespace q19 {
+LBM_LATTICE_LAUNCHERS
+}
+namespace q27 {
+LBM_LATTICE_LAUNCHERS
+}
 lbm_status multires_build(Grid& g, const int finest[3], int n_levels, const uint8_t* level_map);
 lbm_status multires_step(Grid& g, cudaStream_t s);
-lbm_status launch_init_equilibrium(Grid& g, Level& L, const double* rho, const double* u,
-                                   cudaStream_t s);
-lbm_status launch_moments(Grid& g, Level& L, double* rho, double* u, cudaStream_t s);
-lbm_status launch_decode_f64(Grid& g, Level& L, double* dst, cudaStream_t s);
-lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s);
 
 }  // namespace lbm
 

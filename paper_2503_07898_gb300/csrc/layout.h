@@ -5,9 +5,15 @@
 namespace lbm {
 
 // Classification and mapping of a block-sparse level from L.flags_h
-// (virtual box) and L.E: active blocks, boundary-first Morton numbering,
-// neighbour table, virtual block map, per-slot flags.
+// (virtual box) and L.E: active blocks, boundary-first (or, bitmask
+// grouping, plain) Morton numbering, neighbour table, virtual block map,
+// per-slot flags and wall masks (built per lattice).
+namespace q19 {
 lbm_status sparse_build(Grid& g, Level& L);
+}
+namespace q27 {
+lbm_status sparse_build(Grid& g, Level& L);
+}
 // Upload the level's tables to the device.
 lbm_status sparse_upload(Grid& g, Level& L);
 // Boundary values of the regularized voxels (flag-scan order) -> boundary

@@ -194,10 +194,20 @@ __device__ __forceinline__ bool mr_owns(const MrLv& v, int x, int y, int z) {
   return v.bmap[(x >> 3) + v.nbx * ((y >> 3) + v.nby * (z >> 3))] >= 0;
 }
 
-// Population I at a (wrapped) voxel of a level; a miss is an internal error
+// Velocity components by runtime index: the interface rules below run for a
+// few populations of a few voxels only, so they take the direction as a
+// runtime value and exist once in the kernel instead of once per direction.
+#define MR_ROW(f)                                                                        \
+  {f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), \
+   f(14), f(15), f(16), f(17), f(18)}
+static_assert(Q == 19, "multi-resolution grids are D3Q19");
+__constant__ int8_t mr_c[3][Q] = {MR_ROW(cx), MR_ROW(cy), MR_ROW(cz)};
+#undef MR_ROW
+
+// Population i at a (wrapped) voxel of a level; a miss is an internal error
 // (recorded, value 0) rather than an out-of-bounds access.
-template <int S, int I>
-__device__ __forceinline__ float mr_load(const void* buf, const MrLv& v, int x, int y, int z,
+template <int S>
+__device__ __forceinline__ float mr_load(const void* buf, const MrLv& v, int x, int y, int z, int i,
                                          int* status) {
   using T = typename Codec<S>::T;
   const int b = v.bmap[(x >> 3) + v.nbx * ((y >> 3) + v.nby * (z >> 3))];
@@ -205,39 +215,43 @@ __device__ __forceinline__ float mr_load(const void* buf, const MrLv& v, int x, 
     atomicExch(status, (int)LBM_ERR_INTERNAL);
     return 0.f;
   }
-  const int64_t idx = ((int64_t)b * Q + I) * 512 + (x & 7) + 8 * ((y & 7) + 8 * (z & 7));
-  return Codec<S>::template load<I>(((const T*)buf)[idx]);
+  const int64_t idx = ((int64_t)b * Q + i) * 512 + (x & 7) + 8 * ((y & 7) + 8 * (z & 7));
+  return Codec<S>::load_rt(((const T*)buf)[idx], i);
 }
 
-// Explosion: this (finer) level pulls population I of voxel G from a coarser region.
-template <int S, int I>
-__device__ __forceinline__ float explosion(const MrArgs& a, int gx, int gy, int gz) {
-  const int qx = wrapd(gx - cx(I), a.me.nx), qy = wrapd(gy - cy(I), a.me.ny),
-            qz = wrapd(gz - cz(I), a.me.nz);
-  if (a.k == 1) return mr_load<S, I>(a.ccur, a.co, qx >> 1, qy >> 1, qz >> 1, a.status);
-  const int rx = wrapd(qx - cx(I), a.me.nx), ry = wrapd(qy - cy(I), a.me.ny),
-            rz = wrapd(qz - cz(I), a.me.nz);
-  if (mr_owns(a.me, rx, ry, rz)) return mr_load<S, I>(a.prev, a.me, rx, ry, rz, a.status);
-  return mr_load<S, I>(a.ccur, a.co, rx >> 1, ry >> 1, rz >> 1, a.status);
+// Explosion: this (finer) level pulls population i (velocity c) of voxel G
+// from a coarser region.
+template <int S>
+__device__ __forceinline__ float explosion(const MrArgs& a, int i, int ccx, int ccy, int ccz,
+                                           int gx, int gy, int gz) {
+  const int qx = wrapd(gx - ccx, a.me.nx), qy = wrapd(gy - ccy, a.me.ny),
+            qz = wrapd(gz - ccz, a.me.nz);
+  if (a.k == 1) return mr_load<S>(a.ccur, a.co, qx >> 1, qy >> 1, qz >> 1, i, a.status);
+  const int rx = wrapd(qx - ccx, a.me.nx), ry = wrapd(qy - ccy, a.me.ny),
+            rz = wrapd(qz - ccz, a.me.nz);
+  if (mr_owns(a.me, rx, ry, rz)) return mr_load<S>(a.prev, a.me, rx, ry, rz, i, a.status);
+  return mr_load<S>(a.ccur, a.co, rx >> 1, ry >> 1, rz >> 1, i, a.status);
 }
 
-// Coalescence: this (coarser) level pulls population I of voxel G as the mean
+// Coalescence: this (coarser) level pulls population i of voxel G as the mean
 // over its 8 subcells of what they receive in the second finer substep.
-template <int S, int I>
-__device__ __forceinline__ float coalescence(const MrArgs& a, int gx, int gy, int gz) {
+template <int S>
+__device__ __forceinline__ float coalescence(const MrArgs& a, int i, int ccx, int ccy, int ccz,
+                                             int gx, int gy, int gz) {
   float v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const int rx = wrapd(2 * gx + (j & 1) - cx(I), a.fi.nx);
-    const int ry = wrapd(2 * gy + ((j >> 1) & 1) - cy(I), a.fi.ny);
-    const int rz = wrapd(2 * gz + (j >> 2) - cz(I), a.fi.nz);
+    const int rx = wrapd(2 * gx + (j & 1) - ccx, a.fi.nx);
+    const int ry = wrapd(2 * gy + ((j >> 1) & 1) - ccy, a.fi.ny);
+    const int rz = wrapd(2 * gz + (j >> 2) - ccz, a.fi.nz);
     if (mr_owns(a.fi, rx, ry, rz)) {
-      v[j] = mr_load<S, I>(a.ff1, a.fi, rx, ry, rz, a.status);
+      v[j] = mr_load<S>(a.ff1, a.fi, rx, ry, rz, i, a.status);
     } else {
-      const int sx = wrapd(rx - cx(I), a.fi.nx), sy = wrapd(ry - cy(I), a.fi.ny),
-                sz = wrapd(rz - cz(I), a.fi.nz);
-      v[j] = mr_owns(a.fi, sx, sy, sz) ? mr_load<S, I>(a.ff0, a.fi, sx, sy, sz, a.status)
-                                       : mr_load<S, I>(a.cur, a.me, sx >> 1, sy >> 1, sz >> 1, a.status);
+      const int sx = wrapd(rx - ccx, a.fi.nx), sy = wrapd(ry - ccy, a.fi.ny),
+                sz = wrapd(rz - ccz, a.fi.nz);
+      v[j] = mr_owns(a.fi, sx, sy, sz)
+                 ? mr_load<S>(a.ff0, a.fi, sx, sy, sz, i, a.status)
+                 : mr_load<S>(a.cur, a.me, sx >> 1, sy >> 1, sz >> 1, i, a.status);
     }
   }
   // pairwise means along x, then y, then z (exact when the 8 values are equal)
@@ -266,10 +280,11 @@ template <> struct TmpCodec<S_F32> {
 };
 
 template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
-__global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
+__global__ void __launch_bounds__(256, CLOSURE ? 1 : 4) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;
   const int64_t b = a.b0 + blockIdx.x / 2;
   extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
+  __shared__ float mr_slow[Q][256];  // per-thread values of pulls that leave the level
   if (b >= a.b1) return;  // uniform per CTA
   if constexpr (CLOSURE) {
     closure_load_smem(reinterpret_cast<ClosureCta*>(mr_dyn_smem)->w, a.cp);
@@ -295,14 +310,14 @@ __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
   const int xp = (lx - 1) & 7, xn = (lx + 1) & 7;
   const int yp = ((ly - 1) & 7) * 8, yn = ((ly + 1) & 7) * 8, y0 = ly * 8;
   const int zp = ((lz - 1) & 7) * 64, zn = ((lz + 1) & 7) * 64, z0 = lz * 64;
-  float g[Q];
-  static_for<Q>([&](auto ic) {
+  // the source block of pull I, and whether it lies on this level
+  auto source = [&](auto ic, int& nb) -> bool {
     constexpr int I = decltype(ic)::value;
     constexpr int X = cx(I), Y = cy(I), Z = cz(I);
     const bool kx = X != 0 && ex == -X;
     const bool ky = Y != 0 && ey == -Y;
     const bool kz = Z != 0 && ez == -Z;
-    int nb = bb;
+    nb = bb;
     if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : bb);
     else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : bb);
     else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : bb);
@@ -319,14 +334,36 @@ __global__ void __launch_bounds__(256) mr_interface(MrArgs a) {
         if (kz && nZ < 0) plain = false;
       }
     }
-    if (plain) {
+    return plain;
+  };
+  // 1. directions whose pull leaves the level
+  uint32_t cross = 0u;
+  static_for<Q>([&](auto ic) {
+    int nb;
+    if (!source(ic, nb)) cross |= 1u << decltype(ic)::value;
+  });
+  // 2. their values by explosion (from the coarser level) or coalescence
+  // (from the finer one), one direction at a time, parked in this thread's
+  // column of shared memory so that no population is live across the loop
+  for (uint32_t m = cross; m; m &= m - 1) {
+    const int i = __ffs(m) - 1;
+    const int ccx = mr_c[0][i], ccy = mr_c[1][i], ccz = mr_c[2][i];
+    mr_slow[i][threadIdx.x] = jmp == 2 ? explosion<S>(a, i, ccx, ccy, ccz, gx, gy, gz)
+                                       : coalescence<S>(a, i, ccx, ccy, ccz, gx, gy, gz);
+  }
+  // 3. the same-level pulls
+  float g[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+    int nb;
+    source(ic, nb);
+    if ((cross >> I) & 1u) {
+      g[I] = mr_slow[I][threadIdx.x];
+    } else {
       const int ls = (X > 0 ? xp : (X < 0 ? xn : lx)) + (Y > 0 ? yp : (Y < 0 ? yn : y0)) +
                      (Z > 0 ? zp : (Z < 0 ? zn : z0));
       g[I] = Codec<S>::template load<I>(cur[(int64_t)nb * (Q * 512) + (I * 512 + ls)]);
-    } else if (jmp == 2) {
-      g[I] = explosion<S, I>(a, gx, gy, gz);
-    } else {
-      g[I] = coalescence<S, I>(a, gx, gy, gz);
     }
   });
   if constexpr (SPLIT) {

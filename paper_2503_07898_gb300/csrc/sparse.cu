@@ -8,9 +8,9 @@
 //                  count (Sec. 6.2).
 //   classification G_b = boundary blocks, G_nb = the rest.
 //   mapping        G_b stored first, then G_nb; inside each group blocks
-//                  follow the Morton curve of their coordinates (Sec. 4:
-//                  block-sparse grids "commonly managed by space-filling
-//                  curves").  Storage ((b * 19) + pop) * E^3 + l.
+//                  follow the Morton curve of their coordinates (Sec. 4
+//                  orders blocks along a space-filling curve without
+//                  naming one).  Storage ((b * Q) + pop) * E^3 + l.
 //   operations     sparse_kernel<MODE_INTERIOR> on G_nb (lean, 2Q, bounded
 //                  registers); sparse_kernel<MODE_BOUNDARY> on G_b; both
 //                  with direct indexing and no per-voxel boundary storage
@@ -33,6 +33,8 @@
 
 namespace lbm {
 
+#if LBM_Q == 19
+// Lattice-independent host code, compiled once (D3Q19 build).
 // ------------------------------------------------------------- host layout
 
 static uint32_t spread3(uint32_t v) {
@@ -47,6 +49,89 @@ static uint32_t spread3(uint32_t v) {
 uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
 }
+
+lbm_status sparse_upload(Grid& g, Level& L) {
+  auto up = [&](int32_t** dst, const std::vector<int32_t>& src) -> lbm_status {
+    *dst = (int32_t*)g.dalloc(src.size() * 4 + 4, g.stream);
+    if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
+    if (!src.empty()) LBM_CUDA(cudaMemcpy(*dst, src.data(), src.size() * 4, cudaMemcpyHostToDevice));
+    return LBM_OK;
+  };
+  lbm_status st;
+  if ((st = up(&L.nbr_d, L.nbr_h)) || (st = up(&L.bmap_d, L.bmap_h))) return st;
+  return LBM_OK;
+}
+
+// Regularized voxels in flag-scan order -> (slot, k).
+template <class F> static void for_each_reg(const Level& L, F&& fn) {
+  const int E = L.E;
+  const int64_t E3 = (int64_t)E * E * E;
+  int64_t k = 0;
+  for (int z = 0; z < L.nz; ++z)
+    for (int y = 0; y < L.ny; ++y)
+      for (int x = 0; x < L.nx; ++x) {
+        const uint8_t f = L.flags_h[x + (size_t)L.nx * (y + (size_t)L.ny * z)];
+        if (!type_regularized(flag_type(f))) continue;
+        const int b = L.bmap_h[x / E + (size_t)L.nbx * (y / E + (size_t)L.nby * (z / E))];
+        const int64_t slot = (int64_t)b * E3 + (x % E) + E * ((y % E) + E * (z % E));
+        fn(slot, k++);
+      }
+}
+
+lbm_status sparse_set_bc(Grid& g, Level& L, const float* bc_values, const float* def_bc) {
+  if (L.n_reg > 0 && !bc_values && !def_bc)
+    return fail(LBM_ERR_INVALID, "regularized voxels need bc_values or default_bc");
+  const int64_t E3 = (int64_t)L.E * L.E * L.E;
+  L.bc_h.assign((size_t)L.n_reg * 4, 0.f);
+  if (L.bitmask) {
+    // indirect indexing: a per-slot rank into one compact value per
+    // regularized voxel (flag-scan order)
+    L.bc_idx_h.assign((size_t)L.n_slots, -1);
+    std::vector<float4> cmp((size_t)L.n_reg);
+    for_each_reg(L, [&](int64_t slot, int64_t k) {
+      const float* v = bc_values ? bc_values + k * 4 : def_bc;
+      for (int c = 0; c < 4; ++c) L.bc_h[(size_t)k * 4 + c] = v[c];
+      cmp[(size_t)k] = make_float4(v[0], v[1], v[2], v[3]);
+      L.bc_idx_h[(size_t)slot] = (int32_t)k;
+    });
+    g.dfree(L.bc_idx_d, g.stream);
+    g.dfree(L.bc_cmp_d, g.stream);
+    g.dfree(L.bc_full_d, g.stream);
+    L.bc_full_d = nullptr;
+    L.bc_idx_d = (int32_t*)g.dalloc(L.bc_idx_h.size() * 4 + 4, g.stream);
+    L.bc_cmp_d = (float4*)g.dalloc(cmp.size() * sizeof(float4) + 16, g.stream);
+    if (!L.bc_idx_d || !L.bc_cmp_d) return fail(LBM_ERR_OOM, "device allocation failed");
+    if (!L.bc_idx_h.empty())
+      LBM_CUDA(cudaMemcpy(L.bc_idx_d, L.bc_idx_h.data(), L.bc_idx_h.size() * 4, cudaMemcpyHostToDevice));
+    if (!cmp.empty())
+      LBM_CUDA(cudaMemcpy(L.bc_cmp_d, cmp.data(), cmp.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return LBM_OK;
+  }
+  std::vector<float4> grp((size_t)(L.n_b * E3), make_float4(0.f, 0.f, 0.f, 1.f));
+  for_each_reg(L, [&](int64_t slot, int64_t k) {
+    const float* v = bc_values ? bc_values + k * 4 : def_bc;
+    for (int c = 0; c < 4; ++c) L.bc_h[(size_t)k * 4 + c] = v[c];
+    grp[(size_t)slot] = make_float4(v[0], v[1], v[2], v[3]);
+  });
+  g.dfree(L.bc_grp_d, g.stream);
+  g.dfree(L.bc_full_d, g.stream);
+  L.bc_full_d = nullptr;
+  L.bc_grp_d = (float4*)g.dalloc(grp.size() * sizeof(float4) + 16, g.stream);
+  if (!L.bc_grp_d) return fail(LBM_ERR_OOM, "device allocation failed");
+  if (!grp.empty())
+    LBM_CUDA(cudaMemcpy(L.bc_grp_d, grp.data(), grp.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+void sparse_fill_bc_full(const Level& L, float4* full) {
+  for_each_reg(L, [&](int64_t slot, int64_t k) {
+    full[slot] = make_float4(L.bc_h[k * 4], L.bc_h[k * 4 + 1], L.bc_h[k * 4 + 2], L.bc_h[k * 4 + 3]);
+  });
+}
+
+#endif  // LBM_Q == 19
+
+namespace LBM_LNS {
 
 lbm_status sparse_build(Grid& g, Level& L) {
   const int E = L.E;
@@ -203,85 +288,6 @@ lbm_status sparse_build(Grid& g, Level& L) {
                           cudaMemcpyHostToDevice));
   }
   return LBM_OK;
-}
-
-lbm_status sparse_upload(Grid& g, Level& L) {
-  auto up = [&](int32_t** dst, const std::vector<int32_t>& src) -> lbm_status {
-    *dst = (int32_t*)g.dalloc(src.size() * 4 + 4, g.stream);
-    if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
-    if (!src.empty()) LBM_CUDA(cudaMemcpy(*dst, src.data(), src.size() * 4, cudaMemcpyHostToDevice));
-    return LBM_OK;
-  };
-  lbm_status st;
-  if ((st = up(&L.nbr_d, L.nbr_h)) || (st = up(&L.bmap_d, L.bmap_h))) return st;
-  return LBM_OK;
-}
-
-// Regularized voxels in flag-scan order -> (slot, k).
-template <class F> static void for_each_reg(const Level& L, F&& fn) {
-  const int E = L.E;
-  const int64_t E3 = (int64_t)E * E * E;
-  int64_t k = 0;
-  for (int z = 0; z < L.nz; ++z)
-    for (int y = 0; y < L.ny; ++y)
-      for (int x = 0; x < L.nx; ++x) {
-        const uint8_t f = L.flags_h[x + (size_t)L.nx * (y + (size_t)L.ny * z)];
-        if (!type_regularized(flag_type(f))) continue;
-        const int b = L.bmap_h[x / E + (size_t)L.nbx * (y / E + (size_t)L.nby * (z / E))];
-        const int64_t slot = (int64_t)b * E3 + (x % E) + E * ((y % E) + E * (z % E));
-        fn(slot, k++);
-      }
-}
-
-lbm_status sparse_set_bc(Grid& g, Level& L, const float* bc_values, const float* def_bc) {
-  if (L.n_reg > 0 && !bc_values && !def_bc)
-    return fail(LBM_ERR_INVALID, "regularized voxels need bc_values or default_bc");
-  const int64_t E3 = (int64_t)L.E * L.E * L.E;
-  L.bc_h.assign((size_t)L.n_reg * 4, 0.f);
-  if (L.bitmask) {
-    // indirect indexing: a per-slot rank into one compact value per
-    // regularized voxel (flag-scan order)
-    L.bc_idx_h.assign((size_t)L.n_slots, -1);
-    std::vector<float4> cmp((size_t)L.n_reg);
-    for_each_reg(L, [&](int64_t slot, int64_t k) {
-      const float* v = bc_values ? bc_values + k * 4 : def_bc;
-      for (int c = 0; c < 4; ++c) L.bc_h[(size_t)k * 4 + c] = v[c];
-      cmp[(size_t)k] = make_float4(v[0], v[1], v[2], v[3]);
-      L.bc_idx_h[(size_t)slot] = (int32_t)k;
-    });
-    g.dfree(L.bc_idx_d, g.stream);
-    g.dfree(L.bc_cmp_d, g.stream);
-    g.dfree(L.bc_full_d, g.stream);
-    L.bc_full_d = nullptr;
-    L.bc_idx_d = (int32_t*)g.dalloc(L.bc_idx_h.size() * 4 + 4, g.stream);
-    L.bc_cmp_d = (float4*)g.dalloc(cmp.size() * sizeof(float4) + 16, g.stream);
-    if (!L.bc_idx_d || !L.bc_cmp_d) return fail(LBM_ERR_OOM, "device allocation failed");
-    if (!L.bc_idx_h.empty())
-      LBM_CUDA(cudaMemcpy(L.bc_idx_d, L.bc_idx_h.data(), L.bc_idx_h.size() * 4, cudaMemcpyHostToDevice));
-    if (!cmp.empty())
-      LBM_CUDA(cudaMemcpy(L.bc_cmp_d, cmp.data(), cmp.size() * sizeof(float4), cudaMemcpyHostToDevice));
-    return LBM_OK;
-  }
-  std::vector<float4> grp((size_t)(L.n_b * E3), make_float4(0.f, 0.f, 0.f, 1.f));
-  for_each_reg(L, [&](int64_t slot, int64_t k) {
-    const float* v = bc_values ? bc_values + k * 4 : def_bc;
-    for (int c = 0; c < 4; ++c) L.bc_h[(size_t)k * 4 + c] = v[c];
-    grp[(size_t)slot] = make_float4(v[0], v[1], v[2], v[3]);
-  });
-  g.dfree(L.bc_grp_d, g.stream);
-  g.dfree(L.bc_full_d, g.stream);
-  L.bc_full_d = nullptr;
-  L.bc_grp_d = (float4*)g.dalloc(grp.size() * sizeof(float4) + 16, g.stream);
-  if (!L.bc_grp_d) return fail(LBM_ERR_OOM, "device allocation failed");
-  if (!grp.empty())
-    LBM_CUDA(cudaMemcpy(L.bc_grp_d, grp.data(), grp.size() * sizeof(float4), cudaMemcpyHostToDevice));
-  return LBM_OK;
-}
-
-void sparse_fill_bc_full(const Level& L, float4* full) {
-  for_each_reg(L, [&](int64_t slot, int64_t k) {
-    full[slot] = make_float4(L.bc_h[k * 4], L.bc_h[k * 4 + 1], L.bc_h[k * 4 + 2], L.bc_h[k * 4 + 3]);
-  });
 }
 
 // ------------------------------------------------------------------ kernels
@@ -455,4 +461,5 @@ lbm_status sparse_step(Grid& g, Level& L, cudaStream_t s) {
   }
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

@@ -5,6 +5,7 @@
 #include "d3q19.cuh"
 
 namespace lbm {
+namespace LBM_LNS {
 
 // Pull the 19 populations of voxel l of block b (block edge E) with halfway
 // bounce-back.  nbr27: the block's row of the neighbour table in global
@@ -16,12 +17,13 @@ namespace lbm {
 // mask (bit i = the source of population i bounces back); a block without
 // it pulls with no test at all.
 //
-// Address arithmetic is hoisted out of the 19 pulls: a voxel can only leave
-// its block across the faces it lies on, so the (at most) six blocks a pull
-// can enter — one per face and one per edge between two of them; D3Q19 has
-// no corner velocities — are looked up once, and the source coordinate
-// wrapped into the source block is one of three precomputed values per axis.
-// Each pull then costs a few selects and one 32 x 32 -> 64-bit multiply-add.
+// Address arithmetic is hoisted out of the Q pulls: a voxel can only leave
+// its block across the faces it lies on, so the blocks a pull can enter —
+// one per face, one per edge between two of them and, for D3Q27's corner
+// velocities, the one at the corner of three (six or seven in all) — are
+// looked up once, and the source coordinate wrapped into the source block
+// is one of three precomputed values per axis.  Each pull then costs a few
+// selects and one 32 x 32 -> 64-bit multiply-add.
 template <int S, int E, bool WALLS>
 __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* __restrict__ fin,
                                                     const int32_t* nbr27, uint32_t wm, int b,
@@ -36,6 +38,7 @@ __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* 
   const int nZ = __ldg(nbr27 + 13 + 9 * ez);
   const int nXY = __ldg(nbr27 + 13 + ex + 3 * ey), nXZ = __ldg(nbr27 + 13 + ex + 9 * ez);
   const int nYZ = __ldg(nbr27 + 13 + 3 * ey + 9 * ez);
+  const int nXYZ = Q == 27 ? __ldg(nbr27 + 13 + ex + 3 * ey + 9 * ez) : b;
   // source coordinate inside its block for c = +1, -1 (pre-scaled by the
   // axis stride for y and z)
   const int xp = (lx - 1) & M, xn = (lx + 1) & M;
@@ -49,7 +52,9 @@ __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* 
     const bool ky = Y != 0 && ey == -Y;
     const bool kz = Z != 0 && ez == -Z;
     int nb = b;
-    if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : b);
+    if constexpr (X != 0 && Y != 0 && Z != 0)
+      nb = kz ? (kx ? (ky ? nXYZ : nXZ) : (ky ? nYZ : nZ)) : (kx ? (ky ? nXY : nX) : (ky ? nY : b));
+    else if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : b);
     else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : b);
     else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : b);
     else if constexpr (X != 0) nb = kx ? nX : b;
@@ -75,4 +80,5 @@ __device__ __forceinline__ void sparse_pull_voxel(const typename Codec<S>::T* __
   else sparse_pull_voxel_t<S, E, false>(fin, nbr27, 0u, (int)b, l, g);
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

@@ -27,9 +27,9 @@ def oracle_bc(flags, bc):
 
 
 def make_grid(lbm, kind, flags, bc, tau, collision="bgk", storage="f32",
-              periodic=(0, 0, 0), schedule="disaggregated", block_edge=8):
+              periodic=(0, 0, 0), schedule="disaggregated", block_edge=8, lattice=19):
     nz, ny, nx = flags.shape
-    phys = lbm.physics(tau, collision, storage, periodic, schedule)
+    phys = lbm.physics(tau, collision, storage, periodic, schedule, lattice=lattice)
     if kind == "dense":
         g = lbm.lbm_grid_create_dense((nx, ny, nz), phys)
         lbm.lbm_set_boundary(g, 0, flags, bc_list(flags, bc) if bc is not None else None)
@@ -39,8 +39,8 @@ def make_grid(lbm, kind, flags, bc, tau, collision="bgk", storage="f32",
     return g
 
 
-def run_oracle(flags, bc, rho, u, tau, steps, collision="bgk", periodic=(0, 0, 0)):
-    f = olbm.init_equilibrium(rho, u, flags)
+def run_oracle(flags, bc, rho, u, tau, steps, collision="bgk", periodic=(0, 0, 0), q=19):
+    f = olbm.init_equilibrium(rho, u, flags, q=q)
     obc = oracle_bc(flags, bc) if bc is not None else None
     for _ in range(steps):
         f = olbm.step(f, flags, tau, collision=collision, periodic=periodic, bc=obc)
