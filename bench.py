@@ -30,13 +30,16 @@ BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}   # 19 loads + 19 stores
 METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated error"
 
 # DRAM traffic of the dominant kernel from an ncu capture (profiles/), valid
-# only while the kernel sources hash to the recorded value.
-NCU_TRAFFIC = {}
+# only while the kernel sources hash to the recorded value: the 160^3
+# capture of dense_interior (dram__bytes_read.sum + dram__bytes_write.sum,
+# 4,070,400 updates per launch) scaled by units to one 256^3 launch
+# (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md.
+NCU_TRAFFIC = {"dense_interior": {"bytes_per_launch": 2.349412e+09, "src_sha": "2e631f754389f63b"}}
 
 
 def src_hash():
     h = hashlib.sha256()
-    for f in ("d3q19.cuh", "dense.cu"):
+    for f in ("d3q19.cuh", "dense.cuh", "dense.cu"):
         h.update(open(os.path.join(ROOT, "paper_2503_07898_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -437,10 +440,10 @@ def run_ours(args, rank, world, local_rank):
             vms = a0.elapsed_time(a1)
             lbm.lbm_get_moments(gv, 0, rho_d, u_var)
             l2 = (float(((u_var - u_ref)[:, upd] ** 2).sum()) / u_den) ** 0.5
-            bpu = BYTES_PER_UPDATE[kw["storage"]] * q // 19
+            vbpu = BYTES_PER_UPDATE[kw["storage"]] * q // 19
             variants[name] = {"GLUPS": round(n_upd * kv / (vms * 1e-3) / 1e9, 3),
-                              "roofline_frac": round(n_upd * kv * bpu / (vms * 1e-3) / 1e9 / peak, 4),
-                              "bytes_per_update": bpu,
+                              "roofline_frac": round(n_upd * kv * vbpu / (vms * 1e-3) / 1e9 / peak, 4),
+                              "bytes_per_update": vbpu,
                               ("velocity_l2_vs_f32" if q == 19 else "velocity_l2_vs_d3q19_f32"):
                                   float(f"{l2:.3e}"),
                               "after_steps": 20 + kv}

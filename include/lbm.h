@@ -329,8 +329,9 @@ lbm_status lbm_closure_load(lbm_grid* g, const float* theta, size_t n);
  * (dense: consecutive voxel ids; sparse: half blocks), the steps of one
  * lbm_batch_step call captured once into a CUDA graph and replayed.
  * Cases keep their own state, walls and tau; they must share storage and
- * collision, have no regularized voxels and fewer than 2^31 / 19 voxels
- * (slots) each; otherwise lbm_batch_create returns LBM_ERR_UNSUPPORTED.  A
+ * collision, be D3Q19, have no regularized voxels and fewer than 2^31 / 19
+ * voxels (slots) each, dense cases at most 2047 x 2047 x 1023; otherwise
+ * lbm_batch_create returns LBM_ERR_UNSUPPORTED.  A
  * case may still be used on its own (lbm_get_moments, lbm_step, ...) between
  * batch steps. */
 typedef struct lbm_batch lbm_batch;

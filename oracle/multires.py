@@ -42,8 +42,19 @@ and tau_l; level 0 keeps tau_0.  The network parameters are used as given
 (FP64), so a caller that wants the storage precision of the weights rounds
 them first.
 
+Walls and boundaries (the multi-resolution lid-driven cavity of Sec. 6.3,
+Table 5).  Reading: they lie on the finest level.  Every map cell touching a
+non-periodic box side is owned by level 0, so the coarser levels sit at
+least one coarsest block (8 2^(L-1) finest voxels) away from every wall and
+no explosion / coalescence trace (at most two finest voxels long) reaches
+one.  Level 0 then pulls exactly as the single-resolution oracle does
+(halfway bounce-back at non-periodic box sides and solid voxels,
+regularized velocity / pressure nodes rebuilt after the collision), with
+the pulls whose source a coarser level owns replaced by explosion.
+
 State: f[l] is a (19, nz_l, ny_l, nx_l) array over the whole level-l virtual
-box, zero where level l does not own the region.  The box is periodic.
+box, zero where level l does not own the region (and on level-0 solid
+voxels).  Without walls the box is periodic.
 """
 import numpy as np
 
@@ -78,9 +89,20 @@ class MultiRes:
     """Multi-resolution grid: level_map (Mz, My, Mx) gives the owning level of
     every cube of `cell` finest voxels; cell must be a multiple of 2^(L-1)."""
 
-    def __init__(self, level_map, n_levels, cell, tau0, collision="bgk", theta=None):
+    def __init__(self, level_map, n_levels, cell, tau0, collision="bgk", theta=None,
+                 periodic=(True, True, True), flags0=None, bc0=None):
+        """periodic: per axis (x, y, z); flags0: level-0 flag bytes (solid and
+        regularized voxels, inside the level-0 region); bc0: (4,) + level-0
+        box boundary values of its regularized voxels."""
         level_map = np.asarray(level_map, dtype=np.int64)
         self.theta = None if theta is None else np.asarray(theta, dtype=np.float64)
+        self.periodic = tuple(bool(p) for p in periodic)
+        for a, ax in ((0, 2), (1, 1), (2, 0)):     # map axes are (z, y, x)
+            if not self.periodic[a]:
+                edge = np.concatenate([np.take(level_map, [0], axis=ax).ravel(),
+                                       np.take(level_map, [-1], axis=ax).ravel()])
+                if np.any(edge != 0):
+                    raise ValueError("map cells on a non-periodic side must be level 0")
         assert cell % (2 ** (n_levels - 1)) == 0
         self.L = n_levels
         self.tau0 = tau0
@@ -90,6 +112,13 @@ class MultiRes:
             r = cell // (2 ** lv)
             self.own.append(level_map.repeat(r, 0).repeat(r, 1).repeat(r, 2))
         self.f = [np.zeros((L.Q,) + o.shape) for o in self.own]
+        self.flags0 = (np.zeros(self.own[0].shape, np.uint8) if flags0 is None
+                       else np.asarray(flags0, dtype=np.uint8))
+        if np.any((self.flags0 & 7 != 0) & (self.own[0] != 0)):
+            raise ValueError("walls and boundary nodes must lie in the level-0 region")
+        self.bc0 = None if bc0 is None else np.asarray(bc0, dtype=np.float64)
+        t0 = lbm.flag_type(self.flags0)
+        self.updated0 = (t0 == lbm.FLUID) | (t0 == lbm.VELOCITY) | (t0 == lbm.PRESSURE)
 
     def dims(self, level):
         nz, ny, nx = self.own[level].shape
@@ -97,7 +126,10 @@ class MultiRes:
 
     def init_equilibrium(self, level, rho, u):
         feq = L.equilibrium(rho, u)
-        self.f[level] = np.where(self.own[level][None] == level, feq, 0.0)
+        mine = self.own[level] == level
+        if level == 0:
+            mine = mine & self.updated0
+        self.f[level] = np.where(mine[None], feq, 0.0)
 
     def _neighbour_levels(self, lv):
         own = self.own[lv]
@@ -121,9 +153,12 @@ class MultiRes:
         own = self.own[lv]
         has_finer, _ = self._neighbour_levels(lv)
         g = np.empty_like(S)
+        # level 0 pulls as the single-resolution oracle (walls, solids);
+        # coarser levels never touch a wall
+        base = lbm.stream_with_walls(S, self.flags0, self.periodic) if lv == 0 else None
         for i in range(L.Q):
             c = L.C[i]
-            val = shift(S[i], c)
+            val = base[i] if lv == 0 else shift(S[i], c)
             if lv + 1 < self.L:                       # explosion from level lv+1
                 c_up = upsample(self.f[lv + 1][i])
                 if k == 1:
@@ -148,7 +183,18 @@ class MultiRes:
             tau[mine] = np.maximum(tau[mine] + d_tau, cl.TAU_MIN)
         with np.errstate(invalid="ignore", divide="ignore"):   # unowned voxels hold zeros
             fnew, _, _ = lbm.collide(g, tau, self.collision)
-        self.f[lv] = np.where(own[None] == lv, fnew, 0.0)
+        mine = own == lv
+        if lv == 0:
+            types = lbm.flag_type(self.flags0)
+            normals = lbm.flag_normal(self.flags0)
+            for kind in (lbm.VELOCITY, lbm.PRESSURE):
+                for nrm in range(6):
+                    sel = (types == kind) & (normals == nrm)
+                    if sel.any():
+                        fnew[:, sel], _, _ = lbm.regularized_boundary(
+                            g[:, sel], nrm, self.bc0[:, sel], kind, tau)
+            mine = mine & self.updated0
+        self.f[lv] = np.where(mine[None], fnew, 0.0)
 
     def step(self):
         """One step of the coarsest level (2^(L-1-l) steps of every level l)."""

@@ -105,6 +105,7 @@ static void free_level(Grid& g, Level& L) {
   g.dfree(L.bmap_d, s);
   g.dfree(L.blk_walls_d, s);
   g.dfree(L.bnd_bits_d, s);
+  g.dfree(L.reg_blocks_d, s);
   g.dfree(L.bc_idx_d, s);
   g.dfree(L.bc_cmp_d, s);
   L = Level();
@@ -531,8 +532,9 @@ lbm_status lbm_set_boundary(lbm_grid* h, int level, const uint8_t* flags,
     }
     return LBM_OK;
   }
+  if (g.kind == 2 && level == 0) return multires_set_boundary(g, flags, bc_values, default_bc);
   if (flags && std::memcmp(flags, L.flags_h.data(), nv) != 0)
-    return fail(LBM_ERR_INVALID, "sparse / multi-resolution flags are fixed at creation");
+    return fail(LBM_ERR_INVALID, "sparse flags (and those of multi-resolution levels >= 1) are fixed at creation");
   return sparse_set_bc(g, L, bc_values, default_bc);
 }
 

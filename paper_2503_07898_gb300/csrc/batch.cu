@@ -38,6 +38,7 @@ struct BatchCase {
   float omega;
   float tau;
   int closure;  // learned closure on this case (lbm_batch_closure_load)
+  float inv_nx, inv_ny;  // dense: 1 / nx, 1 / ny (voxel decode)
 };
 
 constexpr int BT = 256;  // threads per CTA = voxels per work item
@@ -67,9 +68,22 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
     if (C.kind == 0) {
       // case sizes are below 2^31 / 19 voxels (checked at creation): 32-bit
       // voxel ids and offsets
-      const int v = (int)t * BT + threadIdx.x;
+      // the item's first voxel, packed x | y << 11 | z << 22; this thread's
+      // voxel follows by carrying across rows and planes with a float
+      // reciprocal (exact: x and y stay below 2^12, so the product's error
+      // is far below the 0.5 / n distance to the next integer)
+      const uint32_t pk = (uint32_t)t;
+      int x = (int)(pk & 2047u) + (int)threadIdx.x, y = (int)((pk >> 11) & 2047u),
+          z = (int)(pk >> 22);
+      int k = (int)(((float)x + 0.5f) * C.inv_nx);
+      x -= k * C.nx;
+      y += k;
+      k = (int)(((float)y + 0.5f) * C.inv_ny);
+      y -= k * C.ny;
+      z += k;
+      const int v = x + C.nx * (y + C.ny * z);
       uint32_t wm = 0u;
-      act = v < C.N;
+      act = z < C.nz;
       if (act && C.wmask) {
         wm = C.wmask[v];
         act = !(wm & (WM_SKIP | WM_REG));
@@ -85,13 +99,9 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
         a.px = C.px;
         a.py = C.py;
         a.pz = C.pz;
-        const int row = v / C.nx;
-        const int x = v - row * C.nx;
-        const int z = row / C.ny;
-        const int y = row - z * C.ny;
-        if (y > 0 && y < C.ny - 1 && z > 0 && z < C.nz - 1) {
-          if (wm) pull_row_interior<S, int, true>(fin, a, x, v, wm, g);
-          else pull_row_interior<S, int, false>(fin, a, x, v, 0u, g);
+        if (lean_row(a, y, z)) {
+          if (wm) pull_row_interior<S, int, true>(fin, a, x, y, z, v, wm, g);
+          else pull_row_interior<S, int, false>(fin, a, x, y, z, v, 0u, g);
         } else {
           pull_all<S>(fin, a, x, y, z, v, wm, g);
         }
@@ -123,10 +133,20 @@ __global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restr
     }
     if (act) {
       collide<COLL>(g, omega);
-      static_for<Q>([&](auto ic) {
-        constexpr int I = decltype(ic)::value;
-        fout[obase + I * ostride] = Codec<S>::template store<I>(g[I]);
-      });
+      // one base pointer; the population stride is a constant for sparse
+      // items (512) and a 32-bit value for dense ones
+      T* __restrict__ o = fout + obase;
+      if (C.kind == 0) {
+        static_for<Q>([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          o[I * ostride] = Codec<S>::template store<I>(g[I]);
+        });
+      } else {
+        static_for<Q>([&](auto ic) {
+          constexpr int I = decltype(ic)::value;
+          o[I * 512] = Codec<S>::template store<I>(g[I]);
+        });
+      }
     }
   }
 }
@@ -169,6 +189,8 @@ struct lbm_batch {
   int64_t n_items = 0;
   int64_t n_plain = 0;                        // items of cases without the closure (listed first)
   std::vector<int32_t> items_per_case;
+  std::vector<int64_t> item_first;      // per case: its first item in creation order
+  std::vector<int32_t> item_local_h;    // per item in creation order: its local code
   int64_t n_updated = 0;
   int storage = 0, collision = 0;
   int n_sm = 1;
@@ -257,6 +279,8 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
     else if (L.n_reg > 0) why = "cases with regularized boundaries cannot join a batch";
     else if (g.kind == 1 && L.E != 8) why = "sparse cases need 8^3 blocks";
     else if (L.n_slots * Q >= ((int64_t)1 << 31)) why = "case too large for a batch (19 N >= 2^31)";
+    else if (g.kind == 0 && (L.nx > 2047 || L.ny > 2047 || L.nz > 1023))
+      why = "dense batch cases need nx, ny <= 2047 and nz <= 1023";
     if (why) {
       batch_free(b);
       return fail(LBM_ERR_UNSUPPORTED, why);
@@ -280,11 +304,19 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
     d.omega = (float)(1.0 / g.phys.tau);
     d.tau = (float)g.phys.tau;
     d.closure = 0;
+    d.inv_nx = 1.f / (float)L.nx;
+    d.inv_ny = 1.f / (float)L.ny;
     b->cases_h.push_back(d);
     const int64_t items = g.kind == 0 ? (L.n_slots + BT - 1) / BT : L.n_blocks * 2;
     for (int64_t t = 0; t < items; ++t) {
       ic.push_back(c);
-      il.push_back((int32_t)t);
+      if (g.kind == 0) {  // dense: first voxel of the item, packed
+        const int64_t v0 = t * BT;
+        const int64_t x0 = v0 % L.nx, y0 = (v0 / L.nx) % L.ny, z0 = v0 / ((int64_t)L.nx * L.ny);
+        il.push_back((int32_t)(uint32_t)(x0 | (y0 << 11) | (z0 << 22)));
+      } else {
+        il.push_back((int32_t)t);
+      }
     }
     b->items_per_case.push_back((int32_t)items);
     b->n_updated += L.n_updated;
@@ -292,6 +324,14 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
   }
   b->n_items = (int64_t)ic.size();
   b->n_plain = b->n_items;
+  b->item_local_h = il;
+  {
+    int64_t first = 0;
+    for (int32_t n : b->items_per_case) {
+      b->item_first.push_back(first);
+      first += n;
+    }
+  }
   b->fn = step_fn(b->storage, b->collision, false);
   b->fn_cl = step_fn(b->storage, b->collision, true);
   int dev = 0;
@@ -352,7 +392,7 @@ lbm_status lbm_batch_closure_load(lbm_batch* b, const float* theta, size_t n, in
       if (d.closure != pass) continue;
       for (int32_t t = 0; t < b->items_per_case[c]; ++t) {
         ic.push_back((int32_t)c);
-        il.push_back(t);
+        il.push_back(b->item_local_h[(size_t)(b->item_first[c] + t)]);
       }
     }
   if (ic.size() != (size_t)b->n_items) return fail(LBM_ERR_INTERNAL, "batch work list size");

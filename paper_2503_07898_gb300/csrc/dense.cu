@@ -40,10 +40,9 @@ __global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
     if (wm & (WM_SKIP | WM_REG)) return;
   }
   // warp-uniform choice: a warp holds one (y, z) row
-  const bool lean = y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1;
-  if (lean) {
-    if (wm) pull_row_interior<S, IDX, true>((const T*)a.fin, a, x, (IDX)v, wm, g);
-    else pull_row_interior<S, IDX, false>((const T*)a.fin, a, x, (IDX)v, 0u, g);
+  if (lean_row(a, y, z)) {
+    if (wm) pull_row_interior<S, IDX, true>((const T*)a.fin, a, x, y, z, (IDX)v, wm, g);
+    else pull_row_interior<S, IDX, false>((const T*)a.fin, a, x, y, z, (IDX)v, 0u, g);
   } else {
     pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
   }

@@ -63,18 +63,29 @@ __device__ __forceinline__ void pull_all(const typename Codec<S>::T* __restrict_
   });
 }
 
-// Lean pull for rows whose y and z neighbours are all inside the box (no
-// wrap, no box-side wall in y or z): one precomputed offset per direction,
-// x edges handled by predicated selects, wall-mask bits (WM) by one bit test
-// per direction.  IDX is int32_t when 19 N fits in 31 bits.
+// Lean pull for rows without a non-periodic box side next to them in y or z
+// (all rows of an axis that is periodic, the inner rows of one that is
+// not): the source row offsets for c_y = +-1 and c_z = +-1 are formed once
+// per voxel (wrapping across periodic sides), x edges are handled by
+// predicated selects, and wall-mask bits (WM) by one bit test per
+// direction.  IDX is int32_t when Q N fits in 31 bits.
 template <int S, class IDX, bool WM>
 __device__ __forceinline__ void pull_row_interior(const typename Codec<S>::T* __restrict__ fin,
-                                                  const DenseArgs& a, int x, IDX v, uint32_t wm,
-                                                  float g[Q]) {
+                                                  const DenseArgs& a, int x, int y, int z, IDX v,
+                                                  uint32_t wm, float g[Q]) {
   const IDX N = (IDX)a.N, nx = (IDX)a.nx, plane = (IDX)a.nx * (IDX)a.ny;
+  // offset of the source row for c = +1 (row y - 1) and c = -1 (row y + 1)
+  const IDX yp = y == 0 ? (IDX)(a.ny - 1) * nx : -nx;
+  const IDX yn = y == a.ny - 1 ? -(IDX)(a.ny - 1) * nx : nx;
+  const IDX zp = z == 0 ? (IDX)(a.nz - 1) * plane : -plane;
+  const IDX zn = z == a.nz - 1 ? -(IDX)(a.nz - 1) * plane : plane;
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
-    IDX src = (IDX)I * N + v - ((IDX)cx(I) + (IDX)cy(I) * nx + (IDX)cz(I) * plane);
+    IDX src = (IDX)I * N + v - (IDX)cx(I);
+    if constexpr (cy(I) > 0) src += yp;
+    else if constexpr (cy(I) < 0) src += yn;
+    if constexpr (cz(I) > 0) src += zp;
+    else if constexpr (cz(I) < 0) src += zn;
     if constexpr (cx(I) > 0) {
       if (x == 0) src = a.px ? src + nx : (IDX)opp(I) * N + v;
     } else if constexpr (cx(I) < 0) {
@@ -85,6 +96,11 @@ __device__ __forceinline__ void pull_row_interior(const typename Codec<S>::T* __
     }
     g[I] = Codec<S>::template load<I>(fin[src]);
   });
+}
+
+// A row of the lean pull: no non-periodic box side next to it in y or z.
+__device__ __forceinline__ bool lean_row(const DenseArgs& a, int y, int z) {
+  return (a.py || (y > 0 && y < a.ny - 1)) && (a.pz || (z > 0 && z < a.nz - 1));
 }
 
 template <int S>

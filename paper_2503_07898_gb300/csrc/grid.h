@@ -71,6 +71,8 @@ struct Level {
   int32_t* bmap_d = nullptr;
   uint8_t* blk_walls_d = nullptr; // sparse: 1 if block or its halo has a wall voxel
   uint32_t* bnd_bits_d = nullptr; // bitmask grouping: boundary block bits
+  int32_t* reg_blocks_d = nullptr;  // multi-res level 0: blocks holding regularized voxels
+  int64_t n_reg_blocks = 0;
   int32_t* bc_idx_d = nullptr;    // bitmask grouping: per-slot index into bc_cmp_d
   float4* bc_cmp_d = nullptr;     // bitmask grouping: BC values, one per regularized voxel
 
@@ -140,6 +142,9 @@ void prof_clear(Grid& g);
   lbm_status sparse_uniform_range(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin, \
                                   void* fout, float omega, cudaStream_t s, const char* name,  \
                                   int64_t units);                                             \
+  /* regularized voxels of the blocks listed in L.reg_blocks_d (multi-res level 0) */        \
+  lbm_status sparse_reg_blocks(Grid& g, Level& L, const void* fin, void* fout, float omega,   \
+                               cudaStream_t s, const char* name);                             \
   lbm_status launch_init_equilibrium(Grid& g, Level& L, const double* rho, const double* u,  \
                                      cudaStream_t s);                                         \
   lbm_status launch_moments(Grid& g, Level& L, double* rho, double* u, cudaStream_t s);     \
@@ -152,6 +157,8 @@ namespace q27 {
 LBM_LATTICE_LAUNCHERS
 }
 lbm_status multires_build(Grid& g, const int finest[3], int n_levels, const uint8_t* level_map);
+lbm_status multires_set_boundary(Grid& g, const uint8_t* flags, const float* bc_values,
+                                 const float* def_bc);
 lbm_status multires_step(Grid& g, cudaStream_t s);
 
 }  // namespace lbm

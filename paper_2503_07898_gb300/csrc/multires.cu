@@ -49,14 +49,31 @@ static inline int wrapi(int v, int n) { return ((v % n) + n) % n; }
 lbm_status multires_build(Grid& g, const int fin[3], int L, const uint8_t* lmap) {
   if (L < 1 || L > 4) return fail(LBM_ERR_INVALID, "n_levels must be 1..4");
   const int C = 8 << (L - 1);  // level-map cell (finest voxels) = coarsest block
-  for (int a = 0; a < 3; ++a) {
+  for (int a = 0; a < 3; ++a)
     if (fin[a] <= 0 || fin[a] % C) return fail(LBM_ERR_INVALID, "finest dims must be multiples of 8*2^(n_levels-1)");
-    if (!g.phys.periodic[a]) return fail(LBM_ERR_UNSUPPORTED, "multi-resolution grids are periodic");
-  }
   const int mx = fin[0] / C, my = fin[1] / C, mz = fin[2] / C;
   auto mapv = [&](int x, int y, int z) {
     return (int)lmap[wrapi(x, mx) + (size_t)mx * (wrapi(y, my) + (size_t)my * wrapi(z, mz))];
   };
+  // walls and boundary nodes lie on the finest level: every map cell on a
+  // non-periodic side is level 0, so coarser levels (and every explosion /
+  // coalescence trace) stay at least one coarsest block from the walls and
+  // the tables below may wrap as on a periodic box
+  const int md[3] = {mx, my, mz};
+  for (int a = 0; a < 3; ++a) {
+    if (g.phys.periodic[a]) continue;
+    for (int i = 0; i < md[(a + 1) % 3]; ++i)
+      for (int j = 0; j < md[(a + 2) % 3]; ++j)
+        for (int side = 0; side < 2; ++side) {
+          int c[3];
+          c[a] = side ? md[a] - 1 : 0;
+          c[(a + 1) % 3] = i;
+          c[(a + 2) % 3] = j;
+          if (mapv(c[0], c[1], c[2]) != 0)
+            return fail(LBM_ERR_UNSUPPORTED,
+                        "map cells on a non-periodic side must be level 0 (walls on the finest level)");
+        }
+  }
   for (int z = 0; z < mz; ++z)
     for (int y = 0; y < my; ++y)
       for (int x = 0; x < mx; ++x) {
@@ -160,6 +177,92 @@ lbm_status multires_build(Grid& g, const int fin[3], int L, const uint8_t* lmap)
       }
   }
   return LBM_OK;
+}
+
+// Walls and boundary nodes of the finest level (Sec. 6.3's lid-driven
+// cavity).  flags: level-0 virtual box; only voxels level 0 owns are read
+// (solid, regularized velocity / pressure or fluid), and solid or
+// regularized voxels must lie in G_i blocks (interface blocks run the
+// interface kernel, which has no wall path).  Builds the per-slot flags, the
+// wall mask (bit i = pull i bounces back: non-periodic box side or solid
+// source; bit 30 regularized, bit 31 not updated), the per-block wall bit and
+// the list of blocks holding regularized voxels, then the boundary values.
+lbm_status multires_set_boundary(Grid& g, const uint8_t* flags, const float* bc_values,
+                                 const float* def_bc) {
+  Level& V = g.lv[0];
+  const int nx = V.nx, ny = V.ny, nz = V.nz;
+  const size_t nv = (size_t)nx * ny * nz;
+  std::vector<uint8_t> fl(V.flags_h);
+  if (flags) {
+    for (size_t v = 0; v < nv; ++v) {
+      if (flag_type(V.flags_h[v]) == T_OUTSIDE) continue;  // owned by another level
+      const int t = flag_type(flags[v]);
+      if (!type_updated(t) && t != T_SOLID)
+        return fail(LBM_ERR_INVALID, "level-0 voxels must be fluid, solid or regularized");
+      if (type_regularized(t) && flag_normal(flags[v]) > 5)
+        return fail(LBM_ERR_INVALID, "regularized voxel with bad normal");
+      fl[v] = flags[v];
+    }
+  }
+  const int per[3] = {g.phys.periodic[0], g.phys.periodic[1], g.phys.periodic[2]};
+  const int n3[3] = {nx, ny, nz};
+  std::vector<uint8_t> sf((size_t)V.n_slots, (uint8_t)T_OUTSIDE);
+  std::vector<uint32_t> wm((size_t)V.n_slots, 0u);
+  std::vector<uint8_t> bw((size_t)V.n_blocks, 0);
+  std::vector<int32_t> regb;
+  int64_t n_upd = 0, n_reg = 0;
+  for (int64_t b = 0; b < V.n_blocks; ++b) {
+    bool has_reg = false;
+    for (int l = 0; l < 512; ++l) {
+      const int x = V.coords_h[b * 3] * 8 + (l & 7), y = V.coords_h[b * 3 + 1] * 8 + ((l >> 3) & 7),
+                z = V.coords_h[b * 3 + 2] * 8 + (l >> 6);
+      const uint8_t f = fl[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)];
+      const int t = flag_type(f);
+      sf[(size_t)(b * 512 + l)] = f;
+      uint32_t m = 0;
+      if (!type_updated(t)) m |= 1u << 31;
+      if (type_regularized(t)) {
+        m |= 1u << 30;
+        has_reg = true;
+        ++n_reg;
+      }
+      if (type_updated(t)) ++n_upd;
+      for (int i = 1; i < Q; ++i) {
+        int sc[3] = {x - cx(i), y - cy(i), z - cz(i)};
+        bool wall = false;
+        for (int a = 0; a < 3; ++a)
+          if (sc[a] < 0 || sc[a] >= n3[a]) {
+            if (per[a]) sc[a] = wrapi(sc[a], n3[a]);
+            else wall = true;
+          }
+        if (!wall) wall = flag_type(fl[(size_t)sc[0] + (size_t)nx * ((size_t)sc[1] + (size_t)ny * sc[2])]) == T_SOLID;
+        if (wall) m |= 1u << i;
+      }
+      wm[(size_t)(b * 512 + l)] = m;
+      if (m) bw[(size_t)b] = 1;
+    }
+    if (bw[(size_t)b] && b < V.n_c)
+      return fail(LBM_ERR_UNSUPPORTED, "walls and boundary nodes must lie in G_i blocks of level 0");
+    if (has_reg) regb.push_back((int32_t)b);
+  }
+  V.flags_h.swap(fl);
+  V.n_updated = n_upd;
+  V.n_reg = n_reg;
+  V.n_reg_blocks = (int64_t)regb.size();
+  auto upload = [&](void** dst, const void* src, size_t bytes) -> lbm_status {
+    g.dfree(*dst, g.stream);
+    *dst = g.dalloc(bytes + 16, g.stream);
+    if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
+    if (bytes) LBM_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return LBM_OK;
+  };
+  lbm_status st;
+  if ((st = upload((void**)&V.flags_d, sf.data(), sf.size())) ||
+      (st = upload((void**)&V.wmask_d, wm.data(), wm.size() * 4)) ||
+      (st = upload((void**)&V.blk_walls_d, bw.data(), bw.size())) ||
+      (st = upload((void**)&V.reg_blocks_d, regb.data(), regb.size() * 4)))
+    return st;
+  return sparse_set_bc(g, V, bc_values, def_bc);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -485,8 +588,10 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
       prof_end(g, s, pr);
     } else {
       st = sparse_uniform_range(g, V, V.n_c, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
-                                (V.n_blocks - V.n_c) * 512);
+                                V.n_updated - V.n_c * 512 - V.n_reg);
       if (st) return st;
+      // regularized boundary voxels (a lid on level 0) of those blocks
+      if ((st = sparse_reg_blocks(g, V, V.f[c], V.f[nx], omega, s, "mr_regularized_l0"))) return st;
     }
     LBM_CUDA(cudaEventRecord(g.mr_join[l], s));
     s = s_main;

@@ -83,7 +83,7 @@ lbm_status sparse_set_bc(Grid& g, Level& L, const float* bc_values, const float*
     return fail(LBM_ERR_INVALID, "regularized voxels need bc_values or default_bc");
   const int64_t E3 = (int64_t)L.E * L.E * L.E;
   L.bc_h.assign((size_t)L.n_reg * 4, 0.f);
-  if (L.bitmask) {
+  if (L.bitmask || g.kind == 2) {
     // indirect indexing: a per-slot rank into one compact value per
     // regularized voxel (flag-scan order)
     L.bc_idx_h.assign((size_t)L.n_slots, -1);
@@ -296,8 +296,10 @@ lbm_status sparse_build(Grid& g, Level& L) {
 // over its own contiguous block range; *_BM: the same kernels under the
 // bitmask grouping, launched over every block and returning at once on a
 // block of the other group; MONOLITHIC: the naive single kernel.
+// REG_LIST: the regularized voxels (only) of a list of 8^3 blocks whose other
+// voxels an INTERIOR launch updates (multi-resolution level 0 with a lid).
 enum { MODE_INTERIOR = 0, MODE_BOUNDARY = 1, MODE_MONOLITHIC = 2, MODE_INTERIOR_BM = 3,
-       MODE_BOUNDARY_BM = 4 };
+       MODE_BOUNDARY_BM = 4, MODE_REG_LIST = 5 };
 constexpr int SP_THREADS = 256;
 
 struct SparseArgs {
@@ -308,6 +310,7 @@ struct SparseArgs {
   const uint32_t* wmask;  // per-slot wall mask (blocks with walls, boundary group)
   const uint8_t* blk_walls;
   const float4* bc;
+  const int32_t* blist;      // REG_LIST: block ids (two CTAs per block)
   const uint32_t* bnd_bits;  // bitmask grouping: boundary block bits
   const int32_t* bc_idx;     // bitmask grouping: per-slot index into bc_cmp
   const float4* bc_cmp;      // bitmask grouping: compact BC values
@@ -317,12 +320,16 @@ struct SparseArgs {
 
 template <int S, int E, int COLL, int MODE>
 __global__ void __launch_bounds__(SP_THREADS,
-                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? 4 : 1)
+                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? (Q == 27 ? 3 : 4) : 1)
     sparse_kernel(SparseArgs a) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E;
   constexpr bool LEAN = MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM;
-  const int64_t slot = a.s0 + (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
+  int64_t slot;
+  if constexpr (MODE == MODE_REG_LIST)
+    slot = (int64_t)a.blist[blockIdx.x >> 1] * E3 + (blockIdx.x & 1) * SP_THREADS + threadIdx.x;
+  else
+    slot = a.s0 + (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
   if (slot >= a.s1) return;
   const int64_t b = slot / E3;
   const int l = (int)(slot - b * E3);
@@ -334,7 +341,9 @@ __global__ void __launch_bounds__(SP_THREADS,
   uint32_t wm = 0;
   if (walls) {
     wm = a.wmask[slot];
-    if (wm & (1u << 31)) return;
+    // lean kernels leave regularized voxels to a boundary launch
+    if (wm & (LEAN ? 0xC0000000u : 0x80000000u)) return;
+    if (MODE == MODE_REG_LIST && !(wm & (1u << 30))) return;
   }
   const T* __restrict__ fin = (const T*)a.fin;
   float g[Q];
@@ -344,7 +353,8 @@ __global__ void __launch_bounds__(SP_THREADS,
   } else {
     if (wm & (1u << 30)) {
       const uint8_t own = a.flags[slot];
-      const float4 bc = MODE == MODE_BOUNDARY_BM ? a.bc_cmp[a.bc_idx[slot]] : a.bc[slot];
+      const float4 bc = (MODE == MODE_BOUNDARY_BM || MODE == MODE_REG_LIST)
+                            ? a.bc_cmp[a.bc_idx[slot]] : a.bc[slot];
       regularized_node(g, flag_type(own), flag_normal(own), bc, a.omega);
     } else {
       collide<COLL>(g, a.omega);
@@ -355,6 +365,27 @@ __global__ void __launch_bounds__(SP_THREADS,
     constexpr int I = decltype(ic)::value;
     fout[(b * Q + I) * E3 + l] = Codec<S>::template store<I>(g[I]);
   });
+}
+
+template <int S, int COLL>
+static void reg_list_t(Grid& g, Level& L, const void* fin, void* fout, float omega, cudaStream_t s,
+                       const char* name) {
+  SparseArgs a{};
+  a.fin = fin;
+  a.fout = fout;
+  a.nbr = L.nbr_d;
+  a.flags = L.flags_d;
+  a.wmask = L.wmask_d;
+  a.blk_walls = L.blk_walls_d;
+  a.blist = L.reg_blocks_d;
+  a.bc_idx = L.bc_idx_d;
+  a.bc_cmp = L.bc_cmp_d;
+  a.omega = omega;
+  a.s0 = 0;
+  a.s1 = L.n_blocks * 512;
+  const int pr = prof_begin(g, s, name, L.n_reg);
+  sparse_kernel<S, 8, COLL, MODE_REG_LIST><<<(unsigned)(2 * L.n_reg_blocks), SP_THREADS, 0, s>>>(a);
+  prof_end(g, s, pr);
 }
 
 template <int S, int E, int COLL, int MODE>
@@ -419,6 +450,27 @@ static void uniform_range_t(Grid& g, Level& L, int64_t b0, int64_t b1, const voi
   a.s0 = b0 * 512;
   a.s1 = b1 * 512;
   launch_range<S, 8, COLL, MODE_INTERIOR>(g, a, s, name, units);
+}
+
+lbm_status sparse_reg_blocks(Grid& g, Level& L, const void* fin, void* fout, float omega,
+                             cudaStream_t s, const char* name) {
+  if (L.n_reg_blocks <= 0) return LBM_OK;
+  const bool bgk = g.phys.collision == C_BGK;
+  switch (g.phys.storage) {
+    case S_F32:
+      bgk ? reg_list_t<S_F32, C_BGK>(g, L, fin, fout, omega, s, name)
+          : reg_list_t<S_F32, C_REG>(g, L, fin, fout, omega, s, name);
+      break;
+    case S_F16:
+      bgk ? reg_list_t<S_F16, C_BGK>(g, L, fin, fout, omega, s, name)
+          : reg_list_t<S_F16, C_REG>(g, L, fin, fout, omega, s, name);
+      break;
+    default:
+      bgk ? reg_list_t<S_BF16, C_BGK>(g, L, fin, fout, omega, s, name)
+          : reg_list_t<S_BF16, C_REG>(g, L, fin, fout, omega, s, name);
+  }
+  LBM_CUDA(cudaGetLastError());
+  return LBM_OK;
 }
 
 lbm_status sparse_uniform_range(Grid& g, Level& L, int64_t b0, int64_t b1, const void* fin,
