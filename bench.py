@@ -221,6 +221,35 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             lbm.lbm_grid_destroy(g)
         res["updates_per_coarsest_step"] = ups
         out["turbulence_256_3level"] = res
+        # the paper's multi-resolution benchmark (Sec. 6.3, Table 5): a
+        # lid-driven cavity, finest level along the walls and the lid
+        n = 384
+        lmap = wl.multires_cavity_map(n, 3, (2, 2))
+        flags, bc = wl.cavity(n)
+        t = flags & 7
+        bcl = np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
+        res = {}
+        for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
+                         ("fused_f16", dict(storage="f16"))):
+            g = lbm.lbm_grid_create_multires((n,) * 3, 3, lmap, lbm.physics(0.52, **kw),
+                                             stream=stream)
+            lbm.lbm_set_boundary(g, 0, flags, bcl)
+            info = lbm.lbm_get_info(g)
+            ups = sum(k * 2 ** (2 - l) for l, k in enumerate(info["n_updated"]))
+            for l in range(3):
+                lbm.lbm_init_equilibrium(g, l, None, None)
+            lbm.lbm_step(g, 3, stream)
+            nst = max(1, steps // 4)
+            ms = _time_steps(torch, lbm, lambda k: lbm.lbm_step(g, k, stream), stream, nst)
+            glups = ups * nst / (ms * 1e-3) / 1e9
+            bpu = 76 if kw.get("storage") == "f16" else 152
+            res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
+            lbm.lbm_grid_destroy(g)
+        tot = n ** 3
+        res["pct_of_finest_box_voxels"] = [round(100 * k / tot, 3) for k in info["n_updated"]]
+        res["voxels_per_level"] = list(info["n_updated"])
+        res["updates_per_coarsest_step"] = ups
+        out[f"cavity_{n}_3level"] = res
     if "batch" in which:
         cases = wl.batch_cases(n_cases=n_batch)
         grids = []
@@ -350,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
     n_upd = info["n_updated"][0]
     lbm.lbm_init_equilibrium(g, 0, None, None)
     variant, variant_ms = lbm.lbm_autotune(g, 20) if args.variant == "auto" else (
-        {"vec16": 0, "scalar": 1, "vec8": 2}[args.variant], None)
+        {"vec16": 0, "scalar": 1, "vec8": 2, "vec4": 3}[args.variant], None)
     lbm.lbm_set_variant(g, variant)
 
     def barrier():
@@ -534,7 +563,7 @@ def main():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--schedule", default="disaggregated", choices=["disaggregated", "monolithic"])
-    ap.add_argument("--variant", default="auto", choices=["auto", "vec16", "scalar", "vec8"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "vec16", "scalar", "vec8", "vec4"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=128,

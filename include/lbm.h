@@ -163,20 +163,21 @@ lbm_status lbm_set_schedule(lbm_grid* g, int schedule);
 
 /* Interior-kernel variant of a dense grid (no counterpart in the paper; a
  * tuning knob of this implementation):
- *   LBM_VARIANT_VEC16  a thread moves 16-byte vectors of consecutive voxels
- *                      (default),
- *   LBM_VARIANT_SCALAR one voxel per thread,
- *   LBM_VARIANT_VEC8   8-byte vectors.
+ *   LBM_VARIANT_VEC16  a thread moves 16-byte vectors of consecutive voxels,
+ *   LBM_VARIANT_SCALAR one voxel per thread (default),
+ *   LBM_VARIANT_VEC8   8-byte vectors,
+ *   LBM_VARIANT_VEC4   4-byte vectors (two voxels per thread under FP16 /
+ *                      BF16 storage; the scalar kernel under FP32).
  * Vector variants apply when walls are only box sides, dims[0] is a multiple
  * of the vector length and the boundary group is whole top planes; otherwise
  * the scalar kernel runs.  Results are identical across variants. */
-enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2 };
+enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2, LBM_VARIANT_VEC4 = 3 };
 lbm_status lbm_set_variant(lbm_grid* g, int variant);
 
 /* Autotuner: times each variant over n_steps steps (CUDA events on the grid's
  * stream) starting from the grid's current state, restores that state, and
- * keeps the fastest variant.  *chosen receives it; ms_per_step (3 doubles, or
- * NULL) receives the measured time per step of each variant. */
+ * keeps the fastest variant.  *chosen receives it; ms_per_step (4 doubles, one
+ * per LBM_VARIANT_*, or NULL) receives the measured time per step of each. */
 lbm_status lbm_autotune(lbm_grid* g, int n_steps, int* chosen, double* ms_per_step);
 
 /* Voxel types and boundary values of one level.

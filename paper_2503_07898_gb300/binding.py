@@ -283,8 +283,8 @@ def lbm_set_schedule(grid, schedule):
     _check(load().lbm_set_schedule(grid.ptr, int(s)), "lbm_set_schedule")
 
 
-LBM_VARIANT_VEC16, LBM_VARIANT_SCALAR, LBM_VARIANT_VEC8 = 0, 1, 2
-VARIANT_NAMES = {0: "vec16", 1: "scalar", 2: "vec8"}
+LBM_VARIANT_VEC16, LBM_VARIANT_SCALAR, LBM_VARIANT_VEC8, LBM_VARIANT_VEC4 = 0, 1, 2, 3
+VARIANT_NAMES = {0: "vec16", 1: "scalar", 2: "vec8", 3: "vec4"}
 
 
 def lbm_set_variant(grid, variant):
@@ -294,7 +294,7 @@ def lbm_set_variant(grid, variant):
 def lbm_autotune(grid, n_steps):
     """Returns (chosen variant, [ms per step of each variant])."""
     chosen = C.c_int()
-    ms = (C.c_double * 3)()
+    ms = (C.c_double * 4)()
     _check(load().lbm_autotune(grid.ptr, int(n_steps), C.byref(chosen), ms), "lbm_autotune")
     return chosen.value, list(ms)
 

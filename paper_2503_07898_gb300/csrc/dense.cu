@@ -74,6 +74,9 @@ __device__ __forceinline__ PVec<T, V> ld_vec(const T* p) {
   if constexpr (sizeof(T) * V == 16) {
     uint4 u = __ldcs(reinterpret_cast<const uint4*>(p));
     memcpy(&r, &u, 16);
+  } else if constexpr (sizeof(T) * V == 4) {
+    unsigned int u = __ldcs(reinterpret_cast<const unsigned int*>(p));
+    memcpy(&r, &u, 4);
   } else {
     uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
     memcpy(&r, &u, 8);
@@ -87,6 +90,10 @@ __device__ __forceinline__ void st_vec(T* p, const PVec<T, V>& r) {
     uint4 u;
     memcpy(&u, &r, 16);
     __stcs(reinterpret_cast<uint4*>(p), u);
+  } else if constexpr (sizeof(T) * V == 4) {
+    unsigned int u;
+    memcpy(&u, &r, 4);
+    __stcs(reinterpret_cast<unsigned int*>(p), u);
   } else {
     uint2 u;
     memcpy(&u, &r, 8);
@@ -246,13 +253,26 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
     // boundary group that is not a whole number of top planes
     constexpr int V16 = 16 / (int)sizeof(typename Codec<S>::T);
     constexpr int V8 = 8 / (int)sizeof(typename Codec<S>::T);
-    const int vw = L.variant == VARIANT_SCALAR ? 0 : (L.variant == VARIANT_VEC8 ? V8 : V16);
+    constexpr int V4 = 4 / (int)sizeof(typename Codec<S>::T);  // 2 for 16-bit storage, else 1
+    const int vw = L.variant == VARIANT_SCALAR ? 0
+                   : L.variant == VARIANT_VEC8 ? V8
+                   : L.variant == VARIANT_VEC4 ? (V4 >= 2 ? V4 : 0)
+                                               : V16;
     const bool vec_ok = vw > 0 && !L.wmask_d && L.nx % vw == 0 && a.vend % plane == 0;
     if (zc > 0 && vec_ok) {
       const int pr = prof_begin(g, s, "dense_interior_vec", L.n_updated - L.n_reg);
       const dim3 vb(32, VEC_ROWS), vg((L.nx + 32 * vw - 1) / (32 * vw), (L.ny + VEC_ROWS - 1) / VEC_ROWS, zc);
-      if (vw == V16) dense_interior_vec<S, COLL, V16><<<vg, vb, 0, s>>>(a);
-      else dense_interior_vec<S, COLL, V8><<<vg, vb, 0, s>>>(a);
+      bool launched = false;
+      if constexpr (V4 >= 2) {
+        if (vw == V4) {
+          dense_interior_vec<S, COLL, V4><<<vg, vb, 0, s>>>(a);
+          launched = true;
+        }
+      }
+      if (!launched) {
+        if (vw == V16) dense_interior_vec<S, COLL, V16><<<vg, vb, 0, s>>>(a);
+        else dense_interior_vec<S, COLL, V8><<<vg, vb, 0, s>>>(a);
+      }
       prof_end(g, s, pr);
     } else if (zc > 0) {
       const int pr = prof_begin(g, s, "dense_interior", L.n_updated - L.n_reg);

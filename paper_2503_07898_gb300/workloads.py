@@ -132,6 +132,26 @@ def multires_slab_map(n=256, n_levels=3):
     return np.ascontiguousarray(np.broadcast_to(zlev[:, None, None], (m, m, m)))
 
 
+def multires_cavity_map(n=384, n_levels=3, shells=(2, 2)):
+    """Level map of a multi-resolution lid-driven cavity (the benchmark of
+    Sec. 6.3, Table 5): level 0 along every box face, shells[0] map cells
+    thick, then level 1 for shells[1] cells, and so on inwards, the coarsest
+    level in the middle.  One map cell is the coarsest block (8 * 2^(L-1)
+    finest voxels); shape (mz, my, mx).  The walls and the lid then lie on
+    the finest level, as the library requires of non-periodic grids."""
+    cell = 8 * 2 ** (n_levels - 1)
+    m = n // cell
+    i = np.arange(m)
+    d = np.minimum(i, m - 1 - i)
+    dist = np.minimum(np.minimum(d[:, None, None], d[None, :, None]), d[None, None, :])
+    lv = np.full((m, m, m), n_levels - 1, np.uint8)
+    edge = 0
+    for level, t in enumerate(shells[:n_levels - 1]):
+        lv[(dist >= edge) & (dist < edge + t)] = level
+        edge += t
+    return lv
+
+
 def turbulence(n, seed=7898, u_rms=0.03, kmax=None, dims=None):
     """Decaying-turbulence start: random-phase Fourier modes on integer wave
     vectors 1 <= |k| <= kmax with shell amplitude sqrt(E(k) / shell count),

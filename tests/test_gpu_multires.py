@@ -9,7 +9,7 @@ FP32 rounding, fused == unfused bit for bit, voxel counts).
 import numpy as np
 import pytest
 
-from cases import F32_RTOL
+from cases import F32_RTOL, bc_list, oracle_bc
 from oracle import layout as olayout
 from oracle import multires as omr
 from paper_2503_07898_gb300 import workloads as wl
@@ -155,3 +155,80 @@ def test_full_size_three_level_turbulence_properties(lbm):
     assert abs(m1[0] - m0[0]) / m0[0] <= 1e-6
     assert np.all(np.abs(m1[1:] - m0[1:]) <= 1e-6 * m0[0])
     lbm.lbm_sync(g)
+
+
+# ------------------------------------------- lid-driven cavity (Sec. 6.3)
+
+def make_cavity(lbm, n, n_levels, shells, tau, schedule="disaggregated", lid=True):
+    lmap = wl.multires_cavity_map(n, n_levels, shells)
+    g = lbm.lbm_grid_create_multires((n,) * 3, n_levels, lmap, lbm.physics(
+        tau, "bgk", "f32", (0, 0, 0), schedule))
+    flags, bc = wl.cavity(n)
+    if not lid:
+        flags = np.zeros_like(flags)
+    lbm.lbm_set_boundary(g, 0, flags, bc_list(flags, bc) if lid else None)
+    cell = 8 * 2 ** (n_levels - 1)
+    o = omr.MultiRes(lmap, n_levels, cell, tau, periodic=(False,) * 3, flags0=flags,
+                     bc0=oracle_bc(flags, bc) if lid else None)
+    return g, o
+
+
+def cavity_fields(n, n_levels, seed):
+    rho, u = wl.random_fields((n,) * 3, seed=seed, u_amp=0.02)
+    out = [(rho, u)]
+    for _ in range(1, n_levels):
+        rho, u = omr.subcell_mean(rho), omr.subcell_mean(u)
+        out.append((rho, u))
+    return out
+
+
+@pytest.mark.parametrize("schedule", ["disaggregated", "monolithic"])
+def test_cavity_two_level_parity(lbm, schedule):
+    """Walls and the regularized lid on level 0, level 1 in the middle."""
+    g, o = make_cavity(lbm, 48, 2, (1,), 0.6, schedule)
+    init_both(lbm, g, o, cavity_fields(48, 2, 70))
+    lbm.lbm_step(g, 4)
+    o.run(4)
+    assert compare(lbm, g, o, 2) <= F32_RTOL
+
+
+def test_cavity_three_level_parity(lbm):
+    """The smallest 3-level cavity the shell rule allows (160^3, level 2 in
+    the central 32^3), one coarsest step (four level-0 substeps)."""
+    g, o = make_cavity(lbm, 160, 3, (1, 1), 0.56)
+    init_both(lbm, g, o, cavity_fields(160, 3, 71))
+    lbm.lbm_step(g, 1)
+    o.run(1)
+    assert compare(lbm, g, o, 3) <= F32_RTOL
+
+
+def test_cavity_fused_equals_unfused_and_closed_box_mass(lbm):
+    out = []
+    for schedule in ("disaggregated", "monolithic"):
+        g, _ = make_cavity(lbm, 160, 3, (1, 1), 0.56, schedule)
+        for lv, (r, u) in enumerate(cavity_fields(160, 3, 72)):
+            lbm.lbm_init_equilibrium(g, lv, r, u)
+        lbm.lbm_step(g, 3)
+        out.append([lbm.lbm_get_populations_f64(g, lv) for lv in range(3)])
+    for a, b in zip(*out):
+        assert np.array_equal(np.nan_to_num(a, nan=-1.0), np.nan_to_num(b, nan=-1.0))
+    g, _ = make_cavity(lbm, 160, 3, (1, 1), 0.56, lid=False)
+    for lv, (r, u) in enumerate(cavity_fields(160, 3, 73)):
+        lbm.lbm_init_equilibrium(g, lv, r, u)
+    m0 = lbm.lbm_conservation(g)[0]
+    lbm.lbm_step(g, 10)
+    assert abs(lbm.lbm_conservation(g)[0] / m0 - 1) <= 1e-6
+
+
+def test_cavity_rules_are_enforced(lbm):
+    with pytest.raises(lbm.LbmError) as e:                # coarse cells on a wall
+        lbm.lbm_grid_create_multires((32, 32, 32), 2, np.ones((2, 2, 2), np.uint8),
+                                     lbm.physics(0.6, periodic=(0, 1, 1)))
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+    lmap = wl.multires_cavity_map(48, 2, (1,))
+    g = lbm.lbm_grid_create_multires((48,) * 3, 2, lmap, lbm.physics(0.6))
+    flags = np.zeros((48,) * 3, np.uint8)
+    flags[15, 20, 20] = wl.SOLID                           # in a G_c block of level 0
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_set_boundary(g, 0, flags)
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED

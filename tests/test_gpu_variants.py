@@ -1,6 +1,6 @@
 """GPU: interior-kernel variants, the autotuner, and FP16 / BF16 shifted storage.
 
-Variants (16-byte vectors, scalar, 8-byte vectors) must give the same
+Variants (16-byte vectors, scalar, 8-byte vectors, 4-byte vectors) must give the same
 populations and match the oracle.  Shifted 16-bit storage (s = f - w, RN-even)
 is compared with the FP64 oracle by the velocity-field L2 error; the bounds
 follow from the storage rounding: one FP16 rounding of |s| <~ 5e-3 costs
@@ -33,7 +33,7 @@ def run_variant(lbm, flags, bc, rho, u, tau, steps, variant, storage="f32", peri
 def test_variants_identical_cavity(lbm, storage):
     flags, bc = wl.cavity(0, dims=(64, 24, 20))
     rho, u = wl.random_fields(flags.shape, seed=40, u_amp=0.02)
-    outs = [run_variant(lbm, flags, bc, rho, u, 0.55, 50, v, storage)[1] for v in (0, 1, 2)]
+    outs = [run_variant(lbm, flags, bc, rho, u, 0.55, 50, v, storage)[1] for v in (0, 1, 2, 3)]
     m = updated_mask(flags)
     for o in outs[1:]:
         assert np.max(np.abs(o[:, m] - outs[0][:, m])) <= 1e-6
@@ -111,7 +111,7 @@ def test_autotune_restores_state(lbm):
     lbm.lbm_step(g, 5)
     before = lbm.lbm_get_populations_f64(g, 0)
     chosen, ms = lbm.lbm_autotune(g, 10)
-    assert chosen in (0, 1, 2) and all(t > 0 for t in ms)
+    assert chosen in (0, 1, 2, 3) and all(t > 0 for t in ms)
     after = lbm.lbm_get_populations_f64(g, 0)
     m = updated_mask(flags)
     assert np.array_equal(before[:, m], after[:, m])

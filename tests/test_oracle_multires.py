@@ -205,3 +205,59 @@ def test_closure_keeps_volume_weighted_conservation():
     m1 = g.conservation()
     assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
     assert np.all(np.abs(m1[1:] - m0[1:]) < 1e-12 * m0[0])
+
+
+# ------------------------------------------------- walls on the finest level
+
+def test_cavity_single_level_equals_plain_oracle():
+    """Walls and a regularized lid on a one-level grid: the plain cavity."""
+    n = 16
+    flags, bc = wl.cavity(n)
+    g = mr.MultiRes(np.zeros((1, 1, 1), int), 1, n, 0.6, periodic=(False,) * 3,
+                    flags0=flags, bc0=bc)
+    rho, u = wl.random_fields((n, n, n), seed=60)
+    g.init_equilibrium(0, rho, u)
+    g.run(5)
+    ref = olbm.run(olbm.init_equilibrium(rho, u, flags), flags, 0.6, 5, bc=bc)
+    assert np.max(np.abs(g.f[0] - ref)) < 1e-15
+
+
+def test_coarse_cells_on_walls_are_rejected():
+    with pytest.raises(ValueError):
+        mr.MultiRes(np.ones((2, 2, 2), int), 2, 16, 0.6, periodic=(False, True, True))
+    with pytest.raises(ValueError):
+        flags = np.zeros((32, 32, 32), np.uint8)
+        flags[20, 20, 20] = wl.SOLID                 # inside the level-1 region
+        mr.MultiRes(np.array([0, 1]).reshape(2, 1, 1), 2, 16, 0.6, flags0=flags)
+
+
+def test_closed_box_conserves_volume_weighted_mass():
+    lmap = wl.multires_cavity_map(48, 2, (1,))     # level 1 in the central 16^3
+    g = mr.MultiRes(lmap, 2, 16, 0.6, periodic=(False,) * 3)
+    init_random(g, 61)
+    m0 = g.conservation()[0]
+    g.run(3)
+    assert abs(g.conservation()[0] / m0 - 1) < 1e-12
+
+
+def test_cavity_near_walls_equals_single_resolution():
+    """Finest-level voxels beyond the light cone of the level jump (lid,
+    walls and the edges between them) evolve exactly as in a plain fine
+    cavity run of the same fine steps."""
+    n, T = 48, 3
+    lmap = wl.multires_cavity_map(n, 2, (1,))
+    flags, bc = wl.cavity(n)
+    rho, u = wl.random_fields((n,) * 3, seed=62, u_amp=0.02)
+    g = mr.MultiRes(lmap, 2, 16, 0.6, periodic=(False,) * 3, flags0=flags, bc0=bc)
+    g.init_equilibrium(0, rho, u)
+    g.init_equilibrium(1, mr.subcell_mean(rho), mr.subcell_mean(u))
+    g.run(T)
+    ref = olbm.run(olbm.init_equilibrium(rho, u, flags), flags, 0.6, 2 * T, bc=bc)
+    c = np.arange(n)
+    d1 = np.maximum(np.maximum(16 - c, c - 31), 0)          # per-axis distance to [16, 31]
+    dist = np.maximum(np.maximum(d1[:, None, None], d1[None, :, None]), d1[None, None, :])
+    far = dist > 2 * T + 4
+    assert far.sum() > 0.4 * n ** 3
+    assert np.max(np.abs(g.f[0][:, far] - ref[:, far])) < 1e-15
+    near = (dist > 0) & ~far
+    assert np.max(np.abs(g.f[0][:, near] - ref[:, near])) > 1e-8   # the jump does reach them
