@@ -383,7 +383,7 @@ template <> struct TmpCodec<S_F32> {
 };
 
 template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
-__global__ void __launch_bounds__(256, CLOSURE ? 1 : 4) mr_interface(MrArgs a) {
+__global__ void __launch_bounds__(256, CLOSURE ? 3 : 4) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;
   const int64_t b = a.b0 + blockIdx.x / 2;
   extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
@@ -484,7 +484,17 @@ __global__ void __launch_bounds__(256, CLOSURE ? 1 : 4) mr_interface(MrArgs a) {
       ClosureCta* sm = reinterpret_cast<ClosureCta*>(mr_dyn_smem);
       float x[MLP_IN];
       closure_features(g, a.tau, x);
+      // park the populations in this thread's shared-memory column while the
+      // network runs (volatile: the copies must really leave the registers)
+      static_for<Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        *(volatile float*)&mr_slow[I][threadIdx.x] = g[I];
+      });
       const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
+      static_for<Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        g[I] = *(volatile float*)&mr_slow[I][threadIdx.x];
+      });
       omega = 1.f / fmaxf(a.tau + dtau, TAU_MIN);
     }
     collide<COLL>(g, omega);
