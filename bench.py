@@ -122,6 +122,23 @@ def oracle_cavity_glups(n, steps, tau=0.515, u_lid=0.05):
     return n ** 3 * steps / dt / 1e9, dt, round(cores, 1)
 
 
+def max_over_ranks(dist, x, device):
+    """The largest per-rank float over all ranks (the job ends with its
+    slowest replica); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_glups(world, updates_per_rank, steps, seconds):
+    """Whole-job GLUPS of `world` independent replicas (weak scaling): the
+    updates of every rank over the slowest rank's time."""
+    return world * updates_per_rank * steps / seconds / 1e9
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -400,12 +417,8 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_upd * args.steps / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(dist, e0.elapsed_time(e1), "cuda")
+    value = job_glups(world, n_upd, args.steps, ms * 1e-3)
 
     # pass (B): per-kernel CUDA events for the roofline of the dominant kernel
     kb = min(args.steps, 200)
@@ -501,12 +514,8 @@ def run_ours(args, rank, world, local_rank):
     lbm.lbm_step(g, args.steps, stream)
     lbm.lbm_get_moments(g, 0, rho_o, u_o)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n_upd * args.steps / e2e_s / 1e9, "unit": "GLUPS",
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    e2e = {"value": job_glups(world, n_upd, args.steps, e2e_s), "unit": "GLUPS",
            "h2d_bytes_per_step": 4 * nv * 8, "d2h_bytes_per_step": 4 * nv * 8,
            "lbm_steps_per_step": args.steps,
            "what": "one call sequence: lbm_init_equilibrium(host rho,u) + lbm_step(K) + "

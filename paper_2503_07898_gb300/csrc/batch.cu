@@ -44,7 +44,7 @@ struct BatchCase {
 constexpr int BT = 256;  // threads per CTA = voxels per work item
 
 template <int S, int COLL, bool CLOSURE>
-__global__ void __launch_bounds__(BT) batch_step_kernel(const BatchCase* __restrict__ cases,
+__global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_step_kernel(const BatchCase* __restrict__ cases,
                                                         const int32_t* __restrict__ item_case,
                                                         const int32_t* __restrict__ item_local,
                                                         int64_t n_items, int parity,

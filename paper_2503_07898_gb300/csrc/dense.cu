@@ -25,7 +25,7 @@ namespace lbm {
 namespace LBM_LNS {
 
 template <int S, int COLL, class IDX>
-__global__ void __launch_bounds__(256, 4) dense_interior(DenseArgs a) {
+__global__ void __launch_bounds__(256, S == S_F32 ? 4 : 5) dense_interior(DenseArgs a) {
   using T = typename Codec<S>::T;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;

@@ -320,7 +320,7 @@ struct SparseArgs {
 
 template <int S, int E, int COLL, int MODE>
 __global__ void __launch_bounds__(SP_THREADS,
-                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? (Q == 27 ? 3 : 4) : 1)
+                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? (Q == 27 ? 3 : (S == S_F32 ? 4 : 5)) : 1)
     sparse_kernel(SparseArgs a) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E;
