@@ -34,7 +34,7 @@ METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated err
 # capture of dense_interior (dram__bytes_read.sum + dram__bytes_write.sum,
 # 4,070,400 updates per launch) scaled by units to one 256^3 launch
 # (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md.
-NCU_TRAFFIC = {"dense_interior": {"bytes_per_launch": 2.349412e+09, "src_sha": "2e631f754389f63b"}}
+NCU_TRAFFIC = {"dense_interior": {"bytes_per_launch": 2.348459e+09, "src_sha": "04a9e819962d707d"}}
 
 
 def src_hash():
