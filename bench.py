@@ -219,7 +219,8 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
         res = {}
         for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
                          ("fused_f16", dict(storage="f16")),
-                         ("fused_f32_learned_closure", dict(closure=1))):
+                         ("fused_f32_learned_closure", dict(closure=1)),
+                         ("fused_f32_d3q27", dict(lattice=27))):
             g = lbm.lbm_grid_create_multires((256, 256, 256), 3, lmap,
                                              lbm.physics(0.52, periodic=(1, 1, 1), **kw),
                                              stream=stream)
@@ -233,7 +234,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             ms = _time_steps(torch, lbm, lambda n: lbm.lbm_step(g, n, stream), stream,
                              max(1, steps // 4))
             glups = ups * max(1, steps // 4) / (ms * 1e-3) / 1e9
-            bpu = 76 if kw.get("storage") == "f16" else 152
+            bpu = (76 if kw.get("storage") == "f16" else 152) * kw.get("lattice", 19) // 19
             res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
             lbm.lbm_grid_destroy(g)
         res["updates_per_coarsest_step"] = ups

@@ -86,10 +86,10 @@ typedef struct {
   int periodic[3];   /* per axis: 1 periodic, 0 bounce-back walls at the box  */
   int schedule;      /* LBM_SCHEDULE_*                                        */
   int lattice;       /* 19 (D3Q19) or 27 (D3Q27); 0 means 19.  D3Q27 runs on
-                        dense and block-sparse grids (every schedule, both
-                        collisions, all storages, regularized boundaries);
-                        multi-resolution grids, the closure and batches are
-                        D3Q19 (LBM_ERR_UNSUPPORTED otherwise).  Populations
+                        dense, block-sparse and multi-resolution grids (every
+                        schedule, both collisions, all storages, regularized
+                        boundaries); the closure and batches are D3Q19
+                        (LBM_ERR_UNSUPPORTED otherwise).  Populations
                         are indexed i = 0..Q-1 in the order: rest, the six
                         axis directions, the twelve edge directions (D3Q19's
                         order), then (D3Q27) the eight corners (+1,+1,+1),

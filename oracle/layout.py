@@ -108,20 +108,22 @@ def block_tables(flags, block_edge=8, periodic=(False, False, False), grouping="
     return out
 
 
-def multires_tables(level_map, n_levels, cell, block_edge=8):
+def multires_tables(level_map, n_levels, cell, block_edge=8, q=19):
     """Brute-force multi-resolution block tables (periodic box).
 
     Reading (Sec. 5; Sec. 6.3): level l owns the regions the level map gives
     it; each level is cut into blocks of block_edge voxels of that level.  A
-    voxel has distance 0 (property P_d) iff one of its D3Q19 neighbours is
-    owned by another level; a block is G_c iff it holds such a voxel, else
+    voxel has distance 0 (property P_d) iff one of its neighbours along the
+    lattice's velocities (D3Q19, or D3Q27 with q = 27) is owned by another
+    level; a block is G_c iff it holds such a voxel, else
     G_i.  Numbering per level: G_c blocks first, then G_i, each in Morton
     order.  Returns one dict per level with coords, n_c, nbr (27 same-level
     neighbours, -1 = none), xnbr_coarse (27: level-(l+1) block covering the
     neighbour region, else -1) and xnbr_fine (27 x 8: the level-(l-1) blocks
     covering the neighbour region, octant j = x + 2y + 4z, else -1).
     """
-    from .lattice import C
+    from .lattice import lattice
+    C = lattice(q).C
     level_map = np.asarray(level_map)
     B = block_edge
     own = []
@@ -133,7 +135,7 @@ def multires_tables(level_map, n_levels, cell, block_edge=8):
     for lv in range(n_levels):
         o = own[lv]
         dist0 = np.zeros(o.shape, bool)
-        for i in range(1, 19):
+        for i in range(1, len(C)):
             cx, cy, cz = (int(v) for v in C[i])
             dist0 |= np.roll(o, shift=(cz, cy, cx), axis=(0, 1, 2)) != lv
         dist0 &= o == lv

@@ -90,10 +90,14 @@ class MultiRes:
     every cube of `cell` finest voxels; cell must be a multiple of 2^(L-1)."""
 
     def __init__(self, level_map, n_levels, cell, tau0, collision="bgk", theta=None,
-                 periodic=(True, True, True), flags0=None, bc0=None):
+                 periodic=(True, True, True), flags0=None, bc0=None, q=19):
         """periodic: per axis (x, y, z); flags0: level-0 flag bytes (solid and
         regularized voxels, inside the level-0 region); bc0: (4,) + level-0
-        box boundary values of its regularized voxels."""
+        box boundary values of its regularized voxels; q: 19 or 27 (the
+        closure is D3Q19 only)."""
+        self.lat = L.lattice(q)
+        if theta is not None and q != 19:
+            raise ValueError("the closure features are those of D3Q19")
         level_map = np.asarray(level_map, dtype=np.int64)
         self.theta = None if theta is None else np.asarray(theta, dtype=np.float64)
         self.periodic = tuple(bool(p) for p in periodic)
@@ -111,7 +115,7 @@ class MultiRes:
         for lv in range(n_levels):
             r = cell // (2 ** lv)
             self.own.append(level_map.repeat(r, 0).repeat(r, 1).repeat(r, 2))
-        self.f = [np.zeros((L.Q,) + o.shape) for o in self.own]
+        self.f = [np.zeros((self.lat.Q,) + o.shape) for o in self.own]
         self.flags0 = (np.zeros(self.own[0].shape, np.uint8) if flags0 is None
                        else np.asarray(flags0, dtype=np.uint8))
         if np.any((self.flags0 & 7 != 0) & (self.own[0] != 0)):
@@ -125,7 +129,7 @@ class MultiRes:
         return nx, ny, nz
 
     def init_equilibrium(self, level, rho, u):
-        feq = L.equilibrium(rho, u)
+        feq = self.lat.equilibrium(rho, u)
         mine = self.own[level] == level
         if level == 0:
             mine = mine & self.updated0
@@ -135,8 +139,8 @@ class MultiRes:
         own = self.own[lv]
         finer = np.zeros(own.shape, bool)
         coarser = np.zeros(own.shape, bool)
-        for i in range(1, L.Q):
-            nb = shift(own, L.C[i])
+        for i in range(1, self.lat.Q):
+            nb = shift(own, self.lat.C[i])
             finer |= nb == lv - 1
             coarser |= nb == lv + 1
         return finer, coarser
@@ -156,8 +160,8 @@ class MultiRes:
         # level 0 pulls as the single-resolution oracle (walls, solids);
         # coarser levels never touch a wall
         base = lbm.stream_with_walls(S, self.flags0, self.periodic) if lv == 0 else None
-        for i in range(L.Q):
-            c = L.C[i]
+        for i in range(self.lat.Q):
+            c = self.lat.C[i]
             val = base[i] if lv == 0 else shift(S[i], c)
             if lv + 1 < self.L:                       # explosion from level lv+1
                 c_up = upsample(self.f[lv + 1][i])

@@ -19,7 +19,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2"]
 SOURCES = ["api.cu", "dense.cu", "sparse.cu", "fields.cu", "multires.cu", "noalloc.cu", "closure.cu", "batch.cu"]
 # The lattice-dependent sources are compiled a second time for D3Q27 (their
 # code lands in namespace lbm::q27; the D3Q19 build in lbm::q19).
-LATTICE_SOURCES = ["dense.cu", "sparse.cu", "fields.cu"]
+LATTICE_SOURCES = ["dense.cu", "sparse.cu", "fields.cu", "multires.cu"]
 UNITS = [(src, [], src.replace(".cu", ".o")) for src in SOURCES] + \
         [(src, ["-DLBM_Q=27"], src.replace(".cu", "_q27.o")) for src in LATTICE_SOURCES]
 

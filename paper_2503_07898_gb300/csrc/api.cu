@@ -362,8 +362,6 @@ lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
   if (!finest_dims || !level_map) return fail(LBM_ERR_INVALID, "NULL argument");
   if (phys && phys->schedule == LBM_SCHEDULE_BITMASK)
     return fail(LBM_ERR_UNSUPPORTED, "bitmask grouping is a block-sparse layout");
-  if (phys && phys->lattice == 27)
-    return fail(LBM_ERR_UNSUPPORTED, "multi-resolution grids are D3Q19");
   Grid* gp = nullptr;
   lbm_status st = begin(out, phys, alloc, stream, gp);
   if (st) return st;
@@ -375,7 +373,9 @@ lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
     *out = nullptr;
     return s;
   };
-  if ((st = multires_build(g, finest_dims, n_levels, level_map))) return bail(st);
+  if ((st = g.q == 27 ? q27::multires_build(g, finest_dims, n_levels, level_map)
+                      : q19::multires_build(g, finest_dims, n_levels, level_map)))
+    return bail(st);
   if ((st = alloc_common(g))) return bail(st);
   for (int l = 0; l < g.n_levels; ++l) {
     Level& L = g.lv[l];
@@ -532,7 +532,9 @@ lbm_status lbm_set_boundary(lbm_grid* h, int level, const uint8_t* flags,
     }
     return LBM_OK;
   }
-  if (g.kind == 2 && level == 0) return multires_set_boundary(g, flags, bc_values, default_bc);
+  if (g.kind == 2 && level == 0)
+    return g.q == 27 ? q27::multires_set_boundary(g, flags, bc_values, default_bc)
+                     : q19::multires_set_boundary(g, flags, bc_values, default_bc);
   if (flags && std::memcmp(flags, L.flags_h.data(), nv) != 0)
     return fail(LBM_ERR_INVALID, "sparse flags (and those of multi-resolution levels >= 1) are fixed at creation");
   return sparse_set_bc(g, L, bc_values, default_bc);
@@ -587,7 +589,7 @@ lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
                                                : q19::dense_step(g, g.lv[0], s))
                     : g.kind == 1 ? (g.q == 27 ? q27::sparse_step(g, g.lv[0], s)
                                                : q19::sparse_step(g, g.lv[0], s))
-                                  : multires_step(g, s);
+                                  : (g.q == 27 ? q27::multires_step(g, s) : q19::multires_step(g, s));
     if (st) return st;
     ++g.steps_done;
   }

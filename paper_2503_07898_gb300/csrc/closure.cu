@@ -516,7 +516,8 @@ lbm_status lbm_closure_load(lbm_grid* h, const float* theta, size_t n) {
   if (!h || !theta) return fail(LBM_ERR_INVALID, "NULL argument");
   if (n != (size_t)MLP_PARAMS) return fail(LBM_ERR_INVALID, "closure weights must have 5313 values");
   Grid& g = h->g;
-  if (g.kind != 2) return fail(LBM_ERR_UNSUPPORTED, "the closure runs on multi-resolution grids");
+  if (g.kind != 2 || g.q != 19)
+    return fail(LBM_ERR_UNSUPPORTED, "the closure runs on D3Q19 multi-resolution grids");
   ClosureParams cp;
   closure_params_from_fp32(theta, &cp);
   if (!g.closure_d) {

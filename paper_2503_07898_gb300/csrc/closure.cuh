@@ -23,6 +23,7 @@
 #include "d3q19.cuh"
 
 namespace lbm {
+namespace LBM_LNS {
 
 constexpr int MLP_IN = 16, MLP_H = 64;
 constexpr int MLP_PARAMS = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;  // 5313
@@ -216,4 +217,5 @@ __device__ __forceinline__ float mlp_bf16_warp(const float x[MLP_IN], const Clos
   return out + P.b3;
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

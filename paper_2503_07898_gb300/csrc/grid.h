@@ -130,7 +130,7 @@ void prof_end(Grid& g, cudaStream_t s, int rec);
 void prof_clear(Grid& g);
 
 // Kernel launchers (defined in the .cu files) -------------------------------
-// dense.cu, sparse.cu and fields.cu are built once per lattice, into
+// dense.cu, sparse.cu, fields.cu and multires.cu are built once per lattice, into
 // namespace q19 (D3Q19) and q27 (D3Q27); the host code picks by Grid::q.
 #define LBM_LATTICE_LAUNCHERS                                                              \
   lbm_status dense_step(Grid& g, Level& L, cudaStream_t s);                                \
@@ -149,17 +149,19 @@ void prof_clear(Grid& g);
                                      cudaStream_t s);                                         \
   lbm_status launch_moments(Grid& g, Level& L, double* rho, double* u, cudaStream_t s);     \
   lbm_status launch_decode_f64(Grid& g, Level& L, double* dst, cudaStream_t s);             \
-  lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s);
+  lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s);                    \
+  lbm_status multires_build(Grid& g, const int finest[3], int n_levels,                      \
+                            const uint8_t* level_map);                                       \
+  lbm_status multires_step(Grid& g, cudaStream_t s);                                         \
+  lbm_status multires_set_boundary(Grid& g, const uint8_t* flags, const float* bc_values,    \
+                                   const float* def_bc);
 namespace q19 {
 LBM_LATTICE_LAUNCHERS
 }
 namespace q27 {
 LBM_LATTICE_LAUNCHERS
 }
-lbm_status multires_build(Grid& g, const int finest[3], int n_levels, const uint8_t* level_map);
-lbm_status multires_set_boundary(Grid& g, const uint8_t* flags, const float* bc_values,
-                                 const float* def_bc);
-lbm_status multires_step(Grid& g, cudaStream_t s);
+
 
 }  // namespace lbm
 

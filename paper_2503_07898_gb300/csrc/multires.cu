@@ -41,6 +41,7 @@
 #include "layout.h"
 
 namespace lbm {
+namespace LBM_LNS {
 
 // ---------------------------------------------------------------- host layout
 
@@ -114,8 +115,8 @@ lbm_status multires_build(Grid& g, const int fin[3], int L, const uint8_t* lmap)
       for (int k = 0; k < 27; ++k) {
         const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
         if (std::abs(dx) + std::abs(dy) + std::abs(dz) == 0 ||
-            std::abs(dx) + std::abs(dy) + std::abs(dz) == 3)
-          continue;  // D3Q19 reaches face and edge neighbours only
+            (Q == 19 && std::abs(dx) + std::abs(dy) + std::abs(dz) == 3))
+          continue;  // D3Q19 reaches face and edge neighbours only, D3Q27 corners too
         const int o = owner(l, wrapi(bx + dx, V.nbx), wrapi(by + dy, V.nby), wrapi(bz + dz, V.nbz));
         if (o == l) continue;
         const int t = o < l ? 1 : 2;
@@ -300,10 +301,15 @@ __device__ __forceinline__ bool mr_owns(const MrLv& v, int x, int y, int z) {
 // Velocity components by runtime index: the interface rules below run for a
 // few populations of a few voxels only, so they take the direction as a
 // runtime value and exist once in the kernel instead of once per direction.
+#if LBM_Q == 27
+#define MR_ROW(f)                                                                        \
+  {f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), \
+   f(14), f(15), f(16), f(17), f(18), f(19), f(20), f(21), f(22), f(23), f(24), f(25), f(26)}
+#else
 #define MR_ROW(f)                                                                        \
   {f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), \
    f(14), f(15), f(16), f(17), f(18)}
-static_assert(Q == 19, "multi-resolution grids are D3Q19");
+#endif
 __constant__ int8_t mr_c[3][Q] = {MR_ROW(cx), MR_ROW(cy), MR_ROW(cz)};
 #undef MR_ROW
 
@@ -383,7 +389,7 @@ template <> struct TmpCodec<S_F32> {
 };
 
 template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
-__global__ void __launch_bounds__(256, CLOSURE ? 3 : 4) mr_interface(MrArgs a) {
+__global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4)) mr_interface(MrArgs a) {
   using T = typename Codec<S>::T;
   const int64_t b = a.b0 + blockIdx.x / 2;
   extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
@@ -410,6 +416,7 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : 4) mr_interface(MrArgs a) {
   const int nZ = __ldg(nbr + 13 + 9 * ez);
   const int nXY = __ldg(nbr + 13 + ex + 3 * ey), nXZ = __ldg(nbr + 13 + ex + 9 * ez);
   const int nYZ = __ldg(nbr + 13 + 3 * ey + 9 * ez);
+  const int nXYZ = Q == 27 ? __ldg(nbr + 13 + ex + 3 * ey + 9 * ez) : bb;
   const int xp = (lx - 1) & 7, xn = (lx + 1) & 7;
   const int yp = ((ly - 1) & 7) * 8, yn = ((ly + 1) & 7) * 8, y0 = ly * 8;
   const int zp = ((lz - 1) & 7) * 64, zn = ((lz + 1) & 7) * 64, z0 = lz * 64;
@@ -421,20 +428,28 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : 4) mr_interface(MrArgs a) {
     const bool ky = Y != 0 && ey == -Y;
     const bool kz = Z != 0 && ez == -Z;
     nb = bb;
-    if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : bb);
+    if constexpr (X != 0 && Y != 0 && Z != 0)
+      nb = kz ? (kx ? (ky ? nXYZ : nXZ) : (ky ? nYZ : nZ)) : (kx ? (ky ? nXY : nX) : (ky ? nY : bb));
+    else if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : bb);
     else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : bb);
     else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : bb);
     else if constexpr (X != 0) nb = kx ? nX : bb;
     else if constexpr (Y != 0) nb = ky ? nY : bb;
     else if constexpr (Z != 0) nb = kz ? nZ : bb;
     bool plain = nb >= 0;
-    if constexpr ((X != 0) + (Y != 0) + (Z != 0) == 2) {
-      // a coarse voxel's subcells also trace through the two face neighbours
-      // of a 2D-diagonal direction; all of them must be on this level
+    if constexpr ((X != 0) + (Y != 0) + (Z != 0) >= 2) {
+      // a coarse voxel's subcells also trace through the face (and, for a
+      // corner direction, edge) neighbours the pull crosses; all of them
+      // must be on this level
       if (plain && jmp == 1) {
         if (kx && nX < 0) plain = false;
         if (ky && nY < 0) plain = false;
         if (kz && nZ < 0) plain = false;
+        if constexpr ((X != 0) + (Y != 0) + (Z != 0) == 3) {
+          if (kx && ky && nXY < 0) plain = false;
+          if (kx && kz && nXZ < 0) plain = false;
+          if (ky && kz && nYZ < 0) plain = false;
+        }
       }
     }
     return plain;
@@ -674,4 +689,5 @@ lbm_status multires_step(Grid& g, cudaStream_t s) {
   }
 }
 
+}  // namespace LBM_LNS
 }  // namespace lbm

@@ -1,4 +1,5 @@
-"""GPU: D3Q27 dense and block-sparse grids against the FP64 D3Q27 oracle.
+"""GPU: D3Q27 dense, block-sparse and multi-resolution grids against the FP64
+D3Q27 oracle.
 
 The paper runs its block-sparse register-pressure study on D3Q27 with
 regularized inflow and outflow (Sec. 6.2).  The same kernels as for D3Q19,
@@ -125,10 +126,11 @@ def test_mass_conservation_fp32(lbm):
 
 
 def test_d3q27_scope(lbm):
-    """Multi-resolution grids, the closure and batches are D3Q19."""
+    """The closure and batches are D3Q19."""
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_grid_create_multires((32, 32, 32), 2, np.zeros((1, 1, 1), np.uint8),
-                                     lbm.physics(0.6, periodic=(1, 1, 1), lattice=27))
+                                     lbm.physics(0.6, periodic=(1, 1, 1), lattice=27,
+                                                 closure=1))
     assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
     g27 = lbm.lbm_grid_create_dense((16, 16, 16), lbm.physics(0.6, periodic=(1, 1, 1),
                                                               lattice=27))
@@ -138,3 +140,81 @@ def test_d3q27_scope(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_grid_create_dense((16, 16, 16), lbm.physics(0.6, lattice=23))
     assert e.value.status == lbm.LBM_ERR_INVALID
+
+
+# ------------------------------------------------------ multi-resolution
+
+def _mr_fields(dims, n_levels, seed):
+    out = []
+    for lv in range(n_levels):
+        nx, ny, nz = (d >> lv for d in dims)
+        out.append(wl.random_fields((nz, ny, nx), seed=seed + lv, u_amp=0.02))
+    return out
+
+
+def _mr_compare(lbm, g, o, n_levels):
+    worst = 0.0
+    for lv in range(n_levels):
+        f = lbm.lbm_get_populations_f64(g, lv)
+        assert f.shape[0] == 27
+        m = o.own[lv] == lv
+        ref = o.f[lv][:, m]
+        worst = max(worst, float(np.max(np.abs(f[:, m] - ref) / np.abs(ref))))
+    return worst
+
+
+@pytest.mark.parametrize("collision,schedule,lmap", [
+    ("bgk", "disaggregated", (2, 1, 0, 1)),
+    ("reg", "disaggregated", (2, 1, 0, 1)),
+    ("bgk", "monolithic", (2, 1, 0, 1)),
+])
+def test_multires_parity(lbm, collision, schedule, lmap):
+    """Corner velocities across level jumps (explosion, coalescence)."""
+    from oracle import multires as omr
+    lm = np.array(lmap, np.uint8).reshape(4, 1, 1)
+    dims = (32, 32, 128)
+    g = lbm.lbm_grid_create_multires(dims, 3, lm, lbm.physics(
+        0.58, collision, "f32", (1, 1, 1), schedule, lattice=27))
+    o = omr.MultiRes(lm, 3, 32, 0.58, collision, q=27)
+    for lv, (r, u) in enumerate(_mr_fields(dims, 3, 170)):
+        lbm.lbm_init_equilibrium(g, lv, r, u)
+        o.init_equilibrium(lv, r, u)
+    lbm.lbm_step(g, 4)
+    o.run(4)
+    assert _mr_compare(lbm, g, o, 3) <= F32_RTOL
+
+
+def test_multires_cavity(lbm):
+    """Walls and the regularized lid on level 0, D3Q27."""
+    from cases import bc_list, oracle_bc
+    from oracle import multires as omr
+    n = 48
+    lmap = wl.multires_cavity_map(n, 2, (1,))
+    flags, bc = wl.cavity(n)
+    g = lbm.lbm_grid_create_multires((n,) * 3, 2, lmap, lbm.physics(0.6, lattice=27))
+    lbm.lbm_set_boundary(g, 0, flags, bc_list(flags, bc))
+    o = omr.MultiRes(lmap, 2, 16, 0.6, periodic=(False,) * 3, flags0=flags,
+                     bc0=oracle_bc(flags, bc), q=27)
+    rho, u = wl.random_fields((n,) * 3, seed=171, u_amp=0.02)
+    fields = [(rho, u), (omr.subcell_mean(rho), omr.subcell_mean(u))]
+    for lv, (r, v) in enumerate(fields):
+        lbm.lbm_init_equilibrium(g, lv, r, v)
+        o.init_equilibrium(lv, r, v)
+    lbm.lbm_step(g, 3)
+    o.run(3)
+    assert _mr_compare(lbm, g, o, 2) <= F32_RTOL
+
+
+def test_multires_fused_equals_unfused(lbm):
+    lm = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
+    dims = (32, 32, 128)
+    out = []
+    for schedule in ("disaggregated", "monolithic"):
+        g = lbm.lbm_grid_create_multires(dims, 3, lm, lbm.physics(
+            0.58, "bgk", "f32", (1, 1, 1), schedule, lattice=27))
+        for lv, (r, u) in enumerate(_mr_fields(dims, 3, 172)):
+            lbm.lbm_init_equilibrium(g, lv, r, u)
+        lbm.lbm_step(g, 5)
+        out.append([lbm.lbm_get_populations_f64(g, lv) for lv in range(3)])
+    for a, b in zip(*out):
+        assert np.array_equal(np.nan_to_num(a, nan=-1.0), np.nan_to_num(b, nan=-1.0))

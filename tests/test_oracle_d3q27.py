@@ -183,3 +183,83 @@ def test_poiseuille_regularized_inlet_outlet():
     assert np.max(np.abs(u[0, 0, :, mid] / prof - 1)) < 2e-3
     drho = (rho[0, H // 2, NX - 4] - rho[0, H // 2, 3]) / (NX - 7)
     assert abs(drho / (-24 * nu * umax / H ** 2) - 1) < 1e-2
+
+
+# ------------------------------------------------------ multi-resolution
+
+def _mr(lmap, n_levels, cell, tau, **kw):
+    from oracle import multires as mr
+    return mr.MultiRes(np.asarray(lmap), n_levels, cell, tau, q=27, **kw)
+
+
+def _init_random(g, seed):
+    for lv in range(g.L):
+        nx, ny, nz = g.dims(lv)
+        rho, u = wl.random_fields((nz, ny, nx), seed=seed + lv)
+        g.init_equilibrium(lv, rho, u)
+
+
+@pytest.mark.parametrize("collision", ["bgk", "reg"])
+def test_multires_volume_weighted_conservation_exact(collision):
+    """Corner directions cross the level jumps too: mass and momentum,
+    weighted by voxel volume, are still conserved exactly."""
+    g = _mr(np.array([2, 1, 0, 1]).reshape(4, 1, 1), 3, 8, 0.6, collision=collision)
+    _init_random(g, 160)
+    m0 = g.conservation()
+    g.run(4)
+    m1 = g.conservation()
+    assert g.f[0].shape[0] == 27
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-12
+    assert np.all(np.abs(m1[1:] - m0[1:]) < 1e-12 * m0[0])
+
+
+def test_multires_uniform_state_is_stationary():
+    g = _mr(np.array([2, 1, 0, 1]).reshape(4, 1, 1), 3, 8, 0.57)
+    for lv in range(3):
+        nx, ny, nz = g.dims(lv)
+        u = np.zeros((3, nz, ny, nx))
+        u[:] = np.array([0.02, -0.01, 0.03])[:, None, None, None]
+        g.init_equilibrium(lv, np.full((nz, ny, nx), 1.01), u)
+    f0 = [a.copy() for a in g.f]
+    g.run(3)
+    for a, b in zip(f0, g.f):
+        assert np.max(np.abs(a - b)) < 1e-15
+
+
+def test_multires_single_level_equals_plain_oracle():
+    g = _mr(np.zeros((1, 1, 1), int), 1, 12, 0.6)
+    rho, u = wl.random_fields((12, 12, 12), seed=161)
+    g.init_equilibrium(0, rho, u)
+    g.run(4)
+    ref = lbm.run(lbm.init_equilibrium(rho, u, q=27), np.zeros((12, 12, 12), np.uint8), 0.6, 4,
+                  periodic=(True, True, True))
+    assert np.max(np.abs(g.f[0] - ref)) < 1e-15
+
+
+def test_multires_cavity_near_walls_equals_single_resolution():
+    from oracle import multires as mr
+    n, T = 48, 3
+    lmap = wl.multires_cavity_map(n, 2, (1,))
+    flags, bc = wl.cavity(n)
+    rho, u = wl.random_fields((n,) * 3, seed=162, u_amp=0.02)
+    g = _mr(lmap, 2, 16, 0.6, periodic=(False,) * 3, flags0=flags, bc0=bc)
+    g.init_equilibrium(0, rho, u)
+    g.init_equilibrium(1, mr.subcell_mean(rho), mr.subcell_mean(u))
+    g.run(T)
+    ref = lbm.run(lbm.init_equilibrium(rho, u, flags, q=27), flags, 0.6, 2 * T, bc=bc)
+    c = np.arange(n)
+    d1 = np.maximum(np.maximum(16 - c, c - 31), 0)
+    dist = np.maximum(np.maximum(d1[:, None, None], d1[None, :, None]), d1[None, None, :])
+    far = dist > 2 * T + 4
+    assert np.max(np.abs(g.f[0][:, far] - ref[:, far])) < 1e-15
+
+
+def test_multires_tables_count_corner_neighbours():
+    """A level-0 block that meets level 1 only across a block corner is G_c
+    for D3Q27 and G_i for D3Q19."""
+    from oracle import layout
+    lmap = np.zeros((2, 2, 2), np.uint8)
+    lmap[1, 1, 1] = 1                       # one coarse cell at the far corner
+    t19 = layout.multires_tables(lmap, 2, 16, q=19)
+    t27 = layout.multires_tables(lmap, 2, 16, q=27)
+    assert t27[0]["n_c"] > t19[0]["n_c"]
