@@ -235,9 +235,16 @@ enum {
   LBM_LAYOUT_XNBR_FINE = 5,    /* int32  n_blocks x 27 x 8 (multi-res)         */
   LBM_LAYOUT_BOUNDARY_BITS = 6,/* uint32 ceil(n_blocks / 32): bit b % 32 of word
                                   b / 32 = block b is a boundary block (BITMASK) */
-  LBM_LAYOUT_BC_INDEX = 7      /* int32  n_blocks x E^3: rank of the slot's
+  LBM_LAYOUT_BC_INDEX = 7,     /* int32  n_blocks x E^3: rank of the slot's
                                   regularized voxel in flag-scan order, or -1
                                   (BITMASK)                                     */
+  LBM_LAYOUT_IFACE_SLOTS = 8,  /* int32  n_iface: slots (block * 512 + voxel) of
+                                  the level's interface voxels, ascending: the
+                                  voxels with a pull whose value depends on
+                                  another level (multi-res; Sec. 5, P_d = 0) */
+  LBM_LAYOUT_IFACE_CROSS = 9   /* uint32 n_iface: bit i = population i of that
+                                  voxel comes from explosion (from the coarser
+                                  level) or coalescence (from the finer one)  */
 };
 /* Copy one host-side layout table (for bit-exact checks).  bytes must equal
  * the table's size; lbm_layout_bytes reports it. */

@@ -177,3 +177,53 @@ def multires_tables(level_map, n_levels, cell, block_edge=8, q=19):
                         xf[b, k, j] = bmaps[lv - 1][f]
         t.update(nbr=nbr, xnbr_coarse=xc, xnbr_fine=xf)
     return out
+
+
+def multires_interface(level_map, n_levels, cell, q=19):
+    """Interface voxels of every level and the populations they read from
+    another level's buffers (Sec. 5: voxels with P_d = 0; exchange as in
+    oracle.multires, whose reading of the two-substep exchange it follows).
+
+    Population i of a voxel G owned by level l is read from another level iff
+      explosion:   the voxel G - c_i belongs to level l+1, or
+      coalescence: one of the 8 subcells p of G reads level-(l-1) data in the
+                   two virtual substeps, i.e. the level-(l-1) voxel p - c_i or
+                   p - 2 c_i belongs to level l-1 (otherwise all 8 subcells
+                   read G - c_i of level l and their mean is the plain pull).
+    Returns one (slots, cross) pair per level: slot = block * 512 + x + 8 y +
+    64 z (block ids of multires_tables, voxel inside the 8^3 block) in
+    ascending order, cross = uint32 bit set of those populations.
+    """
+    from .lattice import lattice
+    C = lattice(q).C
+    level_map = np.asarray(level_map)
+    tabs = multires_tables(level_map, n_levels, cell, q=q)
+    own = []
+    for lv in range(n_levels):
+        r = cell // (2 ** lv)
+        own.append(level_map.repeat(r, 0).repeat(r, 1).repeat(r, 2))
+
+    def at(a, c, k):  # value at x - k c, periodic (axes z, y, x)
+        return np.roll(a, shift=(k * int(c[2]), k * int(c[1]), k * int(c[0])), axis=(0, 1, 2))
+
+    out = []
+    for lv in range(n_levels):
+        o = own[lv]
+        cross = np.zeros(o.shape, np.uint32)
+        for i in range(1, len(C)):
+            dep = np.zeros(o.shape, bool)
+            if lv + 1 < n_levels:
+                dep |= at(o, C[i], 1) == lv + 1
+            if lv > 0:
+                fine = own[lv - 1] == lv - 1
+                reads = at(fine, C[i], 1) | at(fine, C[i], 2)
+                for j in range(8):
+                    dep |= reads[(j >> 2)::2, ((j >> 1) & 1)::2, (j & 1)::2]
+            cross |= np.where(dep & (o == lv), np.uint32(1 << i), np.uint32(0))
+        bmap = {tuple(int(v) for v in c): b for b, c in enumerate(tabs[lv]["coords"])}
+        zz, yy, xx = np.nonzero(cross)
+        slots = np.array([bmap[(x // 8, y // 8, z // 8)] * 512 + (x % 8) + 8 * (y % 8) + 64 * (z % 8)
+                          for x, y, z in zip(xx, yy, zz)], dtype=np.int64)
+        order = np.argsort(slots, kind="stable")
+        out.append((slots[order].astype(np.int32), cross[zz, yy, xx][order]))
+    return out

@@ -26,6 +26,7 @@ LBM_SCHEDULE_DISAGGREGATED, LBM_SCHEDULE_MONOLITHIC = 0, 1
 LBM_LAYOUT_FLAGS, LBM_LAYOUT_BLOCK_COORDS, LBM_LAYOUT_NBR = 0, 1, 2
 LBM_LAYOUT_BLOCK_MAP, LBM_LAYOUT_XNBR_COARSE, LBM_LAYOUT_XNBR_FINE = 3, 4, 5
 LBM_LAYOUT_BOUNDARY_BITS, LBM_LAYOUT_BC_INDEX = 6, 7
+LBM_LAYOUT_IFACE_SLOTS, LBM_LAYOUT_IFACE_CROSS = 8, 9
 SCHEDULES = {"disaggregated": 0, "monolithic": 1, "bitmask": 2}
 
 
@@ -373,7 +374,8 @@ def lbm_get_layout(grid, level, what):
     lib = load()
     _check(lib.lbm_layout_bytes(grid.ptr, int(level), int(what), C.byref(n)), "lbm_layout_bytes")
     dtype = (np.uint8 if what == LBM_LAYOUT_FLAGS
-             else np.uint32 if what == LBM_LAYOUT_BOUNDARY_BITS else np.int32)
+             else np.uint32 if what in (LBM_LAYOUT_BOUNDARY_BITS, LBM_LAYOUT_IFACE_CROSS)
+             else np.int32)
     out = np.empty(n.value // np.dtype(dtype).itemsize, dtype)
     _check(lib.lbm_get_layout(grid.ptr, int(level), int(what), C.c_void_p(out.ctypes.data),
                               n.value), "lbm_get_layout")

@@ -106,6 +106,8 @@ static void free_level(Grid& g, Level& L) {
   g.dfree(L.blk_walls_d, s);
   g.dfree(L.bnd_bits_d, s);
   g.dfree(L.reg_blocks_d, s);
+  g.dfree(L.iface_slot_d, s);
+  g.dfree(L.iface_cross_d, s);
   g.dfree(L.bc_idx_d, s);
   g.dfree(L.bc_cmp_d, s);
   L = Level();
@@ -124,6 +126,14 @@ static void free_grid(Grid& g) {
     g.mr_aux[l] = nullptr;
     g.mr_fork[l] = g.mr_join[l] = nullptr;
   }
+  if (g.mr_hi) {
+    cudaStreamSynchronize(g.mr_hi);
+    cudaStreamDestroy(g.mr_hi);
+  }
+  if (g.mr_in) cudaEventDestroy(g.mr_in);
+  if (g.mr_out) cudaEventDestroy(g.mr_out);
+  g.mr_hi = nullptr;
+  g.mr_in = g.mr_out = nullptr;
   for (int l = 0; l < 4; ++l) free_level(g, g.lv[l]);
   g.dfree(g.status_d, g.stream);
   g.dfree(g.partials_d, g.stream);
@@ -400,6 +410,7 @@ lbm_status lbm_grid_create_multires(const int finest_dims[3], int n_levels,
       }
     }
   }
+  if ((st = g.q == 27 ? q27::multires_finish(g) : q19::multires_finish(g))) return bail(st);
   LBM_CUDA(cudaStreamSynchronize(g.stream));
   return LBM_OK;
 }
@@ -589,7 +600,7 @@ lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
                                                : q19::dense_step(g, g.lv[0], s))
                     : g.kind == 1 ? (g.q == 27 ? q27::sparse_step(g, g.lv[0], s)
                                                : q19::sparse_step(g, g.lv[0], s))
-                                  : (g.q == 27 ? q27::multires_step(g, s) : q19::multires_step(g, s));
+                                  : (g.q == 27 ? q27::multires_step(g, s, k == 0) : q19::multires_step(g, s, k == 0));
     if (st) return st;
     ++g.steps_done;
   }
@@ -716,6 +727,11 @@ lbm_status lbm_layout_bytes(const lbm_grid* h, int level, int what, size_t* byte
       if (!L.bitmask) break;
       *bytes = L.bc_idx_h.size() * 4;
       return LBM_OK;
+    case LBM_LAYOUT_IFACE_SLOTS:
+    case LBM_LAYOUT_IFACE_CROSS:
+      if (g.kind != 2) break;
+      *bytes = (size_t)L.n_iface * 4;
+      return LBM_OK;
     default: break;
   }
   return fail(LBM_ERR_UNSUPPORTED, "layout table not available for this grid");
@@ -734,6 +750,8 @@ lbm_status lbm_get_layout(const lbm_grid* h, int level, int what, void* dst, siz
                     : what == LBM_LAYOUT_XNBR_COARSE ? (const void*)L.xnbr_coarse_h.data()
                     : what == LBM_LAYOUT_XNBR_FINE ? (const void*)L.xnbr_fine_h.data()
                     : what == LBM_LAYOUT_BOUNDARY_BITS ? (const void*)L.bnd_bits_h.data()
+                    : what == LBM_LAYOUT_IFACE_SLOTS ? (const void*)L.iface_slot_h.data()
+                    : what == LBM_LAYOUT_IFACE_CROSS ? (const void*)L.iface_cross_h.data()
                                                        : (const void*)L.bc_idx_h.data();
   if (need) std::memcpy(dst, src, need);
   return LBM_OK;

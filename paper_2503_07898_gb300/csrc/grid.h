@@ -51,6 +51,14 @@ struct Level {
   int32_t* coords_d = nullptr;
   std::vector<int32_t> xnbr_coarse_h; // n_blocks x 27
   std::vector<int32_t> xnbr_fine_h;   // n_blocks x 27 x 8
+  // interface voxels (a pull leaves the level): slot and the bit set of the
+  // directions whose pull does; every other voxel of the level runs the lean
+  // kernel, which the per-slot mask keeps off these
+  std::vector<int32_t> iface_slot_h;
+  std::vector<uint32_t> iface_cross_h;
+  int32_t* iface_slot_d = nullptr;
+  uint32_t* iface_cross_d = nullptr;
+  int64_t n_iface = 0;
 
   // host tables
   std::vector<uint8_t> flags_h;       // virtual box
@@ -106,10 +114,13 @@ struct Grid {
   int64_t steps_done = 0;
 
   // multi-resolution: a second stream per level for the G_i launch, which
-  // overlaps the finer substeps and the G_c launch of its level
+  // overlaps the finer substeps and the G_c launch of its level; the G_c
+  // launches (the critical path) run on a high-priority stream
   cudaStream_t mr_aux[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t mr_fork[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t mr_join[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t mr_hi = nullptr;
+  cudaEvent_t mr_in = nullptr, mr_out = nullptr;
 
   // learned closure (multi-resolution levels >= 1)
   void* closure_d = nullptr;     // ClosureParams on the device
@@ -152,7 +163,8 @@ void prof_clear(Grid& g);
   lbm_status launch_conservation(Grid& g, double* out4, cudaStream_t s);                    \
   lbm_status multires_build(Grid& g, const int finest[3], int n_levels,                      \
                             const uint8_t* level_map);                                       \
-  lbm_status multires_step(Grid& g, cudaStream_t s);                                         \
+  lbm_status multires_finish(Grid& g);                                                       \
+  lbm_status multires_step(Grid& g, cudaStream_t s, bool first);                             \
   lbm_status multires_set_boundary(Grid& g, const uint8_t* flags, const float* bc_values,    \
                                    const float* def_bc);
 namespace q19 {

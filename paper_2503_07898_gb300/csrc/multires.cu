@@ -47,6 +47,74 @@ namespace LBM_LNS {
 
 static inline int wrapi(int v, int n) { return ((v % n) + n) % n; }
 
+// Directions whose pull from voxel l of block b leaves the level: the source
+// block belongs to another level or, in a block next to a finer level
+// (jump 1), a pull with two or three nonzero components crosses a face (or,
+// for a corner direction, edge) neighbour block of another level, through
+// which the subcells of the voxel trace.  mr_interface evaluates the same
+// rule on the device.
+static uint32_t mr_cross(const Level& V, int64_t b, int l) {
+  const int lc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+  int e[3];
+  for (int a = 0; a < 3; ++a) e[a] = lc[a] == 0 ? -1 : (lc[a] == 7 ? 1 : 0);
+  const int32_t* nb = &V.nbr_h[(size_t)b * 27];
+  auto at = [&](int dx, int dy, int dz) { return nb[13 + dx + 3 * dy + 9 * dz]; };
+  const int jmp = V.jump_h[(size_t)b];
+  uint32_t m = 0;
+  for (int i = 1; i < Q; ++i) {
+    const int c[3] = {cx(i), cy(i), cz(i)};
+    bool k[3];
+    int d[3], nnz = 0;
+    for (int a = 0; a < 3; ++a) {
+      k[a] = c[a] != 0 && e[a] == -c[a];
+      d[a] = k[a] ? e[a] : 0;
+      nnz += c[a] != 0;
+    }
+    bool plain = at(d[0], d[1], d[2]) >= 0;
+    if (plain && jmp == 1 && nnz >= 2) {
+      if ((k[0] && at(e[0], 0, 0) < 0) || (k[1] && at(0, e[1], 0) < 0) || (k[2] && at(0, 0, e[2]) < 0))
+        plain = false;
+      if (nnz == 3 && ((k[0] && k[1] && at(e[0], e[1], 0) < 0) || (k[0] && k[2] && at(e[0], 0, e[2]) < 0) ||
+                       (k[1] && k[2] && at(0, e[1], e[2]) < 0)))
+        plain = false;
+    }
+    if (!plain) m |= 1u << i;
+  }
+  return m;
+}
+
+// The interface voxels of a level (all in G_c blocks) in slot order.
+static void mr_iface_list(Level& V) {
+  V.iface_slot_h.clear();
+  V.iface_cross_h.clear();
+  for (int64_t b = 0; b < V.n_c; ++b)
+    for (int l = 0; l < 512; ++l) {
+      const uint32_t m = mr_cross(V, b, l);
+      if (!m) continue;
+      V.iface_slot_h.push_back((int32_t)(b * 512 + l));
+      V.iface_cross_h.push_back(m);
+    }
+  V.n_iface = (int64_t)V.iface_slot_h.size();
+}
+
+// Mark the interface voxels in a per-slot lean-kernel mask (bit 31) and their
+// blocks in the per-block mask bits.
+static void mr_iface_masks(const Level& V, std::vector<uint32_t>& wm, std::vector<uint8_t>& bw) {
+  for (int64_t k = 0; k < V.n_iface; ++k) {
+    const int32_t sl = V.iface_slot_h[(size_t)k];
+    wm[(size_t)sl] |= 1u << 31;
+    bw[(size_t)(sl / 512)] = 1;
+  }
+}
+
+static lbm_status mr_upload(Grid& g, void** dst, const void* src, size_t bytes) {
+  g.dfree(*dst, g.stream);
+  *dst = g.dalloc(bytes + 16, g.stream);
+  if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
+  if (bytes) LBM_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
 lbm_status multires_build(Grid& g, const int fin[3], int L, const uint8_t* lmap) {
   if (L < 1 || L > 4) return fail(LBM_ERR_INVALID, "n_levels must be 1..4");
   const int C = 8 << (L - 1);  // level-map cell (finest voxels) = coarsest block
@@ -177,6 +245,27 @@ lbm_status multires_build(Grid& g, const int fin[3], int L, const uint8_t* lmap)
         }
       }
   }
+  // pass 3: interface voxels
+  for (int l = 0; l < L; ++l) mr_iface_list(g.lv[l]);
+  return LBM_OK;
+}
+
+// Per-slot mask of the lean kernel (bit 31: the voxel is left to the
+// interface kernel) and per-block mask bit, for every level; level 0 merges
+// them with its walls in multires_set_boundary.  Uploads the interface lists.
+lbm_status multires_finish(Grid& g) {
+  for (int l = 0; l < g.n_levels; ++l) {
+    Level& V = g.lv[l];
+    std::vector<uint32_t> wm((size_t)V.n_slots, 0u);
+    std::vector<uint8_t> bw((size_t)V.n_blocks, 0);
+    mr_iface_masks(V, wm, bw);
+    lbm_status st;
+    if ((st = mr_upload(g, (void**)&V.wmask_d, wm.data(), wm.size() * 4)) ||
+        (st = mr_upload(g, (void**)&V.blk_walls_d, bw.data(), bw.size())) ||
+        (st = mr_upload(g, (void**)&V.iface_slot_d, V.iface_slot_h.data(), V.iface_slot_h.size() * 4)) ||
+        (st = mr_upload(g, (void**)&V.iface_cross_d, V.iface_cross_h.data(), V.iface_cross_h.size() * 4)))
+      return st;
+  }
   return LBM_OK;
 }
 
@@ -246,22 +335,17 @@ lbm_status multires_set_boundary(Grid& g, const uint8_t* flags, const float* bc_
       return fail(LBM_ERR_UNSUPPORTED, "walls and boundary nodes must lie in G_i blocks of level 0");
     if (has_reg) regb.push_back((int32_t)b);
   }
+  // the interface voxels of the G_c blocks stay off the lean kernel
+  mr_iface_masks(V, wm, bw);
   V.flags_h.swap(fl);
   V.n_updated = n_upd;
   V.n_reg = n_reg;
   V.n_reg_blocks = (int64_t)regb.size();
-  auto upload = [&](void** dst, const void* src, size_t bytes) -> lbm_status {
-    g.dfree(*dst, g.stream);
-    *dst = g.dalloc(bytes + 16, g.stream);
-    if (!*dst) return fail(LBM_ERR_OOM, "device allocation failed");
-    if (bytes) LBM_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
-    return LBM_OK;
-  };
   lbm_status st;
-  if ((st = upload((void**)&V.flags_d, sf.data(), sf.size())) ||
-      (st = upload((void**)&V.wmask_d, wm.data(), wm.size() * 4)) ||
-      (st = upload((void**)&V.blk_walls_d, bw.data(), bw.size())) ||
-      (st = upload((void**)&V.reg_blocks_d, regb.data(), regb.size() * 4)))
+  if ((st = mr_upload(g, (void**)&V.flags_d, sf.data(), sf.size())) ||
+      (st = mr_upload(g, (void**)&V.wmask_d, wm.data(), wm.size() * 4)) ||
+      (st = mr_upload(g, (void**)&V.blk_walls_d, bw.data(), bw.size())) ||
+      (st = mr_upload(g, (void**)&V.reg_blocks_d, regb.data(), regb.size() * 4)))
     return st;
   return sparse_set_bc(g, V, bc_values, def_bc);
 }
@@ -402,8 +486,7 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4)) mr_inter
   const int32_t* __restrict__ nbr = a.nbr + b * 27;
   const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-  const int gx = a.coords[b * 3] * 8 + lx, gy = a.coords[b * 3 + 1] * 8 + ly,
-            gz = a.coords[b * 3 + 2] * 8 + lz;
+  const int ox = a.coords[b * 3] * 8, oy = a.coords[b * 3 + 1] * 8, oz = a.coords[b * 3 + 2] * 8;
   const int jmp = a.jump[b];
   const T* __restrict__ cur = (const T*)a.cur;
   // same-level pulls: the blocks a pull can enter are looked up once per
@@ -461,13 +544,46 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4)) mr_inter
     if (!source(ic, nb)) cross |= 1u << decltype(ic)::value;
   });
   // 2. their values by explosion (from the coarser level) or coalescence
-  // (from the finer one), one direction at a time, parked in this thread's
-  // column of shared memory so that no population is live across the loop
-  for (uint32_t m = cross; m; m &= m - 1) {
-    const int i = __ffs(m) - 1;
-    const int ccx = mr_c[0][i], ccy = mr_c[1][i], ccz = mr_c[2][i];
-    mr_slow[i][threadIdx.x] = jmp == 2 ? explosion<S>(a, i, ccx, ccy, ccz, gx, gy, gz)
-                                       : coalescence<S>(a, i, ccx, ccy, ccz, gx, gy, gz);
+  // (from the finer one).  Only the voxels on a block face next to another
+  // level have such pulls, so the (voxel, direction) pairs of the whole CTA
+  // are listed and spread over all its threads: each pair is a chain of
+  // dependent lookups, and one lane working through its own five or more
+  // would hold up the CTA.  The values are parked in the owning thread's
+  // column of shared memory, so no population is live across the loop.
+  __shared__ uint16_t mr_work[256 * (Q - 1)];  // (thread << 5) | direction
+  __shared__ int mr_wcount[8];
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = __popc(cross);
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (lane == 31) mr_wcount[warp] = incl;
+    __syncthreads();
+    int pos = incl - n, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const int c = mr_wcount[w];
+      pos += w < warp ? c : 0;
+      total += c;
+    }
+    for (uint32_t m = cross; m; m &= m - 1) mr_work[pos++] = (uint16_t)((threadIdx.x << 5) | (__ffs(m) - 1));
+    if (total > 0) {  // uniform per CTA
+      __syncthreads();
+      for (int e = threadIdx.x; e < total; e += 256) {
+        const int w = mr_work[e];
+        const int t = w >> 5, i = w & 31;
+        const int tl = (blockIdx.x & 1) * 256 + t;
+        const int gx = ox + (tl & 7), gy = oy + ((tl >> 3) & 7), gz = oz + (tl >> 6);
+        const int ccx = mr_c[0][i], ccy = mr_c[1][i], ccz = mr_c[2][i];
+        mr_slow[i][t] = jmp == 2 ? explosion<S>(a, i, ccx, ccy, ccz, gx, gy, gz)
+                                 : coalescence<S>(a, i, ccx, ccy, ccz, gx, gy, gz);
+      }
+      __syncthreads();
+    }
   }
   // 3. the same-level pulls
   float g[Q];
@@ -519,6 +635,76 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4)) mr_inter
       out[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
     });
   }
+}
+
+// Interface voxels of the fused schedule, one thread each (the list holds
+// only voxels with a pull that leaves the level; the lean kernel updates the
+// rest of their blocks).  Cross-level values first, parked in the thread's
+// shared-memory column, then the same-level pulls, collision and store.
+template <int S, int COLL>
+__global__ void __launch_bounds__(256, Q == 27 ? 3 : 4)
+    mr_iface(MrArgs a, const int32_t* __restrict__ slots, const uint32_t* __restrict__ crosses,
+             int n) {
+  using T = typename Codec<S>::T;
+  __shared__ float mr_slow[Q][256];
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  if (t >= n) return;
+  const int slot = slots[t];
+  const uint32_t cross = crosses[t];
+  const int b = slot >> 9, l = slot & 511;
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+  const int jmp = a.jump[b];
+  {
+    const int gx = a.coords[b * 3] * 8 + lx, gy = a.coords[b * 3 + 1] * 8 + ly,
+              gz = a.coords[b * 3 + 2] * 8 + lz;
+    for (uint32_t m = cross; m; m &= m - 1) {
+      const int i = __ffs(m) - 1;
+      const int ccx = mr_c[0][i], ccy = mr_c[1][i], ccz = mr_c[2][i];
+      mr_slow[i][threadIdx.x] = jmp == 2 ? explosion<S>(a, i, ccx, ccy, ccz, gx, gy, gz)
+                                         : coalescence<S>(a, i, ccx, ccy, ccz, gx, gy, gz);
+    }
+  }
+  const int32_t* __restrict__ nbr = a.nbr + (int64_t)b * 27;
+  const int ex = lx == 0 ? -1 : (lx == 7 ? 1 : 0);
+  const int ey = ly == 0 ? -1 : (ly == 7 ? 1 : 0);
+  const int ez = lz == 0 ? -1 : (lz == 7 ? 1 : 0);
+  const int nX = __ldg(nbr + 13 + ex), nY = __ldg(nbr + 13 + 3 * ey);
+  const int nZ = __ldg(nbr + 13 + 9 * ez);
+  const int nXY = __ldg(nbr + 13 + ex + 3 * ey), nXZ = __ldg(nbr + 13 + ex + 9 * ez);
+  const int nYZ = __ldg(nbr + 13 + 3 * ey + 9 * ez);
+  const int nXYZ = Q == 27 ? __ldg(nbr + 13 + ex + 3 * ey + 9 * ez) : b;
+  const int xp = (lx - 1) & 7, xn = (lx + 1) & 7;
+  const int yp = ((ly - 1) & 7) * 8, yn = ((ly + 1) & 7) * 8, y0 = ly * 8;
+  const int zp = ((lz - 1) & 7) * 64, zn = ((lz + 1) & 7) * 64, z0 = lz * 64;
+  const T* __restrict__ cur = (const T*)a.cur;
+  float g[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+    if ((cross >> I) & 1u) {
+      g[I] = mr_slow[I][threadIdx.x];
+    } else {
+      const bool kx = X != 0 && ex == -X, ky = Y != 0 && ey == -Y, kz = Z != 0 && ez == -Z;
+      int nb = b;
+      if constexpr (X != 0 && Y != 0 && Z != 0)
+        nb = kz ? (kx ? (ky ? nXYZ : nXZ) : (ky ? nYZ : nZ)) : (kx ? (ky ? nXY : nX) : (ky ? nY : b));
+      else if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : b);
+      else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : b);
+      else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : b);
+      else if constexpr (X != 0) nb = kx ? nX : b;
+      else if constexpr (Y != 0) nb = ky ? nY : b;
+      else if constexpr (Z != 0) nb = kz ? nZ : b;
+      const int ls = (X > 0 ? xp : (X < 0 ? xn : lx)) + (Y > 0 ? yp : (Y < 0 ? yn : y0)) +
+                     (Z > 0 ? zp : (Z < 0 ? zn : z0));
+      g[I] = Codec<S>::template load<I>(cur[(int64_t)nb * (Q * 512) + (I * 512 + ls)]);
+    }
+  });
+  collide<COLL>(g, a.omega);
+  T* __restrict__ out = (T*)a.out;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    out[((int64_t)b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
+  });
 }
 
 // Unfused baseline: collision of the pre-collision values written by the
@@ -576,6 +762,16 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
   const bool unfused = g.phys.schedule == LBM_SCHEDULE_MONOLITHIC && l > 0;
   const bool closure = g.phys.closure && g.closure_loaded && l > 0;
   const size_t csm = closure ? sizeof(ClosureCta) : 0;
+  if (closure) {
+    // static shared memory (interface values and work list) plus the
+    // network's dynamic part exceed the default 48 KB per CTA
+    static bool opted_in = false;
+    if (!opted_in) {
+      LBM_CUDA(cudaFuncSetAttribute(mr_interface<S, COLL, false, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      opted_in = true;
+    }
+  }
   lbm_status st;
   MrArgs a{};
   a.me = view(V);
@@ -594,13 +790,20 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
     a.co = view(W);
     a.ccur = W.f[W.cur];
   }
-  // G_i blocks need no cross-level data and share no output with the rest of
-  // this substep: launched first, on the level's second stream, they overlap
-  // the finer substeps and this level's G_c launch; joined before returning
-  const bool fork = !unfused && V.n_blocks > V.n_c;
+  // Fused schedule: every voxel without a cross-level pull (all of G_i and
+  // most of G_c) runs the lean kernel, which needs no cross-level data and
+  // shares no output with the interface voxels: launched first, on the
+  // level's second stream, it overlaps the finer substeps and this level's
+  // interface launch; joined before returning.  It waits only for this
+  // level's previous step (mr_fork, recorded when it completed), so it also
+  // overlaps the coarser levels' interface launches that run between two
+  // steps of this level.  Those read this level's ring buffers only at its
+  // interface voxels (next to another level), which the lean kernel never
+  // writes.  With the closure, G_i blocks run mr_interface there instead and
+  // G_c blocks run it whole.
+  const bool fork = !unfused && (closure ? V.n_blocks > V.n_c : V.n_blocks > 0);
   const cudaStream_t s_main = s;
   if (fork) {
-    LBM_CUDA(cudaEventRecord(g.mr_fork[l], s_main));
     LBM_CUDA(cudaStreamWaitEvent(g.mr_aux[l], g.mr_fork[l], 0));
     s = g.mr_aux[l];
     if (closure) {
@@ -612,10 +815,10 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
       mr_interface<S, COLL, false, true><<<(unsigned)(2 * (V.n_blocks - V.n_c)), 256, csm, s>>>(ai);
       prof_end(g, s, pr);
     } else {
-      st = sparse_uniform_range(g, V, V.n_c, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
-                                V.n_updated - V.n_c * 512 - V.n_reg);
+      st = sparse_uniform_range(g, V, 0, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
+                                V.n_updated - V.n_iface - V.n_reg);
       if (st) return st;
-      // regularized boundary voxels (a lid on level 0) of those blocks
+      // regularized boundary voxels (a lid on level 0, in G_i blocks)
       if ((st = sparse_reg_blocks(g, V, V.f[c], V.f[nx], omega, s, "mr_regularized_l0"))) return st;
     }
     LBM_CUDA(cudaEventRecord(g.mr_join[l], s));
@@ -644,24 +847,32 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
       mr_collide<S, COLL><<<nb, 256, 0, s>>>(V.tmp, V.f[nx], 0, V.n_blocks, omega);
       prof_end(g, s, pr);
     }
-  } else if (V.n_c > 0) {
-    a.b0 = 0;
-    a.b1 = V.n_c;
-    a.out = V.f[nx];
-    const int pr = prof_begin(g, s, kname(1, l), V.n_c * 512);
-    if (closure)
+  } else if (closure) {
+    if (V.n_c > 0) {
+      a.b0 = 0;
+      a.b1 = V.n_c;
+      a.out = V.f[nx];
+      const int pr = prof_begin(g, s, kname(1, l), V.n_c * 512);
       mr_interface<S, COLL, false, true><<<(unsigned)(2 * V.n_c), 256, csm, s>>>(a);
-    else
-      mr_interface<S, COLL, false><<<(unsigned)(2 * V.n_c), 256, 0, s>>>(a);
+      prof_end(g, s, pr);
+    }
+  } else if (V.n_iface > 0) {
+    a.out = V.f[nx];
+    const int pr = prof_begin(g, s, kname(1, l), V.n_iface);
+    mr_iface<S, COLL><<<(unsigned)((V.n_iface + 255) / 256), 256, 0, s>>>(
+        a, V.iface_slot_d, V.iface_cross_d, (int)V.n_iface);
     prof_end(g, s, pr);
   }
   LBM_CUDA(cudaGetLastError());
-  if (fork) LBM_CUDA(cudaStreamWaitEvent(s, g.mr_join[l], 0));
+  if (fork) {
+    LBM_CUDA(cudaStreamWaitEvent(s, g.mr_join[l], 0));
+    LBM_CUDA(cudaEventRecord(g.mr_fork[l], s));
+  }
   V.cur = nx;
   return LBM_OK;
 }
 
-lbm_status multires_step(Grid& g, cudaStream_t s) {
+lbm_status multires_step(Grid& g, cudaStream_t s, bool first) {
   const int top = g.n_levels - 1;
   if (g.phys.closure && !g.closure_loaded)
     return fail(LBM_ERR_INVALID, "closure enabled but no weights loaded (lbm_closure_load)");
@@ -676,17 +887,39 @@ lbm_status multires_step(Grid& g, cudaStream_t s) {
       }
     }
   }
+  if (!g.mr_hi) {
+    int least = 0, greatest = 0;
+    LBM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    LBM_CUDA(cudaStreamCreateWithPriority(&g.mr_hi, cudaStreamNonBlocking, greatest));
+    LBM_CUDA(cudaEventCreateWithFlags(&g.mr_in, cudaEventDisableTiming));
+    LBM_CUDA(cudaEventCreateWithFlags(&g.mr_out, cudaEventDisableTiming));
+  }
+  // the coarse steps of one lbm_step call follow everything already on s;
+  // between them only the level streams order the work
+  if (first) {
+    LBM_CUDA(cudaEventRecord(g.mr_in, s));
+    LBM_CUDA(cudaStreamWaitEvent(g.mr_hi, g.mr_in, 0));
+  }
   for (int l = 0; l < g.n_levels; ++l) {
     if (!g.mr_aux[l]) LBM_CUDA(cudaStreamCreateWithFlags(&g.mr_aux[l], cudaStreamNonBlocking));
     if (!g.mr_fork[l]) LBM_CUDA(cudaEventCreateWithFlags(&g.mr_fork[l], cudaEventDisableTiming));
     if (!g.mr_join[l]) LBM_CUDA(cudaEventCreateWithFlags(&g.mr_join[l], cudaEventDisableTiming));
+    if (first) LBM_CUDA(cudaEventRecord(g.mr_fork[l], g.mr_hi));
   }
+  // G_c launches on the high-priority stream: the scheduler hands them SMs
+  // ahead of the bandwidth-bound G_i launches they overlap
+  const cudaStream_t h = g.mr_hi;
   const bool bgk = g.phys.collision == C_BGK;
+  lbm_status st;
   switch (g.phys.storage) {
-    case S_F32: return bgk ? mr_advance<S_F32, C_BGK>(g, top, 1, s) : mr_advance<S_F32, C_REG>(g, top, 1, s);
-    case S_F16: return bgk ? mr_advance<S_F16, C_BGK>(g, top, 1, s) : mr_advance<S_F16, C_REG>(g, top, 1, s);
-    default: return bgk ? mr_advance<S_BF16, C_BGK>(g, top, 1, s) : mr_advance<S_BF16, C_REG>(g, top, 1, s);
+    case S_F32: st = bgk ? mr_advance<S_F32, C_BGK>(g, top, 1, h) : mr_advance<S_F32, C_REG>(g, top, 1, h); break;
+    case S_F16: st = bgk ? mr_advance<S_F16, C_BGK>(g, top, 1, h) : mr_advance<S_F16, C_REG>(g, top, 1, h); break;
+    default: st = bgk ? mr_advance<S_BF16, C_BGK>(g, top, 1, h) : mr_advance<S_BF16, C_REG>(g, top, 1, h);
   }
+  if (st) return st;
+  LBM_CUDA(cudaEventRecord(g.mr_out, h));
+  LBM_CUDA(cudaStreamWaitEvent(s, g.mr_out, 0));
+  return LBM_OK;
 }
 
 }  // namespace LBM_LNS

@@ -232,3 +232,29 @@ def test_cavity_rules_are_enforced(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_set_boundary(g, 0, flags)
     assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_interface_voxel_lists_bit_exact(lbm, q):
+    """The per-level interface voxel lists (slot and the bit set of the
+    populations taken from another level) equal the oracle's, on maps with
+    face, edge and corner contacts and on the cavity's nested shells."""
+    lmap = np.zeros((4, 2, 2), np.uint8)
+    lmap[:, 0, 0] = [2, 1, 0, 1]
+    lmap[:, 1, 1] = [1, 1, 0, 1]
+    lmap[:, 0, 1] = [2, 1, 1, 1]
+    lmap[:, 1, 0] = [1, 1, 1, 1]
+    cases = [(lmap, 3, (1, 1, 1)), (LMAP3, 3, (1, 1, 1)), (LMAP2, 2, (1, 1, 1)),
+             (wl.multires_cavity_map(160, 3, (1, 1)), 3, (0, 0, 0))]
+    for m, n_levels, per in cases:
+        cell = 8 * 2 ** (n_levels - 1)
+        mz, my, mx = m.shape
+        g = lbm.lbm_grid_create_multires((mx * cell, my * cell, mz * cell), n_levels, m,
+                                         lbm.physics(0.6, periodic=per, lattice=q))
+        want = olayout.multires_interface(m, n_levels, cell, q=q)
+        for lv in range(n_levels):
+            slots = lbm.lbm_get_layout(g, lv, lbm.LBM_LAYOUT_IFACE_SLOTS)
+            cross = lbm.lbm_get_layout(g, lv, lbm.LBM_LAYOUT_IFACE_CROSS)
+            assert slots.tobytes() == want[lv][0].tobytes(), (m.shape, lv)
+            assert cross.tobytes() == want[lv][1].tobytes(), (m.shape, lv)
+        lbm.lbm_grid_destroy(g)

@@ -261,3 +261,66 @@ def test_cavity_near_walls_equals_single_resolution():
     assert np.max(np.abs(g.f[0][:, far] - ref[:, far])) < 1e-15
     near = (dist > 0) & ~far
     assert np.max(np.abs(g.f[0][:, near] - ref[:, near])) > 1e-8   # the jump does reach them
+
+
+# ------------------------------------ interface voxels (Sec. 5, P_d = 0)
+
+def _exchange_dependence(lmap, n_levels, cell, lv, q):
+    """Which populations of level lv the oracle's exchange reads from another
+    level's buffers, found by running it: every other level holds NaN (the
+    finer level also after each of its substeps), level lv holds ones,
+    collision is the identity, and one step of level lv is taken; a
+    population comes out NaN iff its pre-collision value read another level."""
+    o = mr.MultiRes(lmap, n_levels, cell, 0.6, q=q)
+    for k in range(n_levels):
+        o.f[k][:] = 1.0 if k == lv else np.nan
+    real_advance = o._advance
+
+    def advance(level, k, f0_self):
+        if level < lv:
+            o.f[level][:] = np.nan
+        else:
+            real_advance(level, k, f0_self)
+
+    o._advance = advance
+    real = olbm.collide
+    olbm.collide = lambda g, tau, collision="bgk", force=None: (g, None, None)
+    try:
+        o._advance(lv, 1, o.f[lv].copy())
+    finally:
+        olbm.collide = real
+    mine = o.own[lv] == lv
+    dep = np.zeros(mine.shape, np.uint32)
+    for i in range(1, o.lat.Q):
+        dep |= np.where(np.isnan(o.f[lv][i]) & mine, np.uint32(1 << i), np.uint32(0))
+    return dep
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_interface_voxels_match_the_exchange(q):
+    """layout.multires_interface (a direct formula) against the exchange the
+    multi-resolution oracle performs, on a map with face, edge and corner
+    contacts between the three levels."""
+    from oracle import layout as olayout
+    lmap = np.zeros((4, 2, 2), np.uint8)
+    lmap[:, 0, 0] = [2, 1, 0, 1]
+    lmap[:, 1, 1] = [1, 1, 0, 1]
+    lmap[:, 0, 1] = [2, 1, 1, 1]
+    lmap[:, 1, 0] = [1, 1, 1, 1]
+    cell = 32
+    res = olayout.multires_interface(lmap, 3, cell, q=q)
+    tabs = olayout.multires_tables(lmap, 3, cell, q=q)
+    for lv in range(3):
+        dep = _exchange_dependence(lmap, 3, cell, lv, q)
+        slots, cross = res[lv]
+        coords = tabs[lv]["coords"]
+        b, v = slots // 512, slots % 512
+        x = coords[b, 0] * 8 + v % 8
+        y = coords[b, 1] * 8 + (v // 8) % 8
+        z = coords[b, 2] * 8 + v // 64
+        want = np.zeros_like(dep)
+        want[z, y, x] = cross
+        assert np.array_equal(want, dep), lv
+        assert np.all(np.diff(slots) > 0)
+        # every interface voxel lies in a G_c block, and a G_c block holds one
+        assert np.array_equal(np.unique(b), np.arange(tabs[lv]["n_c"]))
