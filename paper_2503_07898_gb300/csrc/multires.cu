@@ -7,10 +7,13 @@
 //                  G_i = all other blocks.
 //   mapping        per level an 8^3-block sparse grid; G_c blocks first,
 //                  then G_i, each in Morton order.
-//   operations     G_i blocks run the lean fused stream-collide kernel of the
-//                  sparse grid at every level (no cross-level data); G_c
-//                  blocks run mr_interface, which evaluates explosion and
-//                  coalescence per voxel.
+//   operations     inside G_c the grouping goes down to the voxel: the
+//                  interface voxels (a pull read from another level) run
+//                  mr_iface from a per-level list; every other voxel of the
+//                  level runs the lean fused stream-collide kernel of the
+//                  sparse grid (no cross-level data), kept off the interface
+//                  voxels by a per-slot mask.  With the learned closure, and
+//                  in the unfused schedule, whole blocks run mr_interface.
 //
 // Time stepping (refinement factor 2, acoustic scaling): one step of level l
 // contains two steps of level l-1.  Across a level jump the exchange is the
