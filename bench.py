@@ -214,7 +214,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
                              "bytes_per_update": bpu}
                 lbm.lbm_grid_destroy(g)
             out[key] = res
-    if "multires" in which:
+    if "multires" in which or "turbulence" in which:
         lmap = wl.multires_slab_map()
         res = {}
         for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
@@ -239,6 +239,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             lbm.lbm_grid_destroy(g)
         res["updates_per_coarsest_step"] = ups
         out["turbulence_256_3level"] = res
+    if "multires" in which or "cavity" in which:
         # the paper's multi-resolution benchmark (Sec. 6.3, Table 5): a
         # lid-driven cavity, finest level along the walls and the lid
         n = 384
@@ -579,7 +580,8 @@ def main():
     ap.add_argument("--batch-cases", type=int, default=128,
                     help="cases of the serving-batch workload (its first n of the 128)")
     ap.add_argument("--workloads", default="all",
-                    help="all | none | comma list of sparse,multires,batch,closure")
+                    help="all | none | comma list of sparse,multires,batch,closure "
+                         "(turbulence / cavity: one of the two multires workloads)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
