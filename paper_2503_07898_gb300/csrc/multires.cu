@@ -12,8 +12,10 @@
 //                  mr_iface from a per-level list; every other voxel of the
 //                  level runs the lean fused stream-collide kernel of the
 //                  sparse grid (no cross-level data), kept off the interface
-//                  voxels by a per-slot mask.  With the learned closure, and
-//                  in the unfused schedule, whole blocks run mr_interface.
+//                  voxels by a per-slot mask; on the learned closure's levels
+//                  both run the network in the collision.  The unfused
+//                  schedule streams whole blocks (mr_stream_split) and
+//                  collides in a second pass (mr_collide).
 //
 // Time stepping (refinement factor 2, acoustic scaling): one step of level l
 // contains two steps of level l-1.  Across a level jump the exchange is the
@@ -42,6 +44,7 @@
 #include "grid.h"
 #include "closure.cuh"
 #include "layout.h"
+#include "sparse.cuh"
 
 namespace lbm {
 namespace LBM_LNS {
@@ -54,7 +57,7 @@ static inline int wrapi(int v, int n) { return ((v % n) + n) % n; }
 // block belongs to another level or, in a block next to a finer level
 // (jump 1), a pull with two or three nonzero components crosses a face (or,
 // for a corner direction, edge) neighbour block of another level, through
-// which the subcells of the voxel trace.  mr_interface evaluates the same
+// which the subcells of the voxel trace.  mr_stream_split evaluates the same
 // rule on the device.
 static uint32_t mr_cross(const Level& V, int64_t b, int l) {
   const int lc[3] = {l & 7, (l >> 3) & 7, l >> 6};
@@ -475,17 +478,15 @@ template <> struct TmpCodec<S_F32> {
   template <int I> __device__ static __forceinline__ T store(float s) { return s; }
 };
 
-template <int S, int COLL, bool SPLIT, bool CLOSURE = false>
-__global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4)) mr_interface(MrArgs a) {
+// Stream pass of the unfused schedule (Sec. 6.3's baseline): every voxel of
+// every block of the level pulls, explosion / coalescence included, and
+// writes its pre-collision values to the scratch buffer; mr_collide follows.
+template <int S>
+__global__ void __launch_bounds__(256, Q == 27 ? 3 : 4) mr_stream_split(MrArgs a) {
   using T = typename Codec<S>::T;
   const int64_t b = a.b0 + blockIdx.x / 2;
-  extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
   __shared__ float mr_slow[Q][256];  // per-thread values of pulls that leave the level
   if (b >= a.b1) return;  // uniform per CTA
-  if constexpr (CLOSURE) {
-    closure_load_smem(reinterpret_cast<ClosureCta*>(mr_dyn_smem)->w, a.cp);
-    __syncthreads();
-  }
   const int32_t* __restrict__ nbr = a.nbr + b * 27;
   const int l = (blockIdx.x & 1) * 256 + threadIdx.x;
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
@@ -603,57 +604,81 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4)) mr_inter
       g[I] = Codec<S>::template load<I>(cur[(int64_t)nb * (Q * 512) + (I * 512 + ls)]);
     }
   });
-  if constexpr (SPLIT) {
-    using TT = typename TmpCodec<S>::T;
-    TT* __restrict__ out = (TT*)a.out;
-    static_for<Q>([&](auto ic) {
-      constexpr int I = decltype(ic)::value;
-      out[(b * Q + I) * 512 + l] = TmpCodec<S>::template store<I>(g[I]);
-    });
-  } else {
-    float omega = a.omega;
-    if constexpr (CLOSURE) {
-      // every thread of the CTA holds a voxel, so the warp-collective MMAs
-      // run with full warps
-      ClosureCta* sm = reinterpret_cast<ClosureCta*>(mr_dyn_smem);
-      float x[MLP_IN];
-      closure_features(g, a.tau, x);
-      // park the populations in this thread's shared-memory column while the
-      // network runs (volatile: the copies must really leave the registers)
-      static_for<Q>([&](auto ic) {
-        constexpr int I = decltype(ic)::value;
-        *(volatile float*)&mr_slow[I][threadIdx.x] = g[I];
-      });
-      const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
-      static_for<Q>([&](auto ic) {
-        constexpr int I = decltype(ic)::value;
-        g[I] = *(volatile float*)&mr_slow[I][threadIdx.x];
-      });
-      omega = 1.f / fmaxf(a.tau + dtau, TAU_MIN);
-    }
-    collide<COLL>(g, omega);
-    T* __restrict__ out = (T*)a.out;
-    static_for<Q>([&](auto ic) {
-      constexpr int I = decltype(ic)::value;
-      out[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
-    });
-  }
+  using TT = typename TmpCodec<S>::T;
+  TT* __restrict__ out = (TT*)a.out;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    out[(b * Q + I) * 512 + l] = TmpCodec<S>::template store<I>(g[I]);
+  });
 }
 
-// Interface voxels of the fused schedule, one thread each (the list holds
-// only voxels with a pull that leaves the level; the lean kernel updates the
-// rest of their blocks).  Cross-level values first, parked in the thread's
-// shared-memory column, then the same-level pulls, collision and store.
+// The learned closure's relaxation rate for this thread's voxel: features of
+// its pulled populations, then the network over the warp's 32 voxels (warp-
+// collective: every lane takes part).  The populations wait in the thread's
+// column of `park` meanwhile (volatile: the copies must really leave the
+// registers, which the network needs).
+__device__ __forceinline__ float closure_omega(float g[Q], float tau, ClosureCta* sm,
+                                               float (*park)[256]) {
+  float x[MLP_IN];
+  closure_features(g, tau, x);
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    *(volatile float*)&park[I][threadIdx.x] = g[I];
+  });
+  const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    g[I] = *(volatile float*)&park[I][threadIdx.x];
+  });
+  return 1.f / fmaxf(tau + dtau, TAU_MIN);
+}
+
+// Lean step of a closure level: every non-interface voxel of the level pulls
+// as in the sparse lean kernel, and the closure runs in the collision.  The
+// masked voxels (interface voxels, bit 31) take part in the network with the
+// rest state, so its warps stay full, and store nothing.
 template <int S, int COLL>
-__global__ void __launch_bounds__(256, Q == 27 ? 3 : 4)
-    mr_iface(MrArgs a, const int32_t* __restrict__ slots, const uint32_t* __restrict__ crosses,
-             int n) {
+__global__ void __launch_bounds__(256, 3)
+    mr_lean_closure(const void* fin, void* fout, const int32_t* __restrict__ nbr,
+                    const uint32_t* __restrict__ wmask, const uint8_t* __restrict__ blk_walls,
+                    float tau, const ClosureParams* cp) {
   using T = typename Codec<S>::T;
-  __shared__ float mr_slow[Q][256];
-  const int t = blockIdx.x * 256 + threadIdx.x;
-  if (t >= n) return;
-  const int slot = slots[t];
-  const uint32_t cross = crosses[t];
+  extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
+  __shared__ float park[Q][256];
+  ClosureCta* sm = reinterpret_cast<ClosureCta*>(mr_dyn_smem);
+  closure_load_smem(sm->w, cp);
+  __syncthreads();
+  const int64_t slot = (int64_t)blockIdx.x * 256 + threadIdx.x;  // whole blocks: always a slot
+  const int64_t b = slot >> 9;
+  const int l = (int)(slot & 511);
+  const bool walls = blk_walls[b] != 0;
+  const uint32_t wm = walls ? wmask[slot] : 0u;
+  const bool act = !(wm & 0xC0000000u);
+  float g[Q];
+  if (act) {
+    sparse_pull_voxel<S, 8>((const T*)fin, nbr + b * 27, wm, b, l, walls, g);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = 0.f;
+  }
+  const float omega = closure_omega(g, tau, sm, park);
+  if (!act) return;
+  collide<COLL>(g, omega);
+  T* __restrict__ out = (T*)fout;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    out[(b * Q + I) * 512 + l] = Codec<S>::template store<I>(g[I]);
+  });
+}
+
+// Pull of one interface voxel (slot, bit set of its cross-level
+// populations): explosion / coalescence values first, parked in the thread's
+// column of `slow`, then the same-level pulls through the hoisted neighbour
+// blocks.
+template <int S>
+__device__ __forceinline__ void mr_iface_pull(const MrArgs& a, int slot, uint32_t cross,
+                                              float (*slow)[256], float g[Q]) {
+  using T = typename Codec<S>::T;
   const int b = slot >> 9, l = slot & 511;
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
   const int jmp = a.jump[b];
@@ -663,8 +688,8 @@ __global__ void __launch_bounds__(256, Q == 27 ? 3 : 4)
     for (uint32_t m = cross; m; m &= m - 1) {
       const int i = __ffs(m) - 1;
       const int ccx = mr_c[0][i], ccy = mr_c[1][i], ccz = mr_c[2][i];
-      mr_slow[i][threadIdx.x] = jmp == 2 ? explosion<S>(a, i, ccx, ccy, ccz, gx, gy, gz)
-                                         : coalescence<S>(a, i, ccx, ccy, ccz, gx, gy, gz);
+      slow[i][threadIdx.x] = jmp == 2 ? explosion<S>(a, i, ccx, ccy, ccz, gx, gy, gz)
+                                      : coalescence<S>(a, i, ccx, ccy, ccz, gx, gy, gz);
     }
   }
   const int32_t* __restrict__ nbr = a.nbr + (int64_t)b * 27;
@@ -680,12 +705,11 @@ __global__ void __launch_bounds__(256, Q == 27 ? 3 : 4)
   const int yp = ((ly - 1) & 7) * 8, yn = ((ly + 1) & 7) * 8, y0 = ly * 8;
   const int zp = ((lz - 1) & 7) * 64, zn = ((lz + 1) & 7) * 64, z0 = lz * 64;
   const T* __restrict__ cur = (const T*)a.cur;
-  float g[Q];
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     constexpr int X = cx(I), Y = cy(I), Z = cz(I);
     if ((cross >> I) & 1u) {
-      g[I] = mr_slow[I][threadIdx.x];
+      g[I] = slow[I][threadIdx.x];
     } else {
       const bool kx = X != 0 && ex == -X, ky = Y != 0 && ey == -Y, kz = Z != 0 && ez == -Z;
       int nb = b;
@@ -702,7 +726,43 @@ __global__ void __launch_bounds__(256, Q == 27 ? 3 : 4)
       g[I] = Codec<S>::template load<I>(cur[(int64_t)nb * (Q * 512) + (I * 512 + ls)]);
     }
   });
-  collide<COLL>(g, a.omega);
+}
+
+// Interface voxels of the fused schedule, one thread each (the list holds
+// only voxels with a pull that leaves the level; the lean kernel updates the
+// rest of their blocks).  CLOSURE: the learned closure in the collision;
+// threads past the end of the list take part in the network (warp-
+// collective, one call site) with the rest state and store nothing.
+template <int S, int COLL, bool CLOSURE = false>
+__global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4))
+    mr_iface(MrArgs a, const int32_t* __restrict__ slots, const uint32_t* __restrict__ crosses,
+             int n) {
+  using T = typename Codec<S>::T;
+  extern __shared__ __align__(16) unsigned char mr_dyn_smem[];
+  __shared__ float mr_slow[Q][256];
+  if constexpr (CLOSURE) {
+    closure_load_smem(reinterpret_cast<ClosureCta*>(mr_dyn_smem)->w, a.cp);
+    __syncthreads();
+  }
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  const bool act = t < n;
+  if constexpr (!CLOSURE) {
+    if (!act) return;
+  }
+  int slot = 0;
+  float g[Q];
+  if (act) {
+    slot = slots[t];
+    mr_iface_pull<S>(a, slot, crosses[t], mr_slow, g);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = 0.f;
+  }
+  float omega = a.omega;
+  if constexpr (CLOSURE) omega = closure_omega(g, a.tau, reinterpret_cast<ClosureCta*>(mr_dyn_smem), mr_slow);
+  if (!act) return;
+  collide<COLL>(g, omega);
+  const int b = slot >> 9, l = slot & 511;
   T* __restrict__ out = (T*)a.out;
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
@@ -750,7 +810,7 @@ static MrLv view(const Level& V) {
 static const char* kname(int kind, int l) {
   static const char* names[4][4] = {
       {"mr_uniform_l0", "mr_uniform_l1", "mr_uniform_l2", "mr_uniform_l3"},
-      {"mr_interface_l0", "mr_interface_l1", "mr_interface_l2", "mr_interface_l3"},
+      {"mr_iface_l0", "mr_iface_l1", "mr_iface_l2", "mr_iface_l3"},
       {"mr_stream_split_l0", "mr_stream_split_l1", "mr_stream_split_l2", "mr_stream_split_l3"},
       {"mr_collide_l0", "mr_collide_l1", "mr_collide_l2", "mr_collide_l3"}};
   return names[kind][l];
@@ -765,16 +825,6 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
   const bool unfused = g.phys.schedule == LBM_SCHEDULE_MONOLITHIC && l > 0;
   const bool closure = g.phys.closure && g.closure_loaded && l > 0;
   const size_t csm = closure ? sizeof(ClosureCta) : 0;
-  if (closure) {
-    // static shared memory (interface values and work list) plus the
-    // network's dynamic part exceed the default 48 KB per CTA
-    static bool opted_in = false;
-    if (!opted_in) {
-      LBM_CUDA(cudaFuncSetAttribute(mr_interface<S, COLL, false, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-      opted_in = true;
-    }
-  }
   lbm_status st;
   MrArgs a{};
   a.me = view(V);
@@ -802,20 +852,16 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
   // overlaps the coarser levels' interface launches that run between two
   // steps of this level.  Those read this level's ring buffers only at its
   // interface voxels (next to another level), which the lean kernel never
-  // writes.  With the closure, G_i blocks run mr_interface there instead and
-  // G_c blocks run it whole.
-  const bool fork = !unfused && (closure ? V.n_blocks > V.n_c : V.n_blocks > 0);
+  // writes.  On closure levels both kernels run the network in the collision.
+  const bool fork = !unfused && V.n_blocks > 0;
   const cudaStream_t s_main = s;
   if (fork) {
     LBM_CUDA(cudaStreamWaitEvent(g.mr_aux[l], g.mr_fork[l], 0));
     s = g.mr_aux[l];
     if (closure) {
-      MrArgs ai = a;
-      ai.b0 = V.n_c;
-      ai.b1 = V.n_blocks;
-      ai.out = V.f[nx];
-      const int pr = prof_begin(g, s, kname(0, l), (V.n_blocks - V.n_c) * 512);
-      mr_interface<S, COLL, false, true><<<(unsigned)(2 * (V.n_blocks - V.n_c)), 256, csm, s>>>(ai);
+      const int pr = prof_begin(g, s, kname(0, l), V.n_updated - V.n_iface);
+      mr_lean_closure<S, COLL><<<(unsigned)(2 * V.n_blocks), 256, csm, s>>>(
+          V.f[c], V.f[nx], V.nbr_d, V.wmask_d, V.blk_walls_d, (float)tau_l, a.cp);
       prof_end(g, s, pr);
     } else {
       st = sparse_uniform_range(g, V, 0, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),
@@ -844,26 +890,20 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
     if (V.n_blocks > 0) {
       const unsigned nb = (unsigned)(2 * V.n_blocks);
       int pr = prof_begin(g, s, kname(2, l), V.n_blocks * 512);
-      mr_interface<S, COLL, true><<<nb, 256, 0, s>>>(a);
+      mr_stream_split<S><<<nb, 256, 0, s>>>(a);
       prof_end(g, s, pr);
       pr = prof_begin(g, s, kname(3, l), V.n_blocks * 512);
       mr_collide<S, COLL><<<nb, 256, 0, s>>>(V.tmp, V.f[nx], 0, V.n_blocks, omega);
       prof_end(g, s, pr);
     }
-  } else if (closure) {
-    if (V.n_c > 0) {
-      a.b0 = 0;
-      a.b1 = V.n_c;
-      a.out = V.f[nx];
-      const int pr = prof_begin(g, s, kname(1, l), V.n_c * 512);
-      mr_interface<S, COLL, false, true><<<(unsigned)(2 * V.n_c), 256, csm, s>>>(a);
-      prof_end(g, s, pr);
-    }
   } else if (V.n_iface > 0) {
     a.out = V.f[nx];
+    const unsigned nb = (unsigned)((V.n_iface + 255) / 256);
     const int pr = prof_begin(g, s, kname(1, l), V.n_iface);
-    mr_iface<S, COLL><<<(unsigned)((V.n_iface + 255) / 256), 256, 0, s>>>(
-        a, V.iface_slot_d, V.iface_cross_d, (int)V.n_iface);
+    if (closure)
+      mr_iface<S, COLL, true><<<nb, 256, csm, s>>>(a, V.iface_slot_d, V.iface_cross_d, (int)V.n_iface);
+    else
+      mr_iface<S, COLL><<<nb, 256, 0, s>>>(a, V.iface_slot_d, V.iface_cross_d, (int)V.n_iface);
     prof_end(g, s, pr);
   }
   LBM_CUDA(cudaGetLastError());
