@@ -203,8 +203,10 @@ lbm_status lbm_init_equilibrium(lbm_grid* g, int level, const double* rho,
                                 const double* u, int device_ptrs);
 
 /* Advance n_steps time steps (coarsest steps on a multi-resolution grid) on
- * `stream`.  Asynchronous; device errors are latched.  LBM_ERR_INVALID when
- * the grid has regularized voxels whose boundary values were never given
+ * `stream`.  Asynchronous; device errors are latched.  The steps order after
+ * the grid's work on the stream of its previous call (and on `stream`); the
+ * other calls then use `stream`.  LBM_ERR_INVALID when the grid has
+ * regularized voxels whose boundary values were never given
  * (lbm_set_boundary). */
 lbm_status lbm_step(lbm_grid* g, int n_steps, void* stream);
 

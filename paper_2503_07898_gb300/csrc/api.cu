@@ -134,6 +134,8 @@ static void free_grid(Grid& g) {
   if (g.mr_out) cudaEventDestroy(g.mr_out);
   g.mr_hi = nullptr;
   g.mr_in = g.mr_out = nullptr;
+  if (g.stream_ev) cudaEventDestroy(g.stream_ev);
+  g.stream_ev = nullptr;
   for (int l = 0; l < 4; ++l) free_level(g, g.lv[l]);
   g.dfree(g.status_d, g.stream);
   g.dfree(g.partials_d, g.stream);
@@ -588,6 +590,11 @@ lbm_status lbm_step(lbm_grid* h, int n_steps, void* stream) {
     if (g.lv[l].n_reg > 0 && g.lv[l].bc_h.size() != (size_t)g.lv[l].n_reg * 4)
       return fail(LBM_ERR_INVALID, "regularized voxels have no boundary values (lbm_set_boundary)");
   cudaStream_t s = stream ? (cudaStream_t)stream : g.stream;
+  if (s != g.stream) {
+    if (!g.stream_ev) LBM_CUDA(cudaEventCreateWithFlags(&g.stream_ev, cudaEventDisableTiming));
+    LBM_CUDA(cudaEventRecord(g.stream_ev, g.stream));
+    LBM_CUDA(cudaStreamWaitEvent(s, g.stream_ev, 0));
+  }
   g.stream = s;
   if (g.phys.schedule == LBM_SCHEDULE_MONOLITHIC) {
     for (int l = 0; l < g.n_levels; ++l) {

@@ -104,6 +104,7 @@ struct Grid {
   lbm_allocator alloc{};
   bool have_alloc = false;
   cudaStream_t stream = nullptr;
+  cudaEvent_t stream_ev = nullptr;  // orders a call on a new stream after the previous one
   int n_levels = 1;
   Level lv[4];
   int device = 0;
