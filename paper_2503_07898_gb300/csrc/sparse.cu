@@ -318,19 +318,12 @@ struct SparseArgs {
   float omega;
 };
 
+// One voxel (slot) of the group the mode selects.
 template <int S, int E, int COLL, int MODE>
-__global__ void __launch_bounds__(SP_THREADS,
-                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? (Q == 27 ? 3 : (S == S_F32 ? 4 : 5)) : 1)
-    sparse_kernel(SparseArgs a) {
+__device__ __forceinline__ void sparse_update(const SparseArgs& a, int64_t slot) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E;
   constexpr bool LEAN = MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM;
-  int64_t slot;
-  if constexpr (MODE == MODE_REG_LIST)
-    slot = (int64_t)a.blist[blockIdx.x >> 1] * E3 + (blockIdx.x & 1) * SP_THREADS + threadIdx.x;
-  else
-    slot = a.s0 + (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
-  if (slot >= a.s1) return;
   const int64_t b = slot / E3;
   const int l = (int)(slot - b * E3);
   if constexpr (MODE == MODE_INTERIOR_BM || MODE == MODE_BOUNDARY_BM) {
@@ -367,6 +360,30 @@ __global__ void __launch_bounds__(SP_THREADS,
   });
 }
 
+// BOUNDARY_BM with 8^3 blocks takes one block per CTA (two voxels per
+// thread): the launch over every block, most of which leave at once on
+// their boundary bit, then has half as many CTAs.
+template <int S, int E, int COLL, int MODE>
+__global__ void __launch_bounds__(SP_THREADS,
+                                  (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? (Q == 27 ? 3 : (S == S_F32 ? 4 : 5)) : 1)
+    sparse_kernel(SparseArgs a) {
+  constexpr int E3 = E * E * E;
+  if constexpr (MODE == MODE_BOUNDARY_BM && E3 == 2 * SP_THREADS) {
+    const int64_t b = blockIdx.x;
+    if (!((a.bnd_bits[b >> 5] >> (b & 31)) & 1u)) return;  // uniform per CTA
+    sparse_update<S, E, COLL, MODE>(a, b * E3 + threadIdx.x);
+    sparse_update<S, E, COLL, MODE>(a, b * E3 + SP_THREADS + threadIdx.x);
+  } else {
+    int64_t slot;
+    if constexpr (MODE == MODE_REG_LIST)
+      slot = (int64_t)a.blist[blockIdx.x >> 1] * E3 + (blockIdx.x & 1) * SP_THREADS + threadIdx.x;
+    else
+      slot = a.s0 + (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
+    if (slot >= a.s1) return;
+    sparse_update<S, E, COLL, MODE>(a, slot);
+  }
+}
+
 template <int S, int COLL>
 static void reg_list_t(Grid& g, Level& L, const void* fin, void* fout, float omega, cudaStream_t s,
                        const char* name) {
@@ -391,7 +408,10 @@ static void reg_list_t(Grid& g, Level& L, const void* fin, void* fout, float ome
 template <int S, int E, int COLL, int MODE>
 static void launch_range(Grid& g, SparseArgs a, cudaStream_t s, const char* name, int64_t units) {
   if (a.s1 <= a.s0) return;
-  const unsigned nb = (unsigned)((a.s1 - a.s0 + SP_THREADS - 1) / SP_THREADS);
+  constexpr int64_t E3 = (int64_t)E * E * E;
+  const unsigned nb = (MODE == MODE_BOUNDARY_BM && E3 == 2 * SP_THREADS)
+                          ? (unsigned)((a.s1 - a.s0) / E3)  // one CTA per block
+                          : (unsigned)((a.s1 - a.s0 + SP_THREADS - 1) / SP_THREADS);
   const int pr = prof_begin(g, s, name, units);
   sparse_kernel<S, E, COLL, MODE><<<nb, SP_THREADS, 0, s>>>(a);
   prof_end(g, s, pr);
