@@ -175,6 +175,7 @@ def _time_steps(torch, lbm, step, stream, n):
 def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
     """GLUPS of the other layouts of the method on their full-size inputs
     (context lines of the same metric; each timed after 3 warm-up steps)."""
+    STAGED = lbm.LBM_VARIANT_STAGED
     out = {}
     # a closure network of the trained one's size and scale (random weights:
     # the cost of inference does not depend on their values)
@@ -189,19 +190,25 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
         for key, q, cases in (
                 ("sphere_channel_512x256x256_sparse8", 19,
                  (("disaggregated_f32", dict(storage="f32")),
+                  ("disaggregated_f32_staged", dict(storage="f32", variant=STAGED)),
                   ("disaggregated_bitmask_f32", dict(storage="f32", schedule="bitmask")),
                   ("monolithic_f32", dict(storage="f32", schedule="monolithic")),
-                  ("disaggregated_f16", dict(storage="f16")))),
+                  ("disaggregated_f16", dict(storage="f16")),
+                  ("disaggregated_f16_staged", dict(storage="f16", variant=STAGED)))),
                 # the paper's register-pressure configuration: D3Q27,
                 # block-sparse, regularized inflow / outflow (Sec. 6.2)
                 ("sphere_channel_512x256x256_sparse8_d3q27", 27,
                  (("disaggregated_f32", dict(storage="f32")),
+                  ("disaggregated_f32_staged", dict(storage="f32", variant=STAGED)),
                   ("disaggregated_bitmask_f32", dict(storage="f32", schedule="bitmask")),
                   ("monolithic_f32", dict(storage="f32", schedule="monolithic"))))):
             res = {}
             for name, kw in cases:
+                pk = {k: v for k, v in kw.items() if k != "variant"}
                 g = lbm.lbm_grid_create_sparse(flags.shape[::-1], 8, flags,
-                                               lbm.physics(0.52, lattice=q, **kw), stream=stream)
+                                               lbm.physics(0.52, lattice=q, **pk), stream=stream)
+                if "variant" in kw:
+                    lbm.lbm_set_variant(g, kw["variant"])
                 lbm.lbm_set_boundary(g, 0, None, bcl)
                 lbm.lbm_init_equilibrium(g, 0, None, None)
                 n_upd = lbm.lbm_get_info(g)["n_updated"][0]
@@ -217,13 +224,18 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
     if "multires" in which or "turbulence" in which:
         lmap = wl.multires_slab_map()
         res = {}
-        for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
+        for name, kw in (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
+                         ("unfused_f32", dict(schedule="monolithic")),
                          ("fused_f16", dict(storage="f16")),
+                         ("fused_f16_staged", dict(storage="f16", variant=STAGED)),
                          ("fused_f32_learned_closure", dict(closure=1)),
                          ("fused_f32_d3q27", dict(lattice=27))):
+            pk = {k: v for k, v in kw.items() if k != "variant"}
             g = lbm.lbm_grid_create_multires((256, 256, 256), 3, lmap,
-                                             lbm.physics(0.52, periodic=(1, 1, 1), **kw),
+                                             lbm.physics(0.52, periodic=(1, 1, 1), **pk),
                                              stream=stream)
+            if "variant" in kw:
+                lbm.lbm_set_variant(g, kw["variant"])
             if kw.get("closure"):
                 lbm.lbm_closure_load(g, theta)
             info = lbm.lbm_get_info(g)
@@ -248,10 +260,14 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
         t = flags & 7
         bcl = np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
         res = {}
-        for name, kw in (("fused_f32", dict()), ("unfused_f32", dict(schedule="monolithic")),
+        for name, kw in (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
+                         ("unfused_f32", dict(schedule="monolithic")),
                          ("fused_f16", dict(storage="f16"))):
-            g = lbm.lbm_grid_create_multires((n,) * 3, 3, lmap, lbm.physics(0.52, **kw),
+            pk = {k: v for k, v in kw.items() if k != "variant"}
+            g = lbm.lbm_grid_create_multires((n,) * 3, 3, lmap, lbm.physics(0.52, **pk),
                                              stream=stream)
+            if "variant" in kw:
+                lbm.lbm_set_variant(g, kw["variant"])
             lbm.lbm_set_boundary(g, 0, flags, bcl)
             info = lbm.lbm_get_info(g)
             ups = sum(k * 2 ** (2 - l) for l, k in enumerate(info["n_updated"]))

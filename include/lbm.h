@@ -170,8 +170,15 @@ lbm_status lbm_set_schedule(lbm_grid* g, int schedule);
  *                      BF16 storage; the scalar kernel under FP32).
  * Vector variants apply when walls are only box sides, dims[0] is a multiple
  * of the vector length and the boundary group is whole top planes; otherwise
- * the scalar kernel runs.  Results are identical across variants. */
-enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2, LBM_VARIANT_VEC4 = 3 };
+ * the scalar kernel runs.  Block-sparse and multi-resolution grids with 8^3
+ * blocks take LBM_VARIANT_STAGED: the lean kernel copies each block's
+ * populations to shared memory with one bulk asynchronous copy (the tensor
+ * memory accelerator, completion on an mbarrier) and pulls the in-block
+ * sources from there, the cross-block ones from global memory; any other
+ * value selects their default kernel (LBM_ERR_UNSUPPORTED for a dense grid
+ * or 4^3 blocks).  Results are identical across variants. */
+enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2, LBM_VARIANT_VEC4 = 3,
+       LBM_VARIANT_STAGED = 4 };
 lbm_status lbm_set_variant(lbm_grid* g, int variant);
 
 /* Autotuner: times each variant over n_steps steps (CUDA events on the grid's

@@ -285,7 +285,8 @@ def lbm_set_schedule(grid, schedule):
 
 
 LBM_VARIANT_VEC16, LBM_VARIANT_SCALAR, LBM_VARIANT_VEC8, LBM_VARIANT_VEC4 = 0, 1, 2, 3
-VARIANT_NAMES = {0: "vec16", 1: "scalar", 2: "vec8", 3: "vec4"}
+LBM_VARIANT_STAGED = 4
+VARIANT_NAMES = {0: "vec16", 1: "scalar", 2: "vec8", 3: "vec4", 4: "staged"}
 
 
 def lbm_set_variant(grid, variant):

@@ -462,7 +462,9 @@ lbm_status lbm_set_schedule(lbm_grid* h, int schedule) {
 
 lbm_status lbm_set_variant(lbm_grid* h, int variant) {
   if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
-  if (variant < 0 || variant >= N_VARIANTS) return fail(LBM_ERR_INVALID, "unknown variant");
+  if (variant < 0 || variant > VARIANT_STAGED) return fail(LBM_ERR_INVALID, "unknown variant");
+  if (variant == VARIANT_STAGED && (h->g.kind == 0 || h->g.lv[0].E != 8))
+    return fail(LBM_ERR_UNSUPPORTED, "the staged variant is a kernel of 8^3-block grids");
   for (int l = 0; l < 4; ++l) h->g.lv[l].variant = variant;
   return LBM_OK;
 }

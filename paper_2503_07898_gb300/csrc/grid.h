@@ -23,7 +23,8 @@ lbm_status cuda_fail(cudaError_t e, const char* where);
 constexpr int kRedCtas = 1216;  // reduction CTAs per level (152 SMs x 8)
 
 // Interior-kernel variants (dense grids): 16-byte vectors, scalar, 8-byte vectors.
-enum { VARIANT_VEC16 = 0, VARIANT_SCALAR = 1, VARIANT_VEC8 = 2, VARIANT_VEC4 = 3, N_VARIANTS = 4 };
+enum { VARIANT_VEC16 = 0, VARIANT_SCALAR = 1, VARIANT_VEC8 = 2, VARIANT_VEC4 = 3, N_VARIANTS = 4,
+       VARIANT_STAGED = 4 /* block-sparse lean kernel staged by a bulk copy (8^3 blocks) */ };
 
 // Per-level data --------------------------------------------------------------
 struct Level {

@@ -316,7 +316,45 @@ struct SparseArgs {
   const float4* bc_cmp;      // bitmask grouping: compact BC values
   int64_t s0, s1;  // slot range [s0, s1), block aligned
   float omega;
+  int* status;     // latched device status (staged kernel: a bulk copy that never lands)
 };
+
+// ---------------------------------------------- bulk-copy staging (TMA)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Arrive once and announce `bytes` of asynchronous copy completing the phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+               " selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of
+// 16), completion counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait on phase `parity`: a copy that has not landed after the limit
+// sets the device status and the caller skips its work (no endless spin).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (status) atomicExch(status, (int)LBM_ERR_TIMEOUT);
+  return false;
+}
 
 // One voxel (slot) of the group the mode selects.
 template <int S, int E, int COLL, int MODE>
@@ -384,6 +422,119 @@ __global__ void __launch_bounds__(SP_THREADS,
   }
 }
 
+// Pull of voxel l of block b with the block's populations staged in shared
+// memory (sb): in-block sources come from there, sources across the block's
+// faces from global memory; block selection and wall rule as in
+// sparse_pull_voxel_t (8^3 blocks).
+template <int S, bool WALLS>
+__device__ __forceinline__ void staged_pull(const typename Codec<S>::T* sb,
+                                            const typename Codec<S>::T* __restrict__ fin,
+                                            const int32_t* nbr27, uint32_t wm, int b, int l,
+                                            float g[Q]) {
+  using T = typename Codec<S>::T;
+  constexpr int E = 8, E3 = 512, M = 7;
+  const int lx = l & M, ly = (l / E) & M, lz = l / (E * E);
+  const int ex = lx == 0 ? -1 : (lx == M ? 1 : 0);
+  const int ey = ly == 0 ? -1 : (ly == M ? 1 : 0);
+  const int ez = lz == 0 ? -1 : (lz == M ? 1 : 0);
+  const int nX = __ldg(nbr27 + 13 + ex), nY = __ldg(nbr27 + 13 + 3 * ey);
+  const int nZ = __ldg(nbr27 + 13 + 9 * ez);
+  const int nXY = __ldg(nbr27 + 13 + ex + 3 * ey), nXZ = __ldg(nbr27 + 13 + ex + 9 * ez);
+  const int nYZ = __ldg(nbr27 + 13 + 3 * ey + 9 * ez);
+  const int nXYZ = Q == 27 ? __ldg(nbr27 + 13 + ex + 3 * ey + 9 * ez) : b;
+  const int xp = (lx - 1) & M, xn = (lx + 1) & M;
+  const int yp = ((ly - 1) & M) * E, yn = ((ly + 1) & M) * E, y0 = ly * E;
+  const int zp = ((lz - 1) & M) * E * E, zn = ((lz + 1) & M) * E * E, z0 = lz * E * E;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+    const bool kx = X != 0 && ex == -X;
+    const bool ky = Y != 0 && ey == -Y;
+    const bool kz = Z != 0 && ez == -Z;
+    int nb = b;
+    if constexpr (X != 0 && Y != 0 && Z != 0)
+      nb = kz ? (kx ? (ky ? nXYZ : nXZ) : (ky ? nYZ : nZ)) : (kx ? (ky ? nXY : nX) : (ky ? nY : b));
+    else if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : b);
+    else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : b);
+    else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : b);
+    else if constexpr (X != 0) nb = kx ? nX : b;
+    else if constexpr (Y != 0) nb = ky ? nY : b;
+    else if constexpr (Z != 0) nb = kz ? nZ : b;
+    const int ls = (X > 0 ? xp : (X < 0 ? xn : lx)) + (Y > 0 ? yp : (Y < 0 ? yn : y0)) +
+                   (Z > 0 ? zp : (Z < 0 ? zn : z0));
+    const bool out = kx || ky || kz;
+    T v;
+    if (WALLS && ((wm >> I) & 1u)) v = sb[opp(I) * E3 + l];
+    else if (out) v = fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)];
+    else v = sb[I * E3 + ls];
+    g[I] = Codec<S>::template load<I>(v);
+  });
+}
+
+// Lean (interior-group) step with each 8^3 block staged in shared memory by
+// one bulk asynchronous copy: thread 0 arms the CTA's mbarrier with the
+// block's byte count and issues the copy, every thread waits on the barrier
+// (bounded), then updates two voxels (z-halves of the block).
+template <int S, int COLL>
+__global__ void __launch_bounds__(SP_THREADS, Q == 27 ? 3 : (S == S_F32 ? 4 : 5))
+    sparse_staged(SparseArgs a) {
+  using T = typename Codec<S>::T;
+  constexpr int E3 = 512;
+  constexpr uint32_t BYTES = (uint32_t)(Q * E3 * sizeof(T));
+  extern __shared__ __align__(128) unsigned char st_smem[];
+  __shared__ __align__(8) uint64_t bar;
+  T* sb = reinterpret_cast<T*>(st_smem);
+  const int64_t b = a.s0 / E3 + blockIdx.x;
+  const T* __restrict__ fin = (const T*)a.fin;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, BYTES);
+    bulk_g2s(sb, fin + b * (Q * E3), BYTES, &bar);
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(&bar, 0, a.status)) {
+    // the copy may still be in flight: wait once more (bounded) before the
+    // CTA gives up its shared memory
+    mbar_wait_bounded(&bar, 0, nullptr);
+    return;
+  }
+  const bool walls = a.blk_walls[b] != 0;
+  T* __restrict__ fout = (T*)a.fout;
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int l = h * SP_THREADS + threadIdx.x;
+    uint32_t wm = 0;
+    if (walls) {
+      wm = a.wmask[b * E3 + l];
+      if (wm & 0xC0000000u) continue;  // not updated, or a regularized voxel of another launch
+    }
+    float g[Q];
+    if (walls) staged_pull<S, true>(sb, fin, a.nbr + b * 27, wm, (int)b, l, g);
+    else staged_pull<S, false>(sb, fin, a.nbr + b * 27, 0u, (int)b, l, g);
+    collide<COLL>(g, a.omega);
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      fout[(b * Q + I) * E3 + l] = Codec<S>::template store<I>(g[I]);
+    });
+  }
+}
+
+template <int S, int COLL>
+static void launch_staged(Grid& g, SparseArgs a, cudaStream_t s, const char* name, int64_t units) {
+  if (a.s1 <= a.s0) return;
+  using T = typename Codec<S>::T;
+  constexpr int BYTES = (int)(Q * 512 * sizeof(T));
+  static bool opted_in = false;  // more than 48 KB of dynamic shared memory with D3Q27 FP32
+  if (!opted_in) {
+    cudaFuncSetAttribute(sparse_staged<S, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
+    opted_in = true;
+  }
+  a.status = g.status_d;
+  const int pr = prof_begin(g, s, name, units);
+  sparse_staged<S, COLL><<<(unsigned)((a.s1 - a.s0) / 512), SP_THREADS, BYTES, s>>>(a);
+  prof_end(g, s, pr);
+}
+
 template <int S, int COLL>
 static void reg_list_t(Grid& g, Level& L, const void* fin, void* fout, float omega, cudaStream_t s,
                        const char* name) {
@@ -449,6 +600,14 @@ static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
     launch_range<S, E, COLL, MODE_BOUNDARY>(g, a, s, "sparse_boundary", L.n_upd_b);
     a.s0 = L.n_b * E3;
     a.s1 = L.n_blocks * E3;
+    if constexpr (E == 8) {
+      if (L.variant == VARIANT_STAGED) {
+        launch_staged<S, COLL>(g, a, s, "sparse_interior_staged", L.n_updated - L.n_upd_b);
+        LBM_CUDA(cudaGetLastError());
+        L.cur ^= 1;
+        return LBM_OK;
+      }
+    }
     launch_range<S, E, COLL, MODE_INTERIOR>(g, a, s, "sparse_interior", L.n_updated - L.n_upd_b);
   }
   LBM_CUDA(cudaGetLastError());
@@ -469,7 +628,8 @@ static void uniform_range_t(Grid& g, Level& L, int64_t b0, int64_t b1, const voi
   a.omega = omega;
   a.s0 = b0 * 512;
   a.s1 = b1 * 512;
-  launch_range<S, 8, COLL, MODE_INTERIOR>(g, a, s, name, units);
+  if (L.variant == VARIANT_STAGED) launch_staged<S, COLL>(g, a, s, name, units);
+  else launch_range<S, 8, COLL, MODE_INTERIOR>(g, a, s, name, units);
 }
 
 lbm_status sparse_reg_blocks(Grid& g, Level& L, const void* fin, void* fout, float omega,
