@@ -116,7 +116,7 @@ def test_training_is_deterministic_and_learns(lbm):
 
 
 def test_closure_gain_over_plain_coarse_level(lbm):
-    """Decaying turbulence, fine 64^3 at tau 0.504 (the judge) vs the coarse
+    """Decaying turbulence, fine 64^3 at tau 0.504 (the reference) vs the coarse
     level 4x coarser (tau_2 = 0.501 of a 3-level hierarchy) with and without
     the learned closure; velocity L2 against the box-filtered fine field."""
     import torch
@@ -140,7 +140,7 @@ def test_closure_gain_over_plain_coarse_level(lbm):
     th = cuda(he_init(0).astype(np.float32))
     lbm.lbm_closure_train(X, Y, 4000, 4096, 1e-3, 1, th)
     theta = th.cpu().numpy()
-    # the judge: plain full-resolution run, box-filtered
+    # the reference: plain full-resolution run, box-filtered
     rho0, u0 = wl.turbulence(N, seed=23, u_rms=urms, kmax=kmax)
     g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau_f, periodic=(1, 1, 1)))
     lbm.lbm_init_equilibrium(g, 0, rho0, u0)
