@@ -33,8 +33,10 @@ METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated err
 # only while the kernel sources hash to the recorded value: the 160^3
 # capture of dense_interior (dram__bytes_read.sum + dram__bytes_write.sum,
 # 4,070,400 updates per launch) scaled by units to one 256^3 launch
-# (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md.
-NCU_TRAFFIC = {"dense_interior": {"bytes_per_launch": 2.348459e+09, "src_sha": "04a9e819962d707d"}}
+# (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md; keyed by
+# kernel and storage (the FP16 capture: dense_interior_f16_cavity160_ncu.md).
+NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.348459e+09, "src_sha": "04a9e819962d707d"},
+               ("dense_interior", "f16"): {"bytes_per_launch": 1.122250e+09, "src_sha": "04a9e819962d707d"}}
 
 
 def src_hash():
@@ -452,7 +454,7 @@ def run_ours(args, rank, world, local_rank):
     units = st["units"] / st["launches"]
     achieved = bpu * units / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    tr = NCU_TRAFFIC.get(top)
+    tr = NCU_TRAFFIC.get((top, args.storage))
     traffic = tr["bytes_per_launch"] if tr and tr["src_sha"] == src_hash() else None
     shares = {k: round(v["total_ms"] / sum(x["total_ms"] for x in stats.values()), 4)
               for k, v in stats.items()}
