@@ -147,15 +147,18 @@ template <> struct Codec<S_BF16> {
 // Every function below takes and returns shifted populations s_i = f_i - w_i.
 
 // drho = rho - 1 = sum s, j = sum c s.
+// Opposite populations (i, i + 1) enter as their sum (mass) and difference
+// (momentum along c_i), which saves an add per nonzero velocity component.
 __device__ __forceinline__ void moments_s(const float s[Q], float& drho, float& jx, float& jy,
                                           float& jz) {
-  float r = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+  float r = s[0], ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    r += s[i];
-    if (cx(i)) ax += cx(i) > 0 ? s[i] : -s[i];
-    if (cy(i)) ay += cy(i) > 0 ? s[i] : -s[i];
-    if (cz(i)) az += cz(i) > 0 ? s[i] : -s[i];
+  for (int i = 1; i < Q; i += 2) {
+    const float p = s[i] + s[i + 1], d = s[i] - s[i + 1];
+    r += p;
+    if (cx(i)) ax += cx(i) > 0 ? d : -d;
+    if (cy(i)) ay += cy(i) > 0 ? d : -d;
+    if (cz(i)) az += cz(i) > 0 ? d : -d;
   }
   drho = r;
   jx = ax;
@@ -213,17 +216,21 @@ __device__ __forceinline__ void collide(float s[Q], float omega) {
   if constexpr (COLL == C_BGK) {
     // The pair (i, opp(i)) = (i, i + 1) shares the even part of the shifted
     // equilibrium: E = sym +- asym with sym = w (drho + rho (9/2 (c.u)^2 -
-    // 3/2 u.u)) and asym = 3 w rho c.u, c = c_i; w rho, w drho and 3 w rho
-    // are formed once per weight class (axis, edge, corner).  e sums exactly
-    // the E values used, so the rest population closes the mass as in the
-    // unpaired form.
+    // 3/2 u.u)) and asym = 3 w rho c.u, c = c_i.  The update is written
+    // s* = (1 - omega) s + omega E with omega folded into the per-class
+    // factors (omega w rho, omega w drho, 3 omega w rho, formed once per
+    // weight class: axis, edge, corner), so each population costs one fused
+    // multiply-add after its pair's omega sym +- omega asym.  The rest
+    // population closes the mass: its equilibrium is drho minus twice the
+    // sum of the pairs' even parts.
     constexpr float W1 = wf(1), W2 = wf(7), W3 = Q == 27 ? wf(Q - 1) : 0.f;
     constexpr float A1 = (float)(3.0 * wd(1)), A2 = (float)(3.0 * wd(7));
     constexpr float A3 = Q == 27 ? (float)(3.0 * wd(Q - 1)) : 0.f;
-    const float r1 = rho * W1, d1 = drho * W1, a1 = rho * A1;
-    const float r2 = rho * W2, d2 = drho * W2, a2 = rho * A2;
-    const float r3 = rho * W3, d3 = drho * W3, a3 = rho * A3;
-    float e = 0.f;
+    const float k = 1.f - omega, orho = omega * rho, odrho = omega * drho;
+    const float r1 = orho * W1, d1 = odrho * W1, a1 = orho * A1;
+    const float r2 = orho * W2, d2 = odrho * W2, a2 = orho * A2;
+    const float r3 = orho * W3, d3 = odrho * W3, a3 = orho * A3;
+    float e = 0.f;  // sum of omega sym over the pairs
     static_for<(Q - 1) / 2>([&](auto pc) {
       constexpr int i = 2 * decltype(pc)::value + 1, o = i + 1;
       constexpr int cls = i < 7 ? 1 : (i < 19 ? 2 : 3);
@@ -231,12 +238,11 @@ __device__ __forceinline__ void collide(float s[Q], float omega) {
       const float t = 4.5f * cu * cu - usq15;
       const float sym = cls == 1 ? fmaf(r1, t, d1) : (cls == 2 ? fmaf(r2, t, d2) : fmaf(r3, t, d3));
       const float asym = (cls == 1 ? a1 : (cls == 2 ? a2 : a3)) * cu;
-      const float Ei = sym + asym, Eo = sym - asym;
-      e += Ei + Eo;
-      s[i] = s[i] + omega * (Ei - s[i]);
-      s[o] = s[o] + omega * (Eo - s[o]);
+      e += sym;
+      s[i] = fmaf(k, s[i], sym + asym);
+      s[o] = fmaf(k, s[o], sym - asym);
     });
-    s[0] = s[0] + omega * ((drho - e) - s[0]);
+    s[0] = fmaf(k, s[0], fmaf(-2.f, e, odrho));
   } else {
     float pxx, pyy, pzz, pxy, pxz, pyz;
     second_moment(s, pxx, pyy, pzz, pxy, pxz, pyz);
