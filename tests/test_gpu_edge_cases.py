@@ -87,3 +87,23 @@ def test_multires_level_without_blocks(lbm):
         ref = o.f[lv][:, m]
         assert np.max(np.abs(f[:, m] - ref) / np.abs(ref)) <= F32_RTOL
     assert np.all(np.isnan(lbm.lbm_get_populations_f64(g, 2)))
+
+
+@pytest.mark.parametrize("kind", ["dense", "sparse"])
+def test_non_finite_state_is_reported_as_diverged(lbm, kind):
+    """A non-finite population (planted through the checkpoint path, on the
+    host) spreads through the pull and collision; the conservation sums then
+    report LBM_ERR_DIVERGED instead of returning NaN."""
+    flags = np.zeros((16, 16, 16), np.uint8)
+    g = make_grid(lbm, kind, flags, None, 0.6, periodic=(1, 1, 1))
+    rho, u = wl.random_fields(flags.shape, seed=153, u_amp=0.02)
+    lbm.lbm_init_equilibrium(g, 0, rho, u)
+    assert np.all(np.isfinite(lbm.lbm_conservation(g)))
+    f = np.empty(19 * 16 ** 3, np.float32)
+    lbm.lbm_get_populations(g, 0, f)
+    f[5 * 16 ** 3 + 100] = np.nan
+    lbm.lbm_set_populations(g, 0, f)
+    lbm.lbm_step(g, 3)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_conservation(g)
+    assert "DIVERGED" in str(e.value)
