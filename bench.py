@@ -545,7 +545,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cn, csteps = 48, 60
+            cn, csteps = 64, 200  # about 10 s of the oracle on the host cores
             cv, cdt, ccores = oracle_cavity_glups(cn, csteps)
             cpu = {"value": cv, "unit": "GLUPS", "cores": ccores, "kind": "oracle",
                    "sample": f"{cn}^3 cavity (tau 0.515, lid 0.05), {csteps} steps, numpy FP64, "
