@@ -204,8 +204,10 @@ lbm_status lbm_set_boundary(lbm_grid* g, int level, const uint8_t* flags,
 /* Initial state f* = f^eq(rho, u), evaluated in FP64 on the GPU and stored in
  * the grid's storage format.  rho: n doubles (NULL -> 1); u: 3*n doubles,
  * component-major (ux[n], uy[n], uz[n]) (NULL -> 0); n = level's virtual box
- * voxel count.  device_ptrs: 0 host arrays, 1 device arrays.  Voxels that are
- * not updated are ignored. */
+ * voxel count.  device_ptrs: 0 host arrays, 1 device arrays.  Page-locked
+ * host arrays mapped into the device address space are read by the kernel
+ * in place; other host arrays are staged through device scratch.  Voxels
+ * that are not updated are ignored. */
 lbm_status lbm_init_equilibrium(lbm_grid* g, int level, const double* rho,
                                 const double* u, int device_ptrs);
 
@@ -219,7 +221,8 @@ lbm_status lbm_step(lbm_grid* g, int n_steps, void* stream);
 
 /* Density and velocity of the stored state in FP64, virtual-box order, NaN on
  * voxels that are not updated.  rho: n doubles or NULL; u: 3*n doubles
- * (component-major) or NULL.  Synchronises the grid's stream. */
+ * (component-major) or NULL.  Page-locked, mapped host arrays are written by
+ * the kernel in place.  Synchronises the grid's stream. */
 lbm_status lbm_get_moments(lbm_grid* g, int level, double* rho, double* u,
                            int device_ptrs);
 

@@ -75,6 +75,19 @@ void prof_clear(Grid& g) {
 }
 
 // RAII scratch allocation through the grid's allocator.
+// Device address of a page-locked, mapped host array, or null (pageable or
+// unregistered memory, or a null pointer).
+template <class T> static T* mapped_host(T* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA-known pointer: clear the error
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<T*>(a.devicePointer);
+}
+
 struct Scratch {
   Grid& g;
   cudaStream_t s;
@@ -571,6 +584,17 @@ lbm_status lbm_init_equilibrium(lbm_grid* h, int level, const double* rho, const
     LBM_CUDA(cudaStreamSynchronize(s));
     return LBM_OK;
   }
+  // page-locked host arrays mapped into the device address space are read
+  // by the kernel in place (one pass over the host link, no staging copy)
+  const double* mr = mapped_host(rho);
+  const double* mu = mapped_host(u);
+  if ((!rho || mr) && (!u || mu)) {
+    lbm_status st = g.q == 27 ? q27::launch_init_equilibrium(g, L, mr, mu, s)
+                              : q19::launch_init_equilibrium(g, L, mr, mu, s);
+    if (st) return st;
+    LBM_CUDA(cudaStreamSynchronize(s));
+    return LBM_OK;
+  }
   Scratch dr(g, rho ? n * sizeof(double) : 16, s), du(g, u ? 3 * n * sizeof(double) : 16, s);
   if (!dr.p || !du.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
   if (rho) LBM_CUDA(cudaMemcpyAsync(dr.p, rho, n * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -642,6 +666,16 @@ lbm_status lbm_get_moments(lbm_grid* h, int level, double* rho, double* u, int d
   if (device_ptrs) {
     if ((st = g.q == 27 ? q27::launch_moments(g, L, rho, u, s)
                         : q19::launch_moments(g, L, rho, u, s)))
+      return st;
+    LBM_CUDA(cudaStreamSynchronize(s));
+    return LBM_OK;
+  }
+  // page-locked host arrays mapped into the device address space are written
+  // by the kernel in place
+  double* mr = mapped_host(rho);
+  double* mu = mapped_host(u);
+  if ((!rho || mr) && (!u || mu)) {
+    if ((st = g.q == 27 ? q27::launch_moments(g, L, mr, mu, s) : q19::launch_moments(g, L, mr, mu, s)))
       return st;
     LBM_CUDA(cudaStreamSynchronize(s));
     return LBM_OK;
