@@ -340,3 +340,31 @@ def test_checkpoint_restore_into_new_grid_bit_exact(lbm):
     lbm.lbm_step(h, 3)
     for lv in range(3):
         assert np.array_equal(lbm.lbm_get_populations_f64(h, lv), want[lv], equal_nan=True)
+
+
+LMAP4 = np.array([3, 2, 1, 0, 1, 2], np.uint8).reshape(6, 1, 1)
+
+
+def test_four_level_parity_and_tables(lbm):
+    """Four levels (refinement 2 at every jump, coarsest cell 64 finest
+    voxels): interface voxel lists bit for bit, populations after one
+    coarsest step (8 level-0 substeps) within 1e-5 of the oracle, and the
+    unfused schedule equal to the fused one bit for bit."""
+    g, dims, cell = make_mr(lbm, LMAP4, 4, 0.6)
+    want = olayout.multires_interface(LMAP4, 4, cell)
+    for lv in range(4):
+        assert lbm.lbm_get_layout(g, lv, lbm.LBM_LAYOUT_IFACE_SLOTS).tobytes() == want[lv][0].tobytes()
+        assert lbm.lbm_get_layout(g, lv, lbm.LBM_LAYOUT_IFACE_CROSS).tobytes() == want[lv][1].tobytes()
+    o = omr.MultiRes(LMAP4, 4, cell, 0.6)
+    fields = level_fields(dims, 4, 67)
+    init_both(lbm, g, o, fields)
+    lbm.lbm_step(g, 1)
+    o.run(1)
+    assert compare(lbm, g, o, 4) <= F32_RTOL
+    u, _, _ = make_mr(lbm, LMAP4, 4, 0.6, "monolithic")
+    for lv, (rho, v) in enumerate(fields):
+        lbm.lbm_init_equilibrium(u, lv, rho, v)
+    lbm.lbm_step(u, 1)
+    for lv in range(4):
+        assert np.array_equal(lbm.lbm_get_populations_f64(u, lv), lbm.lbm_get_populations_f64(g, lv),
+                              equal_nan=True)
