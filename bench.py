@@ -253,27 +253,29 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             lbm.lbm_grid_destroy(g)
         res["updates_per_coarsest_step"] = ups
         out["turbulence_256_3level"] = res
-    if "multires" in which or "cavity" in which:
+    cavities = ((384, 3, (2, 2), (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
+                                  ("unfused_f32", dict(schedule="monolithic")),
+                                  ("fused_f16", dict(storage="f16")))),
+                (512, 4, (1, 1, 1), (("fused_f32", dict()),
+                                     ("unfused_f32", dict(schedule="monolithic")))))
+    for n, nlev, shells, cases in (cavities if ("multires" in which or "cavity" in which) else ()):
         # the paper's multi-resolution benchmark (Sec. 6.3, Table 5): a
         # lid-driven cavity, finest level along the walls and the lid
-        n = 384
-        lmap = wl.multires_cavity_map(n, 3, (2, 2))
+        lmap = wl.multires_cavity_map(n, nlev, shells)
         flags, bc = wl.cavity(n)
         t = flags & 7
         bcl = np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
         res = {}
-        for name, kw in (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
-                         ("unfused_f32", dict(schedule="monolithic")),
-                         ("fused_f16", dict(storage="f16"))):
+        for name, kw in cases:
             pk = {k: v for k, v in kw.items() if k != "variant"}
-            g = lbm.lbm_grid_create_multires((n,) * 3, 3, lmap, lbm.physics(0.52, **pk),
+            g = lbm.lbm_grid_create_multires((n,) * 3, nlev, lmap, lbm.physics(0.52, **pk),
                                              stream=stream)
             if "variant" in kw:
                 lbm.lbm_set_variant(g, kw["variant"])
             lbm.lbm_set_boundary(g, 0, flags, bcl)
             info = lbm.lbm_get_info(g)
-            ups = sum(k * 2 ** (2 - l) for l, k in enumerate(info["n_updated"]))
-            for l in range(3):
+            ups = sum(k * 2 ** (nlev - 1 - l) for l, k in enumerate(info["n_updated"][:nlev]))
+            for l in range(nlev):
                 lbm.lbm_init_equilibrium(g, l, None, None)
             lbm.lbm_step(g, 3, stream)
             nst = max(1, steps // 4)
@@ -283,10 +285,10 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
             lbm.lbm_grid_destroy(g)
         tot = n ** 3
-        res["pct_of_finest_box_voxels"] = [round(100 * k / tot, 3) for k in info["n_updated"]]
-        res["voxels_per_level"] = list(info["n_updated"])
+        res["pct_of_finest_box_voxels"] = [round(100 * k / tot, 3) for k in info["n_updated"][:nlev]]
+        res["voxels_per_level"] = list(info["n_updated"][:nlev])
         res["updates_per_coarsest_step"] = ups
-        out[f"cavity_{n}_3level"] = res
+        out[f"cavity_{n}_{nlev}level"] = res
     if "batch" in which:
         cases = wl.batch_cases(n_cases=n_batch)
         grids = []
