@@ -68,3 +68,23 @@ def test_reference_arm_runs_on_rank_zero_only():
     with redirect_stdout(out):
         assert bench.run_reference(args, 1, 2) is None
     assert out.getvalue() == ""
+
+
+def test_reference_arm_line_on_rank_zero():
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the contract's keys, on the same metric and unit."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "3", "--warmup", "3"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GLUPS"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
