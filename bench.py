@@ -563,7 +563,7 @@ def run_ours(args, rank, world, local_rank):
                        "variant": lbm.VARIANT_NAMES[variant],
                        "autotune_ms_per_step": (None if variant_ms is None else
                                                 {lbm.VARIANT_NAMES[k]: round(t, 5)
-                                                 for k, t in enumerate(variant_ms)}),
+                                                 for k, t in enumerate(variant_ms) if t > 0}),
                        "l2": "inputs larger than L2 (population state "
                              f"{2 * info['population_bytes'][0] / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{world}"},

@@ -181,10 +181,13 @@ enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2, LBM_
        LBM_VARIANT_STAGED = 4 };
 lbm_status lbm_set_variant(lbm_grid* g, int variant);
 
-/* Autotuner: times each variant over n_steps steps (CUDA events on the grid's
- * stream) starting from the grid's current state, restores that state, and
- * keeps the fastest variant.  *chosen receives it; ms_per_step (4 doubles, one
- * per LBM_VARIANT_*, or NULL) receives the measured time per step of each. */
+/* Autotuner: times each variant that applies to the grid (the four dense
+ * interior variants; LBM_VARIANT_SCALAR and LBM_VARIANT_STAGED on 8^3-block
+ * sparse and multi-resolution grids) over n_steps steps (CUDA events on the
+ * grid's stream) starting from the grid's current state, restores that state,
+ * and keeps the fastest.  *chosen receives it; ms_per_step (5 doubles, one
+ * per LBM_VARIANT_*, 0 for a variant not timed, or NULL) receives the
+ * measured time per step of each. */
 lbm_status lbm_autotune(lbm_grid* g, int n_steps, int* chosen, double* ms_per_step);
 
 /* Voxel types and boundary values of one level.

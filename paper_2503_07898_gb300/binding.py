@@ -296,7 +296,7 @@ def lbm_set_variant(grid, variant):
 def lbm_autotune(grid, n_steps):
     """Returns (chosen variant, [ms per step of each variant])."""
     chosen = C.c_int()
-    ms = (C.c_double * 4)()
+    ms = (C.c_double * 5)()
     _check(load().lbm_autotune(grid.ptr, int(n_steps), C.byref(chosen), ms), "lbm_autotune")
     return chosen.value, list(ms)
 

@@ -507,7 +507,19 @@ lbm_status lbm_autotune(lbm_grid* h, int n_steps, int* chosen, double* ms_per_st
   LBM_CUDA(cudaEventCreate(&e0));
   LBM_CUDA(cudaEventCreate(&e1));
   lbm_status st = LBM_OK;
-  for (int v = 0; v < N_VARIANTS && st == LBM_OK; ++v) {
+  // candidates: the dense interior variants, or the block-sparse lean kernel
+  // and its staged form (8^3 blocks); the others keep the default kernel
+  std::vector<int> cand;
+  if (g.kind == 0) {
+    for (int v = 0; v < N_VARIANTS; ++v) cand.push_back(v);
+  } else {
+    cand.push_back(VARIANT_SCALAR);
+    if (g.lv[0].E == 8) cand.push_back(VARIANT_STAGED);
+  }
+  if (ms_per_step)
+    for (int v = 0; v <= VARIANT_STAGED; ++v) ms_per_step[v] = 0.0;
+  for (size_t c = 0; c < cand.size() && st == LBM_OK; ++c) {
+    const int v = cand[c];
     for (int l = 0; l < g.n_levels; ++l) g.lv[l].variant = v;
     st = lbm_step(h, 2, s);  // warm-up of this variant
     if (st) break;

@@ -111,8 +111,29 @@ def test_autotune_restores_state(lbm):
     lbm.lbm_step(g, 5)
     before = lbm.lbm_get_populations_f64(g, 0)
     chosen, ms = lbm.lbm_autotune(g, 10)
-    assert chosen in (0, 1, 2, 3) and all(t > 0 for t in ms)
+    assert chosen in (0, 1, 2, 3) and all(t > 0 for t in ms[:4]) and ms[4] == 0
     after = lbm.lbm_get_populations_f64(g, 0)
     m = updated_mask(flags)
     assert np.array_equal(before[:, m], after[:, m])
     assert lbm.lbm_get_info(g)["steps_done"] == 5
+
+
+def test_autotune_on_multires_restores_state(lbm):
+    """On an 8^3-block multi-resolution grid the autotuner times the default
+    lean kernel and its staged form, restores every level's state and keeps
+    the faster one."""
+    lmap = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
+    dims = (32, 32, 128)
+    g = lbm.lbm_grid_create_multires(dims, 3, lmap, lbm.physics(0.6, periodic=(1, 1, 1)))
+    for lv in range(3):
+        nx, ny, nz = (d >> lv for d in dims)
+        rho, u = wl.random_fields((nz, ny, nx), seed=47 + lv, u_amp=0.02)
+        lbm.lbm_init_equilibrium(g, lv, rho, u)
+    lbm.lbm_step(g, 2)
+    before = [lbm.lbm_get_populations_f64(g, lv) for lv in range(3)]
+    chosen, ms = lbm.lbm_autotune(g, 4)
+    assert chosen in (lbm.LBM_VARIANT_SCALAR, lbm.LBM_VARIANT_STAGED)
+    assert ms[lbm.LBM_VARIANT_SCALAR] > 0 and ms[lbm.LBM_VARIANT_STAGED] > 0
+    assert ms[0] == ms[2] == ms[3] == 0
+    for lv in range(3):
+        assert np.array_equal(lbm.lbm_get_populations_f64(g, lv), before[lv], equal_nan=True)
