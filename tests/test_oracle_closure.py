@@ -195,3 +195,115 @@ def test_closure_step_conserves_mass_in_a_walled_box():
     f1 = cl.run(f0, flags, 0.6, th, 5, periodic=(False, False, False))
     m0, m1 = f0.sum(), f1.sum()
     assert abs(m1 - m0) / m0 < 1e-13
+
+
+# ------------------------------------- filter, coarse pull and target pins
+# Each case below is built so that its answer follows by hand from the
+# definitions (box mean over r^3, pull g_i(X) = f_i(X - c_i), eddy viscosity
+# nu_t = -<tau_sgs_dev : S> / <2 rho S : S>, d_tau = 3 nu_t in coarse lattice
+# units), so a reversed difference, a flipped sign, a dropped factor or a
+# transposed axis in the oracle fails one of them.
+
+def test_box_filter_brute_force_on_distinct_values():
+    """Mean over every r^3 box of a non-cubic array with distinct values,
+    against explicit slicing (a transposed reshape mixes boxes)."""
+    rng = np.random.default_rng(31)
+    a = rng.standard_normal((2, 4, 6, 8))          # (lead, nz, ny, nx)
+    got = cl.box_filter(a, 2)
+    assert got.shape == (2, 2, 3, 4)
+    for l in range(2):
+        for Z in range(2):
+            for Y in range(3):
+                for X in range(4):
+                    box = a[l, 2 * Z:2 * Z + 2, 2 * Y:2 * Y + 2, 2 * X:2 * X + 2]
+                    assert abs(got[l, Z, Y, X] - box.mean()) < 1e-15
+    # r = 3 on a 2^3-distinct pattern: every box holds the same 27 values once
+    b = np.arange(6 * 9 * 3, dtype=np.float64).reshape(6, 9, 3)
+    got = cl.box_filter(b, 3)
+    for Z in range(2):
+        for Y in range(3):
+            assert got[Z, Y, 0] == b[3 * Z:3 * Z + 3, 3 * Y:3 * Y + 3, :].mean()
+
+
+@pytest.mark.parametrize("i", range(19))
+def test_coarse_pulled_moves_an_impulse_by_c_i(i):
+    """A unit population i filling the fine box of coarse voxel X0 is pulled
+    by the coarse voxel X0 + c_i (periodic) and by no other."""
+    r, (nz, ny, nx) = 2, (4, 6, 8)                 # coarse box, axes (z, y, x)
+    f = np.zeros((19, nz * r, ny * r, nx * r))
+    X0 = (1, 2, 3)                                 # (z, y, x)
+    f[i, X0[0] * r:(X0[0] + 1) * r, X0[1] * r:(X0[1] + 1) * r, X0[2] * r:(X0[2] + 1) * r] = 1.0
+    out = cl.coarse_pulled(f, r)
+    cxi, cyi, czi = (int(v) for v in L.C[i])
+    want = np.zeros((19, nz, ny, nx))
+    want[i, (X0[0] + czi) % nz, (X0[1] + cyi) % ny, (X0[2] + cxi) % nx] = 1.0
+    assert np.array_equal(out, want)
+
+
+def _shear_state(a, b, nu0, rho0=1.25, n=8, r=2, A=0.01, only=None):
+    """Fine periodic equilibrium state whose box-filtered velocity is a shear
+    u_b(X) = A sin(2 pi X_a / n) (X_a the coarse coordinate along axis a) and
+    whose sub-filter stress is tau_ab = tau_ba = -2 rho0 nu0 S_ab, written
+    in by a zero-mean fluctuation of u_a and u_b inside every r^3 box.
+    Axes a, b: 0 = x, 1 = y, 2 = z.  Returns (f, D) with D(X) the central
+    difference (u_b(X_a + 1) - u_b(X_a - 1)) / 2 on the coarse lattice, so
+    S_ab = D / 2.  With `only` = (cov, X0): the fluctuation sits in the one
+    box X0 = (z, y, x) with covariance cov, zero elsewhere."""
+    N = n * r
+    zyx = np.indices((n, n, n))                    # coarse (z, y, x)
+    Xa = zyx[2 - a]
+    ub = A * np.sin(2 * np.pi * Xa / n)
+    D = 0.5 * (A * np.sin(2 * np.pi * (Xa + 1) / n) - A * np.sin(2 * np.pi * (Xa - 1) / n))
+    cov = -nu0 * D                                 # <u'_a u'_b> = -2 nu0 S_ab
+    if only is not None:
+        c0, X0 = only
+        cov = np.zeros((n, n, n))
+        cov[X0] = c0
+    up = lambda c: c.repeat(r, 0).repeat(r, 1).repeat(r, 2)
+    # +1 / -1 on alternate fine x inside every box: zero box mean
+    p = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)[None, None, :]
+    al = np.sqrt(np.abs(cov))
+    be = np.sign(cov) * al
+    u = np.zeros((3, N, N, N))
+    u[b] = up(ub) + up(be) * p
+    u[a] = up(al) * p
+    rho = np.full((N, N, N), rho0)
+    return L.equilibrium(rho, u), D
+
+
+@pytest.mark.parametrize("a,b", [(1, 0), (2, 0), (0, 1), (2, 1), (0, 2), (1, 2)])
+@pytest.mark.parametrize("nu0", [0.01, -0.002])
+def test_eddy_target_recovers_a_planted_eddy_viscosity(a, b, nu0):
+    """Sub-filter stress exactly -2 rho nu0 S: the least-squares fit returns
+    nu_t = nu0 in every neighbourhood, so d_tau = 3 nu0 (0.03 and -0.006,
+    both inside the clamp for tau_c = 0.51).  A reversed central difference
+    or a flipped -num/den gives -3 nu0; a dropped 3 gives nu0; a missing
+    density in the denominator gives 1.25 x; a wrong axis gives 0."""
+    f, _ = _shear_state(a, b, nu0)
+    t = cl.eddy_target(f, 2, 0.51)
+    assert np.allclose(t, 3 * nu0, rtol=1e-9, atol=1e-12), (t.min(), t.max())
+
+
+def test_eddy_target_sums_over_the_3x3x3_neighbourhood():
+    """Sub-filter stress in one coarse voxel X0 only: the target is nonzero
+    exactly on the 27 voxels whose neighbourhood holds X0, with the value
+    -3 (2 tau_xy(X0) S_xy(X0)) / (4 rho sum_N S_xy^2), where the
+    neighbourhood sum of S_xy^2 (S_xy depends on y only) is
+    9 (S(y-1)^2 + S(y)^2 + S(y+1)^2)."""
+    rho0, n, X0 = 1.25, 8, (3, 4, 5)
+    _, D = _shear_state(1, 0, 0.0, rho0=rho0)
+    S = D / 2                                      # S_xy as a field over (z, y, x)
+    c0 = -0.06 * S[X0]                             # covariance in X0 (per unit density)
+    f, _ = _shear_state(1, 0, 0.0, rho0=rho0, only=(c0, X0))
+    t = cl.eddy_target(f, 2, 0.51)
+    Sy = S[0, :, 0]                                # S_xy along y
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                near = all(min((p - q) % n, (q - p) % n) <= 1 for p, q in zip((z, y, x), X0))
+                if near:
+                    s2 = 9 * (Sy[(y - 1) % n] ** 2 + Sy[y] ** 2 + Sy[(y + 1) % n] ** 2)
+                    want = -3 * (2 * rho0 * c0 * S[X0]) / (4 * rho0 * s2)
+                else:
+                    want = 0.0
+                assert abs(t[z, y, x] - want) <= 1e-9 * abs(want) + 1e-14, ((z, y, x), t[z, y, x], want)
