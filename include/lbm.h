@@ -279,19 +279,27 @@ lbm_status lbm_conservation(lbm_grid* g, double out_mass_mom[4]);
  * loop that must not synchronise the device (cudaMalloc / cudaFree may wait
  * for all outstanding work) or an application whose device memory belongs to
  * its own pool.
- *   f            device, dense SoA populations f[pop * n_voxels + v] in the
- *                given storage (LBM_STORAGE_*; F16 / BF16 hold f_i - w_i)
+ *   f            device, dense SoA populations f[pop * n_voxels + v], Q
+ *                arrays of the given lattice (the layout of a dense grid's
+ *                lbm_get_populations) in the given storage (LBM_STORAGE_*;
+ *                F16 / BF16 hold f_i - w_i, w_i that lattice's weights)
+ *   lattice      19 (D3Q19) or 27 (D3Q27); 0 means 19
  *   flags        device, one flag byte per voxel, or NULL (all fluid); only
  *                voxels of type 0, 2 and 3 are summed
  *   out_mass_mom device, 4 doubles: sum f_i, sum f_i c_i (FP64, deterministic)
+ * f, flags and out_mass_mom must be device (or managed) memory of the current
+ * device: host or unregistered pointers return LBM_ERR_INVALID before any
+ * launch (checked with cudaPointerGetAttributes, which neither allocates nor
+ * synchronises); the buffer sizes cannot be checked and are the caller's.
  * Asynchronous on `stream`; no allocation, copy or synchronisation.  The
  * partial sums live in one fixed device array of 4096 x 4 doubles per device
  * (held until the process exits), so n_voxels <= 67,108,864; larger inputs
- * return LBM_ERR_INVALID.  The first call on each device looks up that
- * array's device address (cudaGetSymbolAddress, once, with that device
- * current); make that first call before any stream capture.  Calls share the
- * array: calls that overlap on the GPU race, so order them on one stream. */
-lbm_status lbm_conservation_noalloc(const void* f, int storage, int64_t n_voxels,
+ * return LBM_ERR_INVALID.  The first successful call on each device looks up
+ * that array's device address (cudaGetSymbolAddress, with that device
+ * current; a failed lookup is retried by the next call); make that first call
+ * before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU race, so order them on one stream. */
+lbm_status lbm_conservation_noalloc(const void* f, int storage, int lattice, int64_t n_voxels,
                                     const uint8_t* flags, double* out_mass_mom, void* stream);
 
 /* ------------------------------------------------------- learned closure

@@ -96,7 +96,7 @@ def load():
         "lbm_sync": [vp],
         "lbm_set_variant": [vp, I],
         "lbm_autotune": [vp, I, P(I), P(C.c_double)],
-        "lbm_conservation_noalloc": [vp, I, C.c_int64, vp, vp, vp],
+        "lbm_conservation_noalloc": [vp, I, I, C.c_int64, vp, vp, vp],
         "lbm_closure_dataset": [vp, I, C.c_double, vp, vp],
         "lbm_closure_train": [vp, vp, C.c_int64, I, I, C.c_float, C.c_uint64, vp, vp, vp],
         "lbm_closure_grad": [vp, vp, vp, vp, I, vp, vp, vp],
@@ -389,11 +389,35 @@ def lbm_conservation(grid):
     return np.array(list(out))
 
 
-def lbm_conservation_noalloc(f, storage, n_voxels, flags, out, stream=None):
-    """f, flags (or None) and out (4 float64) are CUDA tensors; nothing is allocated."""
+def lbm_conservation_noalloc(f, storage, n_voxels, flags, out, stream=None, lattice=19):
+    """f, flags (or None) and out (4 float64) are contiguous CUDA tensors on
+    the current device; nothing is allocated.  The sizes are checked here,
+    before the pointers reach the kernels: f must hold lattice * n_voxels
+    stored populations, flags n_voxels bytes and out 4 doubles."""
+    import torch
     st = {"f32": 0, "f16": 1, "bf16": 2}[storage] if isinstance(storage, str) else int(storage)
+    if st not in (0, 1, 2):
+        raise ValueError("storage must be f32, f16 or bf16")
+    q = 19 if int(lattice) == 0 else int(lattice)
+    if q not in (19, 27):
+        raise ValueError("lattice must be 19 or 27")
+    dev = torch.cuda.current_device()
+    for name, t in (("f", f), ("out", out), ("flags", flags)):
+        if t is None and name == "flags":
+            continue
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is not on the current device cuda:{dev}")
+    n = int(n_voxels)
+    if out.dtype != torch.float64 or out.numel() < 4:
+        raise ValueError("out must be a float64 tensor of at least 4 elements")
+    if flags is not None and (flags.dtype != torch.uint8 or flags.numel() < n):
+        raise ValueError("flags must be a uint8 tensor of at least n_voxels elements")
+    if n > 0 and f.numel() * f.element_size() < q * n * (4 if st == 0 else 2):
+        raise ValueError(f"f holds fewer than {q} x n_voxels stored populations")
     _check(load().lbm_conservation_noalloc(
-        C.c_void_p(f.data_ptr()), st, C.c_int64(int(n_voxels)),
+        C.c_void_p(f.data_ptr()), st, q, C.c_int64(n),
         None if flags is None else C.c_void_p(flags.data_ptr()), C.c_void_p(out.data_ptr()),
         _stream_ptr(stream)), "lbm_conservation_noalloc")
 
