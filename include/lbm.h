@@ -139,8 +139,12 @@ lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge,
                                   lbm_grid** out);
 
 /* Multi-resolution grid (Sec. 5; Sec. 6.3), refinement factor 2, level 0 =
- * finest, 1 <= n_levels <= 4, periodic on every axis (phys->periodic must be
- * all 1).  level_map (host) gives the owning level of every cube of
+ * finest, 1 <= n_levels <= 4.  Axes may be periodic or walled
+ * (phys->periodic); walls, solids and regularized voxels lie on level 0
+ * only (lbm_set_boundary on level 0), so every map cell touching a walled
+ * box side must belong to level 0 (LBM_ERR_UNSUPPORTED otherwise) — the
+ * lid-driven cavity of Sec. 6.3 / Table 5 has its finest level along the
+ * walls.  level_map (host) gives the owning level of every cube of
  * C = 8 * 2^(n_levels-1) finest voxels, indexed x fastest over
  * finest_dims / C cells; finest_dims must be multiples of C and neighbouring
  * cells (26-neighbourhood, periodic) may differ by at most one level.
@@ -181,6 +185,17 @@ enum { LBM_VARIANT_VEC16 = 0, LBM_VARIANT_SCALAR = 1, LBM_VARIANT_VEC8 = 2, LBM_
        LBM_VARIANT_STAGED = 4 };
 lbm_status lbm_set_variant(lbm_grid* g, int variant);
 
+/* Time limit of the staged kernel's wait (LBM_VARIANT_STAGED; no counterpart
+ * in the paper).  Each CTA of that kernel waits for the bulk copy of its
+ * block on an mbarrier for at most `ns` nanoseconds of the GPU's global
+ * timer (default 200 ms; ns < 0 restores it).  A CTA whose wait runs out
+ * updates nothing, latches LBM_ERR_TIMEOUT (reported by lbm_sync) and, before
+ * it exits, drains its copy for up to one second more, so no copy can land
+ * in shared memory the CTA has released.  ns = 0 makes every wait run out at
+ * once, which is how the timeout path is tested; the state of that step is
+ * then not a valid update. */
+lbm_status lbm_set_wait_limit(lbm_grid* g, int64_t ns);
+
 /* Autotuner: times each variant that applies to the grid (the four dense
  * interior variants; LBM_VARIANT_SCALAR and LBM_VARIANT_STAGED on 8^3-block
  * sparse and multi-resolution grids) over n_steps steps (CUDA events on the
@@ -205,7 +220,10 @@ lbm_status lbm_set_boundary(lbm_grid* g, int level, const uint8_t* flags,
                             const float* bc_values, const float default_bc[4]);
 
 /* Initial state f* = f^eq(rho, u), evaluated in FP64 on the GPU and stored in
- * the grid's storage format.  rho: n doubles (NULL -> 1); u: 3*n doubles,
+ * the grid's storage format.  The stored state of the pull scheme is the
+ * post-collision population f* (Sec. 6: collide and stream fused in one
+ * kernel), and f^eq is the second-order equilibrium of the BGK model the
+ * paper names (Sec. 6), w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u).  rho: n doubles (NULL -> 1); u: 3*n doubles,
  * component-major (ux[n], uy[n], uz[n]) (NULL -> 0); n = level's virtual box
  * voxel count.  device_ptrs: 0 host arrays, 1 device arrays.  Page-locked
  * host arrays mapped into the device address space are read by the kernel
@@ -215,7 +233,13 @@ lbm_status lbm_init_equilibrium(lbm_grid* g, int level, const double* rho,
                                 const double* u, int device_ptrs);
 
 /* Advance n_steps time steps (coarsest steps on a multi-resolution grid) on
- * `stream`.  Asynchronous; device errors are latched.  The steps order after
+ * `stream`.  One step is the fused stream-and-collide update of Sec. 6 (pull
+ * g_i(x) = f*_i(x - c_i), halfway bounce-back on walls and obstacles and the
+ * regularized inflow / outflow nodes of Sec. 6.2, BGK or regularized
+ * collision), run as one lean kernel per voxel group (Sec. 2 Definition;
+ * Sec. 3 dense, Sec. 4 / Table 2 block-sparse); on a multi-resolution grid
+ * level l advances 2^(n_levels-1-l) times with explosion / coalescence at the
+ * level jumps and fused uniform blocks on every level (Sec. 5, Sec. 6.3).  Asynchronous; device errors are latched.  The steps order after
  * the grid's work on the stream of its previous call (and on `stream`); the
  * other calls then use `stream`.  LBM_ERR_INVALID when the grid has
  * regularized voxels whose boundary values were never given
@@ -223,14 +247,17 @@ lbm_status lbm_init_equilibrium(lbm_grid* g, int level, const double* rho,
 lbm_status lbm_step(lbm_grid* g, int n_steps, void* stream);
 
 /* Density and velocity of the stored state in FP64, virtual-box order, NaN on
- * voxels that are not updated.  rho: n doubles or NULL; u: 3*n doubles
+ * voxels that are not updated: rho = sum_i f*_i, u = sum_i f*_i c_i / rho,
+ * the macroscopic moments of the LBM state (Sec. 6).  rho: n doubles or NULL; u: 3*n doubles
  * (component-major) or NULL.  Page-locked, mapped host arrays are written by
  * the kernel in place.  Synchronises the grid's stream. */
 lbm_status lbm_get_moments(lbm_grid* g, int level, double* rho, double* u,
                            int device_ptrs);
 
 /* Raw stored populations (checkpoint format = the grid's storage layout and
- * precision).  bytes must equal info.population_bytes[level]. */
+ * precision): the dense SoA arrays of Sec. 3 (pop * N + v) or the per-block
+ * arrays of Sec. 4 ((block * Q + pop) * E^3 + voxel), post-collision f*.
+ * bytes must equal info.population_bytes[level]. */
 lbm_status lbm_get_populations(lbm_grid* g, int level, void* dst, size_t bytes,
                                int device_ptrs);
 lbm_status lbm_set_populations(lbm_grid* g, int level, const void* src,
@@ -329,7 +356,9 @@ lbm_status lbm_closure_dataset(lbm_grid* fine, int r, double tau_coarse, float* 
  * MSE loss and Adam (beta 0.9 / 0.999, eps 1e-8, learning rate lr) for
  * `steps` minibatches of `batch` samples drawn by SplitMix64 on counter
  * step*batch + b plus `seed`.  Features and targets are standardised
- * internally; theta_io (device, 5313 FP32) holds the initial weights for the
+ * internally (mean and population standard deviation of each column; a
+ * column whose deviation is below 1e-6 of its mean's magnitude counts as
+ * constant and keeps scale 1); theta_io (device, 5313 FP32) holds the initial weights for the
  * standardised problem and receives the trained weights with the
  * standardisation folded in (they take raw features).  loss_out (host, may
  * be NULL) receives the last minibatch loss (standardised).  Synchronises. */

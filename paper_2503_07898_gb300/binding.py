@@ -95,6 +95,7 @@ def load():
         "lbm_conservation": [vp, P(C.c_double)],
         "lbm_sync": [vp],
         "lbm_set_variant": [vp, I],
+        "lbm_set_wait_limit": [vp, C.c_int64],
         "lbm_autotune": [vp, I, P(I), P(C.c_double)],
         "lbm_conservation_noalloc": [vp, I, I, C.c_int64, vp, vp, vp],
         "lbm_closure_dataset": [vp, I, C.c_double, vp, vp],
@@ -291,6 +292,11 @@ VARIANT_NAMES = {0: "vec16", 1: "scalar", 2: "vec8", 3: "vec4", 4: "staged"}
 
 def lbm_set_variant(grid, variant):
     _check(load().lbm_set_variant(grid.ptr, int(variant)), "lbm_set_variant")
+
+
+def lbm_set_wait_limit(grid, ns):
+    """Time limit (ns) of the staged kernel's wait for its block copy; < 0 restores the default."""
+    _check(load().lbm_set_wait_limit(grid.ptr, C.c_int64(int(ns))), "lbm_set_wait_limit")
 
 
 def lbm_autotune(grid, n_steps):

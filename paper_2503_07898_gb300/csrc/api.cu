@@ -482,6 +482,12 @@ lbm_status lbm_set_variant(lbm_grid* h, int variant) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_wait_limit(lbm_grid* h, int64_t ns) {
+  if (!h) return fail(LBM_ERR_INVALID, "grid is NULL");
+  h->g.staged_wait_ns = ns < 0 ? Grid::kStagedWaitNs : (uint64_t)ns;
+  return LBM_OK;
+}
+
 lbm_status lbm_autotune(lbm_grid* h, int n_steps, int* chosen, double* ms_per_step) {
   if (!h || n_steps <= 0) return fail(LBM_ERR_INVALID, "bad autotune arguments");
   Grid& g = h->g;

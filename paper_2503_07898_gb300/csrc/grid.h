@@ -110,6 +110,10 @@ struct Grid {
   Level lv[4];
   int device = 0;
   int* status_d = nullptr;       // latched device status
+  // staged lean kernel: time limit of each CTA's wait for its block copy
+  // (lbm_set_wait_limit; past it the CTA latches LBM_ERR_TIMEOUT)
+  static constexpr uint64_t kStagedWaitNs = 200000000ull;
+  uint64_t staged_wait_ns = kStagedWaitNs;
   double* partials_d = nullptr;  // reduction partials (scratch)
   int n_partials = 0;
   double* sums_d = nullptr;      // 4 doubles

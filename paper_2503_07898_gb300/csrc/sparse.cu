@@ -317,6 +317,7 @@ struct SparseArgs {
   int64_t s0, s1;  // slot range [s0, s1), block aligned
   float omega;
   int* status;     // latched device status (staged kernel: a bulk copy that never lands)
+  uint64_t wait_ns;  // staged kernel: limit of the wait for the block copy
 };
 
 // ---------------------------------------------- bulk-copy staging (TMA)
@@ -347,14 +348,29 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait on phase `parity`: a copy that has not landed after the limit
-// sets the device status and the caller skips its work (no endless spin).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
-  for (int it = 0; it < (1 << 22); ++it)
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait on phase `parity`, bounded by time: false once limit_ns have passed
+// without the phase completing (limit_ns = 0: false at once, no poll).
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return false;
+  const uint64_t t0 = global_ns();
+  do {
     if (mbar_try_wait(bar, parity)) return true;
-  if (status) atomicExch(status, (int)LBM_ERR_TIMEOUT);
+  } while (global_ns() - t0 < limit_ns);
   return false;
 }
+// After a wait has given up, the CTA must not exit while its bulk copy may
+// still write its shared memory: it drains the copy for up to this long.  A
+// 19 KB (D3Q27 FP32: 55 KB) block copy lands within microseconds, so one
+// second covers any copy that is in flight; only a copy that never
+// completes (a lost transfer) can outlast it, and then the CTA leaves
+// rather than hang the device.
+constexpr uint64_t STAGED_DRAIN_NS = 1000000000ull;
 
 // One voxel (slot) of the group the mode selects.
 template <int S, int E, int COLL, int MODE>
@@ -492,10 +508,12 @@ __global__ void __launch_bounds__(SP_THREADS, Q == 27 ? 3 : (S == S_F32 ? 4 : 5)
     bulk_g2s(sb, fin + b * (Q * E3), BYTES, &bar);
   }
   __syncthreads();
-  if (!mbar_wait_bounded(&bar, 0, a.status)) {
-    // the copy may still be in flight: wait once more (bounded) before the
-    // CTA gives up its shared memory
-    mbar_wait_bounded(&bar, 0, nullptr);
+  if (!mbar_wait_ns(&bar, 0, a.wait_ns)) {
+    // the block is not updated this step: latch the timeout, then drain the
+    // copy (it may still be in flight into this CTA's shared memory) before
+    // the CTA gives that memory up
+    if (a.status) atomicExch(a.status, (int)LBM_ERR_TIMEOUT);
+    mbar_wait_ns(&bar, 0, STAGED_DRAIN_NS);
     return;
   }
   const bool walls = a.blk_walls[b] != 0;
@@ -530,6 +548,7 @@ static void launch_staged(Grid& g, SparseArgs a, cudaStream_t s, const char* nam
     opted_in = true;
   }
   a.status = g.status_d;
+  a.wait_ns = g.staged_wait_ns;
   const int pr = prof_begin(g, s, name, units);
   sparse_staged<S, COLL><<<(unsigned)((a.s1 - a.s0) / 512), SP_THREADS, BYTES, s>>>(a);
   prof_end(g, s, pr);
