@@ -31,6 +31,16 @@ training data
     learn from: the network then explains no variance.)
 loss / optimiser
     mean squared error; Adam (beta 0.9, 0.999, eps 1e-8).
+training loop (`train`)
+    features and targets standardised by their mean and population standard
+    deviation over the whole set; a column whose deviation is below 1e-6 of
+    its mean's magnitude (or zero) is constant at FP32 precision -- the tau
+    feature of a one-level training set -- and keeps scale 1, so rounding
+    noise in its deviation never becomes a huge scale in the folded layer; step
+    k = 1..K draws its minibatch of B samples by the counter-based SplitMix64
+    generator, sample b = splitmix64(seed + (k - 1) B + b) mod n; Adam on the
+    standardised problem; the standardisation is folded into the first and
+    last layers at the end (`fold_normalisation`).
 """
 import numpy as np
 
@@ -217,3 +227,57 @@ def run(f, flags, tau, theta, n_steps, **kw):
     for _ in range(n_steps):
         f = step(f, flags, tau, theta, **kw)
     return f
+
+
+# ------------------------------------------------------------ training loop
+
+_M64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix64(x):
+    """SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+    generators", OOPSLA 2014) as a function of its 64-bit counter: add the
+    golden-ratio increment, then the two xor-shift-multiply rounds and a final
+    xor-shift of the published generator."""
+    x = (int(x) + _GOLDEN) & _M64
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & _M64
+    return x ^ (x >> 31)
+
+
+def minibatch_indices(seed, step, batch, n):
+    """Samples of training step `step` (counted from 1)."""
+    c0 = (step - 1) * batch
+    return np.array([splitmix64(seed + c0 + b) % n for b in range(batch)], dtype=np.int64)
+
+
+def standardisation(X, t):
+    """(mu, sd, t_mean, t_sd): column means and population standard deviations
+    of the features and the target; a constant column (deviation <= 1e-6
+    |mean|, or zero) keeps scale 1."""
+    X = np.asarray(X, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    mu, sd = X.mean(axis=0), X.std(axis=0)
+    sd = np.where((sd > 1e-6 * np.abs(mu)) & (sd > 1e-30), sd, 1.0)
+    tm, ts = float(t.mean()), float(t.std())
+    return mu, sd, tm, (ts if ts > 1e-6 * abs(tm) and ts > 1e-30 else 1.0)
+
+
+def train(X, t, theta0, steps, batch, lr, seed):
+    """Adam on the standardised problem for `steps` SplitMix64 minibatches from
+    theta0 (weights of the standardised problem); returns the weights with the
+    standardisation folded in (taking raw features, giving raw d_tau) and the
+    last minibatch loss (standardised)."""
+    X = np.asarray(X, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    mu, sd, tm, ts = standardisation(X, t)
+    theta = np.asarray(theta0, dtype=np.float64).copy()
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    loss = None
+    for k in range(1, steps + 1):
+        idx = minibatch_indices(seed, k, batch, X.shape[0])
+        loss, g = loss_and_grad(theta, (X[idx] - mu) / sd, (t[idx] - tm) / ts)
+        theta, m, v = adam(theta, g, m, v, k, lr=lr)
+    return fold_normalisation(theta, mu, sd, tm, ts), loss

@@ -173,7 +173,10 @@ __global__ void k_stats(const float* X, const float* T, int64_t n, float* stats)
     const double mean = s1[0] / (double)n;
     double var = s2[0] / (double)n - mean * mean;
     double sd = var > 0 ? sqrt(var) : 0.0;
-    if (!(sd > 1e-30)) sd = 1.0;  // constant column
+    // constant column (the tau feature of a one-level set): a deviation below
+    // 1e-6 of the mean's magnitude is rounding noise of the FP64 sums, and as
+    // a scale it would blow up the folded first layer
+    if (!(sd > 1e-30) || !(sd > 1e-6 * fabs(mean))) sd = 1.0;
     const int im = c < MLP_IN ? c : 2 * MLP_IN, is = c < MLP_IN ? MLP_IN + c : 2 * MLP_IN + 1;
     stats[im] = (float)mean;
     stats[is] = (float)sd;

@@ -99,6 +99,38 @@ def test_dataset_matches_oracle(lbm):
     assert np.abs(T - T_ref).max() <= 1e-3 * np.abs(T_ref).max()
 
 
+def test_training_steps_match_oracle_adam(lbm):
+    """lbm_closure_train for 5 Adam steps against the oracle's training loop
+    on the same data: the same SplitMix64 minibatches (both sides implement
+    the published generator on the counter step * batch + b), the same
+    standardisation (with a constant tau column, which keeps scale 1) and the
+    same fold.  The folded weights agree norm-wise to 1e-5, and to 1e-3 of
+    what the five steps changed; the last minibatch loss to 1e-5."""
+    import torch
+    rng = np.random.default_rng(107)
+    n = 6000
+    scale = np.logspace(-4, 0, 16)
+    X = rng.standard_normal((n, 16)) * scale + rng.standard_normal(16) * scale
+    X[:, 15] = 0.501                                      # constant tau feature
+    t = 0.01 * np.tanh(X[:, 0] / scale[0] - 0.5 * X[:, 5] / scale[5]) + 0.003 * X[:, 9] / scale[9]
+    X32, t32 = X.astype(np.float32), t.astype(np.float32)
+    th0 = he_init(108).astype(np.float32)
+    th = cuda(th0)
+    loss = lbm.lbm_closure_train(cuda(X32), cuda(t32), 5, 512, 1e-3, 77, th)
+    got = th.cpu().numpy().astype(np.float64)
+    ref, ref_loss = ocl.train(X32.astype(np.float64), t32.astype(np.float64),
+                              th0.astype(np.float64), 5, 512, 1e-3, 77)
+    mu, sd, tm, ts = ocl.standardisation(X32, t32)
+    moved = np.linalg.norm(ref - ocl.fold_normalisation(th0.astype(np.float64), mu, sd, tm, ts))
+    err = np.linalg.norm(got - ref)
+    print(f"5 Adam steps: |GPU - oracle| {err:.3e}, |oracle update| {moved:.3e}, "
+          f"|weights| {np.linalg.norm(ref):.3e}")
+    assert moved > 0.05
+    assert err <= 1e-5 * np.linalg.norm(ref)
+    assert err <= 1e-3 * moved
+    assert abs(loss / ref_loss - 1) <= 1e-5
+
+
 def test_training_is_deterministic_and_learns(lbm):
     import torch
     rng = np.random.default_rng(105)
@@ -176,17 +208,18 @@ def storage_weights(theta):
     return out
 
 
-@pytest.mark.parametrize("collision", ["bgk", "reg"])
-def test_multires_step_with_closure_matches_oracle(lbm, collision):
+@pytest.mark.parametrize("collision,steps", [("bgk", 25), ("reg", 3)])
+def test_multires_step_with_closure_matches_oracle(lbm, collision, steps):
     """The closure fused into the multi-resolution collision (levels 1 and 2
     of a coarse - middle - fine - middle hierarchy) against the FP64 oracle
-    running the same BF16-rounded network.  Tolerance: the FP32 bar plus the
-    oracle's own response to a 2e-2 relative change of d_tau (the BF16
-    network's bound against the FP64 one)."""
+    running the same BF16-rounded network; BGK for 25 coarsest steps (100
+    level-0 substeps), REG for 3.  Tolerance: the FP32 bar plus the oracle's
+    own response to a 2e-2 relative change of d_tau (the BF16 network's bound
+    against the FP64 one)."""
     from cases import F32_RTOL
     from oracle import multires as omr
     lmap = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
-    tau0, steps = 0.56, 3
+    tau0 = 0.56
     dims = (32, 32, 128)
     fields = []
     for lv in range(3):

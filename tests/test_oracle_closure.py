@@ -307,3 +307,52 @@ def test_eddy_target_sums_over_the_3x3x3_neighbourhood():
                 else:
                     want = 0.0
                 assert abs(t[z, y, x] - want) <= 1e-9 * abs(want) + 1e-14, ((z, y, x), t[z, y, x], want)
+
+
+# ----------------------------------------------------------- training loop
+
+def test_splitmix64_published_sequence():
+    """The first outputs of the published SplitMix64 generator seeded with 0
+    (its state advances by the golden-ratio increment per call)."""
+    g = 0x9E3779B97F4A7C15
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    got = [cl.splitmix64((k * g) & ((1 << 64) - 1)) for k in range(3)]
+    assert got == want
+
+
+def test_minibatch_counter_layout():
+    """Step k draws samples from counters seed + (k - 1) B .. seed + k B - 1."""
+    idx = cl.minibatch_indices(5, 3, 4, 1000)
+    assert list(idx) == [cl.splitmix64(5 + 8 + b) % 1000 for b in range(4)]
+    assert np.all((idx >= 0) & (idx < 1000))
+
+
+def test_train_one_step_is_adam_on_the_standardised_minibatch():
+    """One step: the folded result equals Adam's first step (|update| = lr per
+    parameter, sign of the minibatch gradient of the standardised problem),
+    folded; a constant feature column keeps scale 1."""
+    rng = np.random.default_rng(40)
+    X = rng.standard_normal((300, 16)) * np.arange(1, 17) + 3.0
+    X[:, 15] = 0.51                                        # constant (tau)
+    t = 0.01 * X[:, 0] - 0.002 * X[:, 4] ** 2
+    th0 = random_theta(41)
+    got, _ = cl.train(X, t, th0, 1, 64, 1e-3, 9)
+    mu, sd = X.mean(0), X.std(0)
+    assert sd[15] < 1e-6 * 0.51          # rounding noise of a constant column
+    sd[15] = 1.0
+    idx = [cl.splitmix64(9 + b) % 300 for b in range(64)]
+    _, g = cl.loss_and_grad(th0, (X[idx] - mu) / sd, (t[idx] - t.mean()) / t.std())
+    step = th0 - 1e-3 * g / (np.abs(g) + 1e-8)
+    want = cl.fold_normalisation(step, mu, sd, t.mean(), t.std())
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-15)
+
+
+def test_train_lowers_the_loss():
+    rng = np.random.default_rng(42)
+    X = rng.standard_normal((2000, 16))
+    t = np.tanh(X[:, 0] - 0.5 * X[:, 3])
+    th0 = random_theta(43, scale=0.2)
+    y0, _ = cl.forward(cl.fold_normalisation(th0, X.mean(0), X.std(0), t.mean(), t.std()), X)
+    th, _ = cl.train(X, t, th0, 300, 128, 3e-3, 1)
+    y1, _ = cl.forward(th, X)
+    assert np.mean((y1 - t) ** 2) < 0.5 * np.mean((y0 - t) ** 2)
