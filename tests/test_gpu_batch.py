@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from cases import F32_RTOL, max_rel_err, run_oracle, updated_mask
+from oracle import lbm as olbm
 from paper_2503_07898_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +57,54 @@ def test_batch_cases_match_oracle(lbm):
         rho, u = wl.batch_case_fields(c)
         ref = run_oracle(c["flags"], None, rho, u, c["tau"], 20, periodic=(1, 1, 1))
         assert max_rel_err(lbm.lbm_get_populations_f64(g, 0), ref, c["flags"]) <= F32_RTOL
+
+
+# FP16 storage rounds each stored population once per update; collision
+# damps earlier roundings, so the relative velocity error stays near the
+# format's unit roundoff: bound 4 u = 4 x 2^-11 (as for the other layouts)
+F16_VEL_L2 = 4 * 2.0 ** -11
+
+
+def fp16_cases():
+    """Serving-batch cases at both ends of the tau range: dense and 8^3
+    block-sparse, random spheres and boxes, a 64^3 case."""
+    specs = [("dense", (64, 64, 64), 0.10, "spheres", 0.52),
+             ("sparse", (48, 40, 56), 0.15, "boxes", 0.80),
+             ("dense", (40, 32, 48), 0.20, "boxes", 0.66),
+             ("sparse", (64, 48, 40), 0.05, "spheres", 0.52)]
+    out = []
+    for k, (kind, dims, frac, shape, tau) in enumerate(specs):
+        nx, ny, nz = dims
+        flags = wl.random_obstacles((nz, ny, nx), seed=170 + k, solid_fraction=frac, kind=shape)
+        out.append({"kind": kind, "dims": dims, "flags": flags, "tau": tau, "u0": 0.02,
+                    "solid_fraction": frac})
+    return out
+
+
+def test_fp16_batch_matches_oracle_and_individual_runs(lbm):
+    """The FP16 serving form: 100 batched steps give every case the
+    populations of the same case stepped alone bit for bit, and a velocity
+    field within 4 unit roundoffs of FP16 (relative L2 over the fluid
+    voxels) of the FP64 oracle."""
+    cases = fp16_cases()
+    grids = [make_case(lbm, c, "f16") for c in cases]
+    alone = [make_case(lbm, c, "f16") for c in cases]
+    b = lbm.lbm_batch_create(grids)
+    lbm.lbm_batch_autotune(b, 2)
+    lbm.lbm_batch_step(b, 100)
+    for g in alone:
+        lbm.lbm_step(g, 100)
+    for c, g, a in zip(cases, grids, alone):
+        m = updated_mask(c["flags"])
+        fb = lbm.lbm_get_populations_f64(g, 0)
+        assert np.array_equal(fb[:, m], lbm.lbm_get_populations_f64(a, 0)[:, m]), c["kind"]
+        rho, u = wl.batch_case_fields(c)
+        ref = run_oracle(c["flags"], None, rho, u, c["tau"], 100, periodic=(1, 1, 1))
+        _, ur = olbm.state_moments(ref)
+        _, ug = lbm.lbm_get_moments(g, 0)
+        l2 = float(np.sqrt(((ug[:, m] - ur[:, m]) ** 2).sum() / (ur[:, m] ** 2).sum()))
+        print(f"{c['kind']} {c['dims']} tau {c['tau']}: FP16 velocity L2 vs oracle {l2:.3e}")
+        assert l2 <= F16_VEL_L2
 
 
 def test_batch_autotune_restores_states(lbm):

@@ -61,8 +61,8 @@ def test_two_level_parity(lbm, schedule):
     g, dims, cell = make_mr(lbm, LMAP2, 2, 0.6, schedule)
     o = omr.MultiRes(LMAP2, 2, cell, 0.6)
     init_both(lbm, g, o, level_fields(dims, 2, 60))
-    lbm.lbm_step(g, 20)
-    o.run(20)
+    lbm.lbm_step(g, 50)               # 100 level-0 substeps
+    o.run(50)
     assert compare(lbm, g, o, 2) <= F32_RTOL
 
 
@@ -71,8 +71,8 @@ def test_three_level_parity(lbm, collision):
     g, dims, cell = make_mr(lbm, LMAP3, 3, 0.58, collision=collision)
     o = omr.MultiRes(LMAP3, 3, cell, 0.58, collision)
     init_both(lbm, g, o, level_fields(dims, 3, 61))
-    lbm.lbm_step(g, 8)
-    o.run(8)
+    lbm.lbm_step(g, 25)               # 100 level-0 substeps
+    o.run(25)
     assert compare(lbm, g, o, 3) <= F32_RTOL
 
 
@@ -211,11 +211,12 @@ def cavity_fields(n, n_levels, seed):
 
 @pytest.mark.parametrize("schedule", ["disaggregated", "monolithic"])
 def test_cavity_two_level_parity(lbm, schedule):
-    """Walls and the regularized lid on level 0, level 1 in the middle."""
+    """Walls and the regularized lid on level 0, level 1 in the middle; 50
+    coarsest steps (100 level-0 substeps)."""
     g, o = make_cavity(lbm, 48, 2, (1,), 0.6, schedule)
     init_both(lbm, g, o, cavity_fields(48, 2, 70))
-    lbm.lbm_step(g, 4)
-    o.run(4)
+    lbm.lbm_step(g, 50)
+    o.run(50)
     assert compare(lbm, g, o, 2) <= F32_RTOL
 
 

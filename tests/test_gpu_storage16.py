@@ -143,7 +143,8 @@ def test_multires_three_level_16bit(lbm, storage, schedule):
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_multires_cavity_16bit(lbm, storage):
-    """Two-level lid-driven cavity (walls and regularized lid on level 0)."""
+    """Two-level lid-driven cavity (walls and regularized lid on level 0), 50
+    coarsest steps."""
     n = 48
     lmap = wl.multires_cavity_map(n, 2, (1,))
     g = lbm.lbm_grid_create_multires((n,) * 3, 2, lmap, lbm.physics(
@@ -157,8 +158,8 @@ def test_multires_cavity_16bit(lbm, storage):
     for lv, (r, v) in enumerate(fields):
         lbm.lbm_init_equilibrium(g, lv, r, v)
         o.init_equilibrium(lv, r, v)
-    lbm.lbm_step(g, 20)
-    o.run(20)
+    lbm.lbm_step(g, 50)               # 100 level-0 substeps
+    o.run(50)
     errs = mr_velocity_errors(lbm, g, o, 2)
     print(f"multires cavity {storage}: velocity L2 per level {errs}")
     assert max(errs) <= VEL_L2[storage]
