@@ -9,8 +9,13 @@ L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line.  --impl reference times the FP64 oracle (the plain
-numpy program the CUDA path is checked against) on the host cores.
+Prints one JSON line.  Every result carries its velocity-L2 error against
+the FP64 oracle ("velocity_l2_vs_fp64"): the line's kernels run a reduced
+case of the same workload whose oracle velocities are stored in
+tests/golden/ (written by oracle/make_bench_references.py; the bench itself
+runs no oracle code for this).  cpu_baseline times the FP64 oracle on the
+host cores (one single-threaded process per core, and one alone);
+--impl reference times the same oracle as the reference arm.
 """
 import argparse
 import hashlib
@@ -21,12 +26,18 @@ import sys
 import threading
 import time
 
+if "--cpu-sample" in sys.argv:
+    # a CPU-baseline child: one thread per process (the parent also sets these)
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = {"f32": 152, "f16": 76, "bf16": 76}   # 19 loads + 19 stores
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
 METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated error"
 
 # DRAM traffic of the dominant kernel from an ncu capture (profiles/), valid
@@ -107,21 +118,61 @@ class Clocks:
 
 # ------------------------------------------------------------------ oracle
 
-def oracle_cavity_glups(n, steps, tau=0.515, u_lid=0.05):
-    """The FP64 oracle as it stands on an n^3 cavity (same physics as the
-    GPU workload); returns (GLUPS, seconds)."""
+def cpu_sample(n, steps, warmup):
+    """Child process body: the FP64 oracle as it stands on an n^3 cavity (the
+    GPU workload's boundaries, tau 0.515, lid 0.05); prints its timed window."""
     from oracle import lbm as olbm
     from paper_2503_07898_gb300 import workloads as wl
-    flags, bc = wl.cavity(n, u_lid=u_lid)
+    flags, bc = wl.cavity(n, u_lid=0.05)
     f = olbm.init_equilibrium(np.ones((n, n, n)), np.zeros((3, n, n, n)))
-    f = olbm.step(f, flags, tau, bc=bc)          # warm-up
-    c0 = time.process_time()
-    t0 = time.perf_counter()
+    for _ in range(warmup):
+        f = olbm.step(f, flags, 0.515, bc=bc)
+    t0 = time.time()
     for _ in range(steps):
-        f = olbm.step(f, flags, tau, bc=bc)
-    dt = time.perf_counter() - t0
-    cores = (time.process_time() - c0) / dt      # threads numpy/BLAS actually kept busy
-    return n ** 3 * steps / dt / 1e9, dt, round(cores, 1)
+        f = olbm.step(f, flags, 0.515, bc=bc)
+    t1 = time.time()
+    print(json.dumps({"updates": n ** 3 * steps, "t0": t0, "t1": t1}), flush=True)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_cpu_glups(n, steps, warmup, procs):
+    """GLUPS of `procs` single-threaded oracle processes running the n^3
+    cavity sample side by side: all their updates over the span from the
+    first timed window's start to the last one's end (the processes start
+    together; interpreter start-up and warm-up lie outside the windows).
+    Returns (GLUPS, seconds)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(n), str(steps),
+           str(warmup)]
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                           env=env) for _ in range(procs)]
+    rows = []
+    for p in ps:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("CPU baseline sample failed")
+        rows.append(json.loads(out.strip().splitlines()[-1]))
+    span = max(r["t1"] for r in rows) - min(r["t0"] for r in rows)
+    return sum(r["updates"] for r in rows) / span / 1e9, span
+
+
+def cpu_baseline_line(n=64, steps=100):
+    """The oracle timed on the host cores: one single-threaded process, then
+    one per available core side by side (about 20 s of host time)."""
+    cores = host_cores()
+    one, dt1 = oracle_cpu_glups(n, steps, 1, 1)
+    allc, dta = oracle_cpu_glups(n, steps, 1, cores)
+    return {"value": allc, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n}^3 cavity (tau 0.515, lid 0.05), {steps} steps per process, numpy FP64, "
+                      f"one thread per process ({cores} processes side by side, {dta:.1f} s)",
+            "single_core": {"value": one, "unit": "GLUPS", "cores": 1, "seconds": round(dt1, 2)},
+            "nproc": os.cpu_count(), "threads_per_process": 1}
 
 
 def max_over_ranks(dist, x, device):
@@ -145,10 +196,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     n = 48 if args.steps <= 1000 else 32
-    from oracle import lbm as olbm  # noqa: F401
-    oracle_cavity_glups(n, max(1, args.warmup))
-    value, dt, cores = oracle_cavity_glups(n, args.steps)
-    sample = f"{n}^3 cavity window of the 256^3 workload, tau 0.515, lid 0.05, numpy FP64"
+    cores = host_cores()
+    value, dt = oracle_cpu_glups(n, args.steps, args.warmup, cores)
+    sample = (f"{n}^3 cavity window of the 256^3 workload per process (tau 0.515, lid 0.05), "
+              f"numpy FP64, one thread per process, {cores} processes side by side")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -174,17 +225,131 @@ def _time_steps(torch, lbm, step, stream, n):
     return e0.elapsed_time(e1)
 
 
-def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
+REFS = os.path.join(ROOT, "tests", "golden", "bench_velocity_references.npz")
+
+
+class Accuracy:
+    """Velocity-L2 error against the FP64 oracle of a bench line's form: the
+    reduced case of the line's workload (workloads.accuracy_cases: same
+    layout, boundaries, relaxation time and start, small enough for the
+    oracle) runs through the library with the line's storage, collision,
+    schedule and kernel variant; its velocity at the case's sampled updated
+    voxels is compared with the oracle's, stored by
+    oracle/make_bench_references.py (the bench never runs the oracle for
+    this).  L2 = sqrt(sum |u - u_ref|^2 / sum |u_ref|^2) over the samples,
+    each sample weighted by the volume it stands for (8^l times the level's
+    updated voxels over its samples on multi-resolution grids)."""
+
+    def __init__(self, lbm, wl):
+        self.lbm, self.wl = lbm, wl
+        self.cases = wl.accuracy_cases()
+        self.refs = dict(np.load(REFS)) if os.path.exists(REFS) else {}
+        self.manifest = json.loads(str(self.refs["manifest"])) if "manifest" in self.refs else {}
+
+    def _bc_list(self, flags, bc):
+        t = flags & 7
+        return np.ascontiguousarray(bc[:, (t == 2) | (t == 3)].T, np.float32)
+
+    def _gpu(self, case, samples, storage, collision, schedule, variant, theta):
+        """Velocities at the samples after the case's steps, and the weight of
+        each sample set."""
+        lbm, wl = self.lbm, self.wl
+        kind = case["kind"]
+        if kind in ("dense", "sparse"):
+            flags = case["flags"]
+            nz, ny, nx = flags.shape
+            phys = lbm.physics(case["tau"], collision, storage, case["periodic"], schedule,
+                               lattice=case["q"])
+            if kind == "dense":
+                g = lbm.lbm_grid_create_dense((nx, ny, nz), phys)
+                lbm.lbm_set_boundary(g, 0, flags, self._bc_list(flags, case["bc"]))
+            else:
+                g = lbm.lbm_grid_create_sparse((nx, ny, nz), 8, flags, phys)
+                lbm.lbm_set_boundary(g, 0, None, self._bc_list(flags, case["bc"]))
+            if variant is not None:
+                lbm.lbm_set_variant(g, variant)
+            rho, u = case["fields"][0]
+            lbm.lbm_init_equilibrium(g, 0, rho, u)
+            lbm.lbm_step(g, case["steps"])
+            _, ug = lbm.lbm_get_moments(g, 0)
+            lbm.lbm_grid_destroy(g)
+            return [ug.reshape(3, -1)[:, samples[0]]], [1.0]
+        if kind == "batch":
+            grids = []
+            for c in case["cases"]:
+                phys = lbm.physics(c["tau"], collision, storage, (1, 1, 1))
+                if c["kind"] == "dense":
+                    g = lbm.lbm_grid_create_dense(c["dims"], phys)
+                    lbm.lbm_set_boundary(g, 0, c["flags"])
+                else:
+                    g = lbm.lbm_grid_create_sparse(c["dims"], 8, c["flags"], phys)
+                lbm.lbm_init_equilibrium(g, 0, *wl.batch_case_fields(c))
+                grids.append(g)
+            b = lbm.lbm_batch_create(grids)
+            if theta is not None:
+                lbm.lbm_batch_closure_load(b, theta, 64)
+            lbm.lbm_batch_step(b, case["steps"])
+            us, ws = [], []
+            for g, idx in zip(grids, samples):
+                us.append(lbm.lbm_get_moments(g, 0)[1].reshape(3, -1)[:, idx])
+                ws.append(lbm.lbm_get_info(g)["n_updated"][0] / len(idx))
+            del b
+            for g in grids:
+                lbm.lbm_grid_destroy(g)
+            return us, ws
+        L = case["n_levels"]
+        phys = lbm.physics(case["tau"], collision, storage, case["periodic"], schedule,
+                           closure=1 if theta is not None else 0, lattice=case["q"])
+        g = lbm.lbm_grid_create_multires(case["dims"], L, case["level_map"], phys)
+        if variant is not None:
+            lbm.lbm_set_variant(g, variant)
+        if case["flags"] is not None:
+            lbm.lbm_set_boundary(g, 0, case["flags"], self._bc_list(case["flags"], case["bc"]))
+        if theta is not None:
+            lbm.lbm_closure_load(g, theta)
+        for lv, (rho, u) in enumerate(case["fields"]):
+            lbm.lbm_init_equilibrium(g, lv, rho, u)
+        lbm.lbm_step(g, case["steps"])
+        info = lbm.lbm_get_info(g)
+        us = [lbm.lbm_get_moments(g, lv)[1].reshape(3, -1)[:, samples[lv]] for lv in range(L)]
+        ws = [8.0 ** lv * info["n_updated"][lv] / max(1, len(samples[lv])) for lv in range(L)]
+        lbm.lbm_grid_destroy(g)
+        return us, ws
+
+    def run(self, name, storage="f32", collision="bgk", schedule="disaggregated", variant=None):
+        case = self.cases[name]
+        samples = self.wl.accuracy_samples(case)
+        steps_key = "after_coarsest_steps" if case["kind"] == "multires" else "after_steps"
+        base = {"l2_case": name, steps_key: case["steps"]}
+        for k, idx in enumerate(samples):
+            ref = self.refs.get(f"{name}/idx{k}")
+            if ref is None or not np.array_equal(ref, idx):
+                return dict(base, velocity_l2_vs_fp64=None, why="no stored oracle reference")
+        us, ws = self._gpu(case, samples, storage, collision, schedule, variant,
+                           case.get("theta"))
+        num = den = 0.0
+        for k, (u, w) in enumerate(zip(us, ws)):
+            ur = self.refs[f"{name}/u{k}"].astype(np.float64)
+            num += w * float(((u - ur) ** 2).sum())
+            den += w * float((ur ** 2).sum())
+        return dict(base, velocity_l2_vs_fp64=float(f"{np.sqrt(num / den):.3e}"))
+
+    def cases_used(self):
+        return {k: v["what"] for k, v in self.manifest.items()}
+
+
+def measure_workloads(torch, lbm, wl, stream, peak, steps, which, acc, theta=None, n_batch=128):
     """GLUPS of the other layouts of the method on their full-size inputs
-    (context lines of the same metric; each timed after 3 warm-up steps)."""
+    (context lines of the same metric; each timed after 3 warm-up steps),
+    each with its velocity-L2 error against the FP64 oracle (Accuracy).
+    theta: the learned closure's trained weights for the closure lines
+    (None: a fixed test network of the same size; the cost of inference does
+    not depend on the values)."""
     STAGED = lbm.LBM_VARIANT_STAGED
     out = {}
-    # a closure network of the trained one's size and scale (random weights:
-    # the cost of inference does not depend on their values)
-    rng = np.random.default_rng(0)
-    theta = np.concatenate([rng.standard_normal(1024) * 0.35, np.zeros(64),
-                            rng.standard_normal(4096) * 0.18, np.zeros(64),
-                            rng.standard_normal(64) * 1e-3, np.zeros(1)]).astype(np.float32)
+    trained = theta is not None
+    if theta is None:
+        theta = wl.closure_test_network()
     if "sparse" in which:
         flags, bc = wl.sphere_channel()
         t = flags & 7
@@ -222,9 +387,17 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
                              "roofline_frac": round(glups * bpu / peak, 4),
                              "bytes_per_update": bpu}
                 lbm.lbm_grid_destroy(g)
+                res[name].update(acc.run(f"sphere_small_q{q}", storage=kw["storage"],
+                                         schedule=kw.get("schedule", "disaggregated"),
+                                         variant=kw.get("variant")))
             out[key] = res
     if "multires" in which or "turbulence" in which:
+        # the configuration's start: seeded k^-5/3 field, u_rms 0.03, on the
+        # 256^3 finest box, coarser levels the means over their cubes
         lmap = wl.multires_slab_map()
+        rho, u = wl.turbulence(256, seed=7898, u_rms=0.03)
+        fields = wl.level_fields(rho, u, 3)
+        del rho, u
         res = {}
         for name, kw in (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
                          ("unfused_f32", dict(schedule="monolithic")),
@@ -243,7 +416,7 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             info = lbm.lbm_get_info(g)
             ups = sum(n * 2 ** (2 - l) for l, n in enumerate(info["n_updated"]))
             for l in range(3):
-                lbm.lbm_init_equilibrium(g, l, None, None)
+                lbm.lbm_init_equilibrium(g, l, *fields[l])
             lbm.lbm_step(g, 3, stream)
             ms = _time_steps(torch, lbm, lambda n: lbm.lbm_step(g, n, stream), stream,
                              max(1, steps // 4))
@@ -251,14 +424,26 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             bpu = (76 if kw.get("storage") == "f16" else 152) * kw.get("lattice", 19) // 19
             res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
             lbm.lbm_grid_destroy(g)
+            acc_case = ("turb3_closure" if kw.get("closure") else
+                        f"turb3_q{kw.get('lattice', 19)}")
+            res[name].update(acc.run(acc_case, storage=kw.get("storage", "f32"),
+                                     schedule=kw.get("schedule", "disaggregated"),
+                                     variant=kw.get("variant")))
         res["updates_per_coarsest_step"] = ups
+        res["start"] = "seeded k^-5/3 field (seed 7898, u_rms 0.03), coarse levels its cube means"
+        res["closure_weights"] = ("trained (learned_closure_quality)" if trained else
+                                  "a fixed test network (workloads.closure_test_network)")
         out["turbulence_256_3level"] = res
-    cavities = ((384, 3, (2, 2), (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
-                                  ("unfused_f32", dict(schedule="monolithic")),
-                                  ("fused_f16", dict(storage="f16")))),
-                (512, 4, (1, 1, 1), (("fused_f32", dict()),
-                                     ("unfused_f32", dict(schedule="monolithic")))))
-    for n, nlev, shells, cases in (cavities if ("multires" in which or "cavity" in which) else ()):
+        del fields
+    cavities = ((384, 3, (2, 2), "cavity3_160",
+                 (("fused_f32", dict()), ("fused_f32_staged", dict(variant=STAGED)),
+                  ("unfused_f32", dict(schedule="monolithic")),
+                  ("fused_f16", dict(storage="f16")))),
+                (512, 4, (1, 1, 1), "mr4_small",
+                 (("fused_f32", dict()),
+                  ("unfused_f32", dict(schedule="monolithic")))))
+    for n, nlev, shells, acc_case, cases in (cavities if ("multires" in which or "cavity" in which)
+                                             else ()):
         # the paper's multi-resolution benchmark (Sec. 6.3, Table 5): a
         # lid-driven cavity, finest level along the walls and the lid
         lmap = wl.multires_cavity_map(n, nlev, shells)
@@ -284,6 +469,9 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
             bpu = 76 if kw.get("storage") == "f16" else 152
             res[name] = {"GLUPS": round(glups, 3), "roofline_frac": round(glups * bpu / peak, 4)}
             lbm.lbm_grid_destroy(g)
+            res[name].update(acc.run(acc_case, storage=kw.get("storage", "f32"),
+                                     schedule=kw.get("schedule", "disaggregated"),
+                                     variant=kw.get("variant")))
         tot = n ** 3
         res["pct_of_finest_box_voxels"] = [round(100 * k / tot, 3) for k in info["n_updated"][:nlev]]
         res["voxels_per_level"] = list(info["n_updated"][:nlev])
@@ -309,10 +497,10 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
         torch.cuda.synchronize()
         ms = _time_steps(torch, lbm, lambda n: lbm.lbm_batch_step(b, n, stream), stream, steps)
         glups = info["n_updated"] * steps / (ms * 1e-3) / 1e9
-        out[f"serving_batch_{n_batch}_f16"] = {"GLUPS": round(glups, 3),
-                                        "roofline_frac": round(glups * 76 / peak, 4),
-                                        "updated_voxels": info["n_updated"],
-                                        "ctas_per_sm": k, "launches_per_step": 1}
+        out[f"serving_batch_{n_batch}_f16"] = dict(
+            {"GLUPS": round(glups, 3), "roofline_frac": round(glups * 76 / peak, 4),
+             "updated_voxels": info["n_updated"], "ctas_per_sm": k, "launches_per_step": 1},
+            **acc.run("batch_small", storage="f16"))
         # the learned closure on the cases whose largest edge is <= 64
         lbm.lbm_batch_closure_load(b, theta, 64)
         n_cl = sum(1 for c in cases if max(c["dims"]) <= 64)
@@ -321,77 +509,107 @@ def measure_workloads(torch, lbm, wl, stream, peak, steps, which, n_batch=128):
         torch.cuda.synchronize()
         ms = _time_steps(torch, lbm, lambda n: lbm.lbm_batch_step(b, n, stream), stream, steps)
         glups = info["n_updated"] * steps / (ms * 1e-3) / 1e9
-        out[f"serving_batch_{n_batch}_f16_learned_closure"] = {
-            "GLUPS": round(glups, 3), "roofline_frac": round(glups * 76 / peak, 4),
-            "closure_cases": n_cl, "max_edge": 64, "ctas_per_sm": k, "launches_per_step": 1}
+        out[f"serving_batch_{n_batch}_f16_learned_closure"] = dict(
+            {"GLUPS": round(glups, 3), "roofline_frac": round(glups * 76 / peak, 4),
+             "closure_cases": n_cl, "max_edge": 64, "ctas_per_sm": k, "launches_per_step": 1},
+            **acc.run("batch_small_closure", storage="f16"))
         del b
         for g in grids:
             lbm.lbm_grid_destroy(g)
     return out
 
 
-def closure_quality(torch, lbm, wl, N=64, r=4, tau_f=0.504, T=192, kmax=16, urms=0.03):
-    """Error of the learned closure, through the library's own dataset and
-    training kernels: fine N^3 decaying turbulence at tau_f (two seeds,
-    snapshots every 16 steps) gives the training set of a level r times
-    coarser; the trained network then runs on that coarse level of a 3-level
-    grid (tau_2 = 1/2 + (tau_f - 1/2) / r) started from the box-filtered fine
-    field of a third seed.  Reported: velocity L2 against the box-filtered
-    fine run after T fine steps, with and without the closure."""
-    def box(a):
-        *lead, nz, ny, nx = a.shape
-        return a.reshape(*lead, nz // r, r, ny // r, r, nx // r, r).mean(axis=(-5, -3, -1))
-
-    tau_c = 0.5 + (tau_f - 0.5) / r
-    nc = (N // r) ** 3
-    feats, targs = [], []
+def closure_quality(torch, lbm, wl, N=256, tau0=0.504, T=128, kmax=32, urms=0.03,
+                    train_seeds=(11, 12), eval_seeds=(23, 24, 25), train_steps=4000):
+    """The learned closure at the configuration's scale, through the library's
+    own dataset and training kernels.  Training: plain fine N^3 periodic
+    decaying turbulence at tau0 (k^-5/3 start, u_rms, two seeds), snapshots
+    every 16 steps, filtered by r = 2 (the middle level, tau_1) and r = 4 (the
+    coarse level, tau_2; every r = 2 sample is kept one time in eight so both
+    levels weigh alike).  Evaluation, three more seeds: the 3-level slab map
+    (level 0 the central slab) started from the box-filtered field runs
+    T / 4 coarsest steps with and without the network on levels 1 and 2; the
+    judge is the plain fine run of the same seed, box-filtered to each level.
+    Reported per seed: velocity L2 over the voxels of levels 1 and 2
+    (volume-weighted), and the mean gain with its spread (sample standard
+    deviation).  tau0 0.504 puts the coarse levels (tau_2 = 0.501) where they
+    are under-resolved and under-damped, the regime an eddy-viscosity
+    correction can help (at 0.52 they are over-damped already)."""
     t0 = time.time()
-    for seed in (11, 12):
+    taus = [0.5 + (tau0 - 0.5) / 2 ** l for l in range(3)]
+    feats, targs = [], []
+    for seed in train_seeds:
         rho, u = wl.turbulence(N, seed=seed, u_rms=urms, kmax=kmax)
-        g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau_f, periodic=(1, 1, 1)))
+        g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau0, periodic=(1, 1, 1)))
         lbm.lbm_init_equilibrium(g, 0, rho, u)
+        del rho, u
         for _ in range(T // 16):
             lbm.lbm_step(g, 16)
-            F = torch.empty((nc, 16), dtype=torch.float32, device="cuda")
-            Y = torch.empty(nc, dtype=torch.float32, device="cuda")
-            lbm.lbm_closure_dataset(g, r, tau_c, F, Y)
-            feats.append(F)
-            targs.append(Y)
+            for r, lv, keep in ((2, 1, 8), (4, 2, 1)):
+                nc = (N // r) ** 3
+                F = torch.empty((nc, 16), dtype=torch.float32, device="cuda")
+                Y = torch.empty(nc, dtype=torch.float32, device="cuda")
+                lbm.lbm_closure_dataset(g, r, taus[lv], F, Y)
+                feats.append(F[::keep].contiguous())
+                targs.append(Y[::keep].contiguous())
         lbm.lbm_grid_destroy(g)
     X = torch.cat(feats).contiguous()
     Y = torch.cat(targs).contiguous()
+    del feats, targs
     rng = np.random.default_rng(0)
     th0 = np.concatenate([rng.standard_normal(64 * 16) * np.sqrt(2 / 16), np.zeros(64),
                           rng.standard_normal(64 * 64) * np.sqrt(2 / 64), np.zeros(64),
                           rng.standard_normal(64) * np.sqrt(1 / 64), np.zeros(1)])
     th = torch.from_numpy(th0.astype(np.float32)).cuda()
-    loss = lbm.lbm_closure_train(X, Y, 4000, 4096, 1e-3, 1, th)
+    t_train = time.time()
+    loss = lbm.lbm_closure_train(X, Y, train_steps, 4096, 1e-3, 1, th)
+    torch.cuda.synchronize()
+    t_train = time.time() - t_train
+    n_samples = int(Y.numel())
+    del X, Y
     theta = th.cpu().numpy()
-    rho0, u0 = wl.turbulence(N, seed=23, u_rms=urms, kmax=kmax)
-    g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau_f, periodic=(1, 1, 1)))
-    lbm.lbm_init_equilibrium(g, 0, rho0, u0)
-    lbm.lbm_step(g, T)
-    _, uf = lbm.lbm_get_moments(g, 0)
-    lbm.lbm_grid_destroy(g)
-    ub = box(uf)
-    lmap = np.full((N // 32,) * 3, 2, np.uint8)
-    errs = {}
-    for closure in (0, 1):
-        gc = lbm.lbm_grid_create_multires((N,) * 3, 3, lmap,
-                                          lbm.physics(tau_f, periodic=(1, 1, 1), closure=closure))
-        if closure:
-            lbm.lbm_closure_load(gc, theta)
-        lbm.lbm_init_equilibrium(gc, 2, box(rho0), box(u0))
-        lbm.lbm_step(gc, T // r)
-        _, uc = lbm.lbm_get_moments(gc, 2)
-        lbm.lbm_grid_destroy(gc)
-        errs[closure] = float(np.sqrt(((uc - ub) ** 2).sum() / (ub ** 2).sum()))
-    return {"case": f"decaying turbulence, fine {N}^3 tau {tau_f} u_rms {urms} vs the level "
-                    f"{r}x coarser (tau {tau_c}) after {T} fine steps",
-            "training_samples": int(Y.numel()), "final_loss": float(f"{loss:.4e}"),
-            "velocity_l2_plain": round(errs[0], 5), "velocity_l2_closure": round(errs[1], 5),
-            "gain_pct": round(100 * (1 - errs[1] / errs[0]), 2),
-            "seconds": round(time.time() - t0, 1)}
+    lmap = wl.multires_slab_map(N, 3)
+    rows = []
+    for seed in eval_seeds:
+        rho0, u0 = wl.turbulence(N, seed=seed, u_rms=urms, kmax=kmax)
+        g = lbm.lbm_grid_create_dense((N,) * 3, lbm.physics(tau0, periodic=(1, 1, 1)))
+        lbm.lbm_init_equilibrium(g, 0, rho0, u0)
+        lbm.lbm_step(g, T)
+        _, uf = lbm.lbm_get_moments(g, 0)
+        lbm.lbm_grid_destroy(g)
+        fields = wl.level_fields(rho0, u0, 3)
+        judge = [None] + [wl.box_mean(uf, 2 ** lv) for lv in (1, 2)]
+        del rho0, u0, uf
+        errs = {}
+        for closure in (0, 1):
+            gc = lbm.lbm_grid_create_multires((N,) * 3, 3, lmap, lbm.physics(
+                tau0, periodic=(1, 1, 1), closure=closure))
+            if closure:
+                lbm.lbm_closure_load(gc, theta)
+            for lv, (r_, v_) in enumerate(fields):
+                lbm.lbm_init_equilibrium(gc, lv, r_, v_)
+            lbm.lbm_step(gc, T // 4)
+            num = den = 0.0
+            for lv in (1, 2):
+                _, uc = lbm.lbm_get_moments(gc, lv)
+                m = np.isfinite(uc[0])
+                ub = judge[lv]
+                num += 8.0 ** lv * float(((uc[:, m] - ub[:, m]) ** 2).sum())
+                den += 8.0 ** lv * float((ub[:, m] ** 2).sum())
+            lbm.lbm_grid_destroy(gc)
+            errs[closure] = float(np.sqrt(num / den))
+        rows.append({"seed": seed, "velocity_l2_plain": round(errs[0], 5),
+                     "velocity_l2_closure": round(errs[1], 5),
+                     "gain_pct": round(100 * (1 - errs[1] / errs[0]), 3)})
+    gains = np.array([r["gain_pct"] for r in rows])
+    return {"case": f"decaying turbulence, {N}^3 finest box, 3-level slab map, tau_0 {tau0}, "
+                    f"u_rms {urms}, kmax {kmax}; levels 1-2 after {T // 4} coarsest steps vs the "
+                    f"plain {N}^3 run box-filtered",
+            "training_samples": n_samples, "train_steps": train_steps,
+            "train_seconds": round(t_train, 2), "final_loss": float(f"{loss:.4e}"),
+            "per_seed": rows, "gain_pct_mean": round(float(gains.mean()), 3),
+            "gain_pct_std": round(float(gains.std(ddof=1)), 3) if len(gains) > 1 else None,
+            "seconds": round(time.time() - t0, 1), "theta": theta}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -420,6 +638,7 @@ def run_ours(args, rank, world, local_rank):
     variant, variant_ms = lbm.lbm_autotune(g, 20) if args.variant == "auto" else (
         {"vec16": 0, "scalar": 1, "vec8": 2, "vec4": 3}[args.variant], None)
     lbm.lbm_set_variant(g, variant)
+    acc = Accuracy(lbm, wl)
 
     def barrier():
         if dist is not None:
@@ -492,7 +711,7 @@ def run_ours(args, rank, world, local_rank):
             gv = lbm.lbm_grid_create_dense(dims, lbm.physics(tau, **kw), stream=stream)
             lbm.lbm_set_boundary(gv, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
             lbm.lbm_init_equilibrium(gv, 0, None, None)
-            lbm.lbm_autotune(gv, 20)
+            gv_variant, _ = lbm.lbm_autotune(gv, 20)
             lbm.lbm_step(gv, 20, stream)
             torch.cuda.synchronize()
             a0 = torch.cuda.Event(enable_timing=True)
@@ -510,7 +729,9 @@ def run_ours(args, rank, world, local_rank):
                               "bytes_per_update": vbpu,
                               ("velocity_l2_vs_f32" if q == 19 else "velocity_l2_vs_d3q19_f32"):
                                   float(f"{l2:.3e}"),
-                              "after_steps": 20 + kv}
+                              "l2_vs_f32_after_steps": 20 + kv}
+            variants[name].update(acc.run(f"cavity48_q{q}", storage=kw["storage"],
+                                          schedule=kw["schedule"], variant=gv_variant))
             lbm.lbm_grid_destroy(gv)
         del rho_d, u_ref, u_var
 
@@ -518,10 +739,15 @@ def run_ours(args, rank, world, local_rank):
     if args.workloads != "none" and rank == 0:
         which = ("sparse", "multires", "batch", "closure") if args.workloads == "all" else tuple(
             args.workloads.split(","))
-        workloads = measure_workloads(torch, lbm, wl, stream, peaks()[0], min(args.steps, 100),
-                                      which, args.batch_cases)
+        theta = None
+        quality = None
         if "closure" in which:
-            workloads["learned_closure_quality"] = closure_quality(torch, lbm, wl)
+            quality = closure_quality(torch, lbm, wl)
+            theta = quality.pop("theta")
+        workloads = measure_workloads(torch, lbm, wl, stream, peaks()[0], min(args.steps, 100),
+                                      which, acc, theta, args.batch_cases)
+        if quality is not None:
+            workloads["learned_closure_quality"] = quality
 
     # end to end through the C ABI with pinned host buffers: init from host
     # (rho, u), K steps, moments back to host
@@ -547,11 +773,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cn, csteps = 64, 200  # about 10 s of the oracle on the host cores
-            cv, cdt, ccores = oracle_cavity_glups(cn, csteps)
-            cpu = {"value": cv, "unit": "GLUPS", "cores": ccores, "kind": "oracle",
-                   "sample": f"{cn}^3 cavity (tau 0.515, lid 0.05), {csteps} steps, numpy FP64, "
-                             f"{cdt:.1f} s"}
+            cpu = cpu_baseline_line()
         line = {
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -570,10 +792,14 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                          "peak_kind": f"{peak_kind} (copy, burst)", "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "bytes_per_update": bpu, "units_per_launch": units,
                          "avg_launch_ms": avg_ms, "kernel_time_share": shares},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(),
+            "accuracy": acc.run("cavity48_q19", storage=args.storage, schedule=args.schedule,
+                                variant=variant),
+            "accuracy_cases": acc.cases_used(),
             "variants": variants,
             "workloads": workloads,
             "e2e": e2e,
@@ -602,7 +828,12 @@ def main():
     ap.add_argument("--workloads", default="all",
                     help="all | none | comma list of sparse,multires,batch,closure "
                          "(turbulence / cavity: one of the two multires workloads)")
+    ap.add_argument("--cpu-sample", nargs=3, type=int, metavar=("N", "STEPS", "WARMUP"),
+                    help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_sample:
+        cpu_sample(*args.cpu_sample)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", 0))

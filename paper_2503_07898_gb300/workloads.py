@@ -182,26 +182,172 @@ def turbulence(n, seed=7898, u_rms=0.03, kmax=None, dims=None):
 
 
 def batch_cases(n_cases=128, seed=7898, lmin=32, lmax=160, max_solid=0.20, tau=(0.52, 0.8),
-                u0=0.02):
+                u0=0.02, max_edge=None):
     """Serving-style batch: independent periodic cases, every edge drawn
     uniformly in [lmin, lmax] and rounded to a multiple of 8, even cases dense
     and odd cases 8^3 block-sparse, random solid spheres (or boxes) up to a
     drawn solid fraction in [0, max_solid], tau drawn in `tau`, a 2D
     Taylor-Green start of amplitude u0 (batch_case_fields).  Returns a list
-    of dicts."""
+    of dicts; with max_edge, only the cases whose largest edge is at most
+    max_edge (the same cases, drawn from the same sequence)."""
     rng = np.random.default_rng(seed)
     out = []
     for c in range(n_cases):
         dims = tuple(int(8 * max(1, round(int(rng.integers(lmin, lmax + 1)) / 8))) for _ in range(3))
         frac = float(rng.uniform(0.0, max_solid))
+        tau_c = float(rng.uniform(*tau))
+        if max_edge is not None and max(dims) > max_edge:
+            continue
         nx, ny, nz = dims
         flags = random_obstacles((nz, ny, nx), seed=seed * 1000 + c, solid_fraction=frac,
                                  kind="spheres" if c % 4 < 2 else "boxes")
         out.append({"kind": "dense" if c % 2 == 0 else "sparse", "dims": dims, "flags": flags,
-                    "tau": float(rng.uniform(*tau)), "u0": u0, "solid_fraction": frac})
+                    "tau": tau_c, "u0": u0, "solid_fraction": frac})
     return out
 
 
 def batch_case_fields(case):
     """Initial (rho, u) of a batch case (2D Taylor-Green of amplitude u0)."""
     return taylor_green_2d(0, u0=case["u0"], dims=case["dims"])
+
+
+# ------------------------------------------------- reduced accuracy cases
+# Small cases of the same shape as each benchmark workload (same layout,
+# boundary kinds, relaxation time, start), small enough for the FP64 oracle
+# to run them whole.  The library runs each with a bench line's storage,
+# schedule and kernel variant; the oracle's velocity at the sampled updated
+# voxels is stored once by a script of the oracle package; the comparison
+# gives the line's velocity-L2 error against FP64.
+
+ACC_SAMPLES = 2048  # sampled updated voxels per case (per level)
+
+
+def box_mean(a, r):
+    """Mean over r^3 boxes of the last three axes (coarse-level start of a
+    multi-resolution case: a coarser level takes the mean of its cubes)."""
+    *lead, nz, ny, nx = a.shape
+    return a.reshape(*lead, nz // r, r, ny // r, r, nx // r, r).mean(axis=(-5, -3, -1))
+
+
+def level_fields(rho, u, n_levels):
+    """Per-level (rho, u) of a multi-resolution start: level l is the mean of
+    the finest field over 2^l cubes."""
+    out = [(rho, u)]
+    for _ in range(1, n_levels):
+        rho, u = box_mean(rho, 2), box_mean(u, 2)
+        out.append((rho, u))
+    return out
+
+
+def sample_voxels(mask, n=ACC_SAMPLES, seed=0):
+    """Sorted flat indices (x fastest) of up to n voxels drawn without
+    replacement from the True entries of mask."""
+    idx = np.flatnonzero(np.asarray(mask).ravel())
+    if idx.size <= n:
+        return idx
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(idx, size=n, replace=False))
+
+
+def closure_test_network(seed=2025, out_scale=0.02):
+    """A fixed 16-64-64-1 network (flat FP32 parameters, the library's order
+    W1, b1, W2, b2, W3, b3) whose output varies by ~out_scale over the
+    features of a turbulent state: He-initialised layers, the first layer's
+    columns scaled by the inverse of each feature's typical magnitude
+    (rho - 1 ~ 1e-3, u ~ 3e-2, Pi^neq / (rho c_s^2) ~ 1e-2, its norm and
+    trace ~ 1e-2, third moments ~ 1e-3, tau ~ 0.5)."""
+    rng = np.random.default_rng(seed)
+    typ = np.array([1e-3, 3e-2, 3e-2, 3e-2] + [1e-2] * 6 + [1e-2, 1e-2] + [1e-3] * 3 + [0.5])
+    w1 = rng.standard_normal((64, 16)) * np.sqrt(2 / 16) / typ
+    return np.concatenate([w1.ravel(), 0.1 * rng.standard_normal(64),
+                           rng.standard_normal(64 * 64) * np.sqrt(2 / 64), np.zeros(64),
+                           rng.standard_normal(64) * np.sqrt(1 / 64) * out_scale,
+                           np.zeros(1)]).astype(np.float32)
+
+
+def accuracy_cases():
+    """Reduced case of every benchmark workload, by name.  Each dict holds
+    kind ('dense', 'sparse', 'multires', 'batch'), the inputs both sides
+    need (flags and boundary values, level map, start fields per level,
+    relaxation time, periodic axes, lattice, closure weights, number of
+    steps: coarsest steps on multi-resolution grids) and the sampled voxels
+    per level (or per batch case)."""
+    cases = {}
+    for q in (19, 27):
+        flags, bc = cavity(48)
+        n = 48
+        cases[f"cavity48_q{q}"] = dict(
+            kind="dense", q=q, dims=(n, n, n), flags=flags, bc=bc, tau=0.515,
+            periodic=(0, 0, 0), steps=100,
+            fields=[(np.ones((n, n, n)), np.zeros((3, n, n, n)))],
+            what="48^3 lid-driven cavity (the 256^3 workload's boundaries, tau, lid and rest start), 100 steps")
+        flags, bc = sphere_channel(dims=(76, 44, 44), radius_channel=19, sphere_center_x=22,
+                                   sphere_radius=8, u_in=0.04)
+        t = flags & 7
+        upd = (t == FLUID) | (t == VELOCITY) | (t == PRESSURE)
+        cases[f"sphere_small_q{q}"] = dict(
+            kind="sparse", q=q, dims=(76, 44, 44), flags=flags, bc=bc, tau=0.52,
+            periodic=(0, 0, 0), steps=100,
+            fields=[(np.ones(flags.shape), np.zeros((3,) + flags.shape))],
+            what="76x44x44 sphere channel, 8^3 blocks (the 512x256x256 workload's inlet, outlet, "
+                 "sphere, tau and rest start), 100 steps")
+        lmap = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
+        rho, u = turbulence(0, seed=7898, u_rms=0.03, dims=(32, 32, 128))
+        cases[f"turb3_q{q}"] = dict(
+            kind="multires", q=q, dims=(32, 32, 128), n_levels=3, level_map=lmap, flags=None,
+            bc=None, tau=0.52, periodic=(1, 1, 1), steps=25, fields=level_fields(rho, u, 3),
+            what="3-level periodic map coarse-middle-fine-middle (32x32x128 finest box; the "
+                 "256^3 slab map's level jumps, tau_0 and k^-5/3 start), 25 coarsest steps")
+    c = dict(cases["turb3_q19"])
+    c["theta"] = closure_test_network()
+    c["what"] = c["what"] + ", learned closure on levels 1 and 2 (a fixed test network)"
+    cases["turb3_closure"] = c
+    n = 160
+    flags, bc = cavity(n)
+    rho, u = np.ones((n, n, n)), np.zeros((3, n, n, n))
+    cases["cavity3_160"] = dict(
+        kind="multires", q=19, dims=(n, n, n), n_levels=3,
+        level_map=multires_cavity_map(n, 3, (1, 1)), flags=flags, bc=bc, tau=0.52,
+        periodic=(0, 0, 0), steps=4, fields=level_fields(rho, u, 3),
+        what="160^3 3-level lid-driven cavity (the smallest the shell rule allows; the 384^3 "
+             "workload's walls, lid, tau_0 and rest start), 4 coarsest steps")
+    lmap4 = np.array([3, 2, 1, 0, 1, 2], np.uint8).reshape(6, 1, 1)
+    rho, u = turbulence(0, seed=7898, u_rms=0.03, dims=(64, 64, 384))
+    cases["mr4_small"] = dict(
+        kind="multires", q=19, dims=(64, 64, 384), n_levels=4, level_map=lmap4, flags=None,
+        bc=None, tau=0.52, periodic=(1, 1, 1), steps=2, fields=level_fields(rho, u, 4),
+        what="4-level periodic map 3-2-1-0-1-2 (64x64x384 finest box; the smallest 4-level "
+             "cavity is 448^3), k^-5/3 start, 2 coarsest steps")
+    picked = batch_cases(max_edge=64)
+    cases["batch_small"] = dict(
+        kind="batch", q=19, cases=picked, steps=100, periodic=(1, 1, 1),
+        what="the serving batch's cases with every edge <= 64 (two dense, one 8^3 block-sparse; "
+             "obstacles, their tau and Taylor-Green start), 100 steps")
+    c = dict(cases["batch_small"])
+    c["theta"] = closure_test_network()
+    c["what"] = c["what"] + ", learned closure on every case (a fixed test network)"
+    cases["batch_small_closure"] = c
+    return cases
+
+
+def accuracy_samples(case):
+    """Sampled voxels of a case: a list with one array of flat indices per
+    level (multires), per batch case (batch), or one (dense, sparse)."""
+    if case["kind"] in ("dense", "sparse"):
+        t = case["flags"] & 7
+        return [sample_voxels((t == FLUID) | (t == VELOCITY) | (t == PRESSURE), seed=1)]
+    if case["kind"] == "batch":
+        return [sample_voxels((c["flags"] & 7) == FLUID, seed=2 + k)
+                for k, c in enumerate(case["cases"])]
+    lmap = case["level_map"]
+    nx, ny, nz = case["dims"]
+    cell = nx // lmap.shape[2]
+    out = []
+    for lv in range(case["n_levels"]):
+        r = cell >> lv
+        own = lmap.repeat(r, 0).repeat(r, 1).repeat(r, 2) == lv
+        if lv == 0 and case["flags"] is not None:
+            t = case["flags"] & 7
+            own = own & ((t == FLUID) | (t == VELOCITY) | (t == PRESSURE))
+        out.append(sample_voxels(own, seed=10 + lv))
+    return out
