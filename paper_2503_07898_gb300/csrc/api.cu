@@ -65,6 +65,26 @@ void prof_end(Grid& g, cudaStream_t s, int rec) {
   cudaEventRecord(g.prof_recs[(size_t)rec].b, s);
 }
 
+lbm_status group_fork(Grid& g, cudaStream_t s, cudaStream_t* hi) {
+  if (!g.grp_hi) {
+    int least = 0, greatest = 0;
+    LBM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    LBM_CUDA(cudaStreamCreateWithPriority(&g.grp_hi, cudaStreamNonBlocking, greatest));
+  }
+  if (!g.grp_fork) LBM_CUDA(cudaEventCreateWithFlags(&g.grp_fork, cudaEventDisableTiming));
+  if (!g.grp_join) LBM_CUDA(cudaEventCreateWithFlags(&g.grp_join, cudaEventDisableTiming));
+  LBM_CUDA(cudaEventRecord(g.grp_fork, s));
+  LBM_CUDA(cudaStreamWaitEvent(g.grp_hi, g.grp_fork, 0));
+  *hi = g.grp_hi;
+  return LBM_OK;
+}
+
+lbm_status group_join(Grid& g, cudaStream_t s) {
+  LBM_CUDA(cudaEventRecord(g.grp_join, g.grp_hi));
+  LBM_CUDA(cudaStreamWaitEvent(s, g.grp_join, 0));
+  return LBM_OK;
+}
+
 void prof_clear(Grid& g) {
   for (auto& r : g.prof_recs) {
     cudaEventDestroy(r.a);
@@ -147,6 +167,14 @@ static void free_grid(Grid& g) {
   if (g.mr_out) cudaEventDestroy(g.mr_out);
   g.mr_hi = nullptr;
   g.mr_in = g.mr_out = nullptr;
+  if (g.grp_hi) {
+    cudaStreamSynchronize(g.grp_hi);
+    cudaStreamDestroy(g.grp_hi);
+  }
+  if (g.grp_fork) cudaEventDestroy(g.grp_fork);
+  if (g.grp_join) cudaEventDestroy(g.grp_join);
+  g.grp_hi = nullptr;
+  g.grp_fork = g.grp_join = nullptr;
   if (g.stream_ev) cudaEventDestroy(g.stream_ev);
   g.stream_ev = nullptr;
   for (int l = 0; l < 4; ++l) free_level(g, g.lv[l]);

@@ -259,6 +259,24 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
                    : L.variant == VARIANT_VEC4 ? (V4 >= 2 ? V4 : 0)
                                                : V16;
     const bool vec_ok = vw > 0 && !L.wmask_d && L.nx % vw == 0 && a.vend % plane == 0;
+    // the boundary group (regularized voxels) runs beside the interior
+    // kernel on the grid's high-priority group stream: both read the
+    // previous state and write disjoint voxels
+    const bool fork = L.n_reg > 0 && zc > 0;
+    cudaStream_t sb = s;
+    if (fork) {
+      lbm_status st = group_fork(g, s, &sb);
+      if (st) return st;
+    }
+    if (L.n_reg > 0) {
+      a.bc = L.bc_grp_d;
+      a.list = L.dense_reg_tail ? nullptr : L.reg_list_d;
+      a.v0 = L.n_slots - L.n_reg;
+      a.nlist = L.n_reg;
+      const int pr = prof_begin(g, sb, "dense_boundary", L.n_reg);
+      dense_boundary<S><<<(unsigned)((L.n_reg + 127) / 128), 128, 0, sb>>>(a);
+      prof_end(g, sb, pr);
+    }
     if (zc > 0 && vec_ok) {
       const int pr = prof_begin(g, s, "dense_interior_vec", L.n_updated - L.n_reg);
       const dim3 vb(32, VEC_ROWS), vg((L.nx + 32 * vw - 1) / (32 * vw), (L.ny + VEC_ROWS - 1) / VEC_ROWS, zc);
@@ -282,14 +300,9 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
         dense_interior<S, COLL, int64_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
       prof_end(g, s, pr);
     }
-    if (L.n_reg > 0) {
-      a.bc = L.bc_grp_d;
-      a.list = L.dense_reg_tail ? nullptr : L.reg_list_d;
-      a.v0 = L.n_slots - L.n_reg;
-      a.nlist = L.n_reg;
-      const int pr = prof_begin(g, s, "dense_boundary", L.n_reg);
-      dense_boundary<S><<<(unsigned)((L.n_reg + 127) / 128), 128, 0, s>>>(a);
-      prof_end(g, s, pr);
+    if (fork) {
+      lbm_status st = group_join(g, s);
+      if (st) return st;
     }
   }
   LBM_CUDA(cudaGetLastError());

@@ -128,6 +128,13 @@ struct Grid {
   cudaStream_t mr_hi = nullptr;
   cudaEvent_t mr_in = nullptr, mr_out = nullptr;
 
+  // dense / block-sparse grids: the boundary group's kernel runs on its own
+  // high-priority stream beside the interior kernel (both read the previous
+  // state and write disjoint voxels), forked from and joined back into the
+  // step's stream every step
+  cudaStream_t grp_hi = nullptr;
+  cudaEvent_t grp_fork = nullptr, grp_join = nullptr;
+
   // learned closure (multi-resolution levels >= 1)
   void* closure_d = nullptr;     // ClosureParams on the device
   bool closure_loaded = false;
@@ -140,6 +147,10 @@ struct Grid {
   void* dalloc(size_t bytes, cudaStream_t s);
   void dfree(void* p, cudaStream_t s);
 };
+
+// Fork the boundary-group stream from s (*hi receives it) / join it back.
+lbm_status group_fork(Grid& g, cudaStream_t s, cudaStream_t* hi);
+lbm_status group_join(Grid& g, cudaStream_t s);
 
 // Event pair around one kernel launch when profiling is on (else no-op).
 int prof_begin(Grid& g, cudaStream_t s, const char* name, int64_t units);

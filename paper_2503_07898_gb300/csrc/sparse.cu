@@ -603,31 +603,46 @@ static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
     a.s0 = 0;
     a.s1 = L.n_blocks * E3;
     launch_range<S, E, COLL, MODE_MONOLITHIC>(g, a, s, "sparse_monolithic", L.n_updated);
-  } else if (L.bitmask) {
-    a.bnd_bits = L.bnd_bits_d;
-    a.bc_idx = L.bc_idx_d;
-    a.bc_cmp = L.bc_cmp_d;
-    a.s0 = 0;
-    a.s1 = L.n_blocks * E3;
-    launch_range<S, E, COLL, MODE_BOUNDARY_BM>(g, a, s, "sparse_boundary_bitmask", L.n_upd_b);
-    launch_range<S, E, COLL, MODE_INTERIOR_BM>(g, a, s, "sparse_interior_bitmask",
-                                               L.n_updated - L.n_upd_b);
   } else {
-    a.bc = L.bc_grp_d;
-    a.s0 = 0;
-    a.s1 = L.n_b * E3;
-    launch_range<S, E, COLL, MODE_BOUNDARY>(g, a, s, "sparse_boundary", L.n_upd_b);
-    a.s0 = L.n_b * E3;
-    a.s1 = L.n_blocks * E3;
-    if constexpr (E == 8) {
-      if (L.variant == VARIANT_STAGED) {
-        launch_staged<S, COLL>(g, a, s, "sparse_interior_staged", L.n_updated - L.n_upd_b);
-        LBM_CUDA(cudaGetLastError());
-        L.cur ^= 1;
-        return LBM_OK;
-      }
+    // the two group kernels read the previous state and write disjoint
+    // blocks: the boundary group's runs beside the interior one on the
+    // grid's high-priority group stream
+    const bool fork = L.n_b > 0 && L.n_b < L.n_blocks;
+    cudaStream_t sb = s;
+    if (fork) {
+      lbm_status st = group_fork(g, s, &sb);
+      if (st) return st;
     }
-    launch_range<S, E, COLL, MODE_INTERIOR>(g, a, s, "sparse_interior", L.n_updated - L.n_upd_b);
+    if (L.bitmask) {
+      a.bnd_bits = L.bnd_bits_d;
+      a.bc_idx = L.bc_idx_d;
+      a.bc_cmp = L.bc_cmp_d;
+      a.s0 = 0;
+      a.s1 = L.n_blocks * E3;
+      launch_range<S, E, COLL, MODE_BOUNDARY_BM>(g, a, sb, "sparse_boundary_bitmask", L.n_upd_b);
+      launch_range<S, E, COLL, MODE_INTERIOR_BM>(g, a, s, "sparse_interior_bitmask",
+                                                 L.n_updated - L.n_upd_b);
+    } else {
+      a.bc = L.bc_grp_d;
+      a.s0 = 0;
+      a.s1 = L.n_b * E3;
+      launch_range<S, E, COLL, MODE_BOUNDARY>(g, a, sb, "sparse_boundary", L.n_upd_b);
+      a.s0 = L.n_b * E3;
+      a.s1 = L.n_blocks * E3;
+      bool staged = false;
+      if constexpr (E == 8) {
+        if (L.variant == VARIANT_STAGED) {
+          launch_staged<S, COLL>(g, a, s, "sparse_interior_staged", L.n_updated - L.n_upd_b);
+          staged = true;
+        }
+      }
+      if (!staged)
+        launch_range<S, E, COLL, MODE_INTERIOR>(g, a, s, "sparse_interior", L.n_updated - L.n_upd_b);
+    }
+    if (fork) {
+      lbm_status st = group_join(g, s);
+      if (st) return st;
+    }
   }
   LBM_CUDA(cudaGetLastError());
   L.cur ^= 1;
