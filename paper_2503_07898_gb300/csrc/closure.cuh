@@ -13,10 +13,16 @@
 //   tau.
 //
 // Inference: a warp evaluates the network for its 32 voxels with
-// mma.sync.m16n8k16 (BF16 x BF16 -> FP32): layer 1 is 2 (M) x 8 (N) MMAs on
-// the 32 x 16 feature tile staged in shared memory; its accumulators become
-// the A fragments of layer 2 in registers (2 x 8 x 4 MMAs); layer 3 is a
-// quad-shuffle dot product.  Weights are BF16 in shared memory, biases FP32.
+// mma.sync.m16n8k16 (BF16 x BF16 -> FP32) as two 16-voxel row tiles.  Each
+// layer's bias enters as the MMA's accumulator input, and one
+// cvt.rn.relu.bf16x2 turns two accumulators into the next layer's BF16
+// operand (ReLU, round to nearest even, pack), which by the fragment layout
+// of m16n8k16 is already an A fragment of the next MMA: layer 1 is 2 (M) x 8
+// (N) MMAs on the 32 x 16 feature tile staged in shared memory, layer 2 is
+// 2 x 8 x 4 MMAs from registers, and the output layer is an MMA against a B
+// tile whose one nonzero column holds W3 (2 x 4 MMAs).  Weight fragments
+// come from shared memory by ldmatrix.x4 (BF16 rows of 16-byte multiples);
+// biases stay FP32.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -28,14 +34,16 @@ namespace LBM_LNS {
 constexpr int MLP_IN = 16, MLP_H = 64;
 constexpr int MLP_PARAMS = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;  // 5313
 constexpr float TAU_MIN = 0.5f + 1e-3f;
-constexpr int W1S = 18;  // shared-memory row strides (BF16) chosen against bank conflicts
+// shared-memory row strides (BF16): 16-byte multiples (ldmatrix rows) whose
+// eight rows of a fragment fall on distinct banks
+constexpr int W1S = 24;
 constexpr int W2S = 72;
 constexpr int FSTAGE = 18;
 
 // Device copy of a loaded network (global memory).
 struct ClosureParams {
-  __nv_bfloat16 w1[MLP_H * MLP_IN];
-  __nv_bfloat16 w2[MLP_H * MLP_H];
+  alignas(16) __nv_bfloat16 w1[MLP_H * MLP_IN];
+  alignas(16) __nv_bfloat16 w2[MLP_H * MLP_H];
   float w3[MLP_H];  // BF16-rounded values
   float b1[MLP_H];
   float b2[MLP_H];
@@ -55,11 +63,11 @@ inline void closure_params_from_fp32(const float* th, ClosureParams* p) {
 }
 
 struct ClosureSmem {
-  __nv_bfloat16 w1[MLP_H * W1S];
-  __nv_bfloat16 w2[MLP_H * W2S];
-  float w3[MLP_H];
-  float b1[MLP_H];
-  float b2[MLP_H];
+  alignas(16) __nv_bfloat16 w1[MLP_H * W1S];
+  alignas(16) __nv_bfloat16 w2[MLP_H * W2S];
+  alignas(16) __nv_bfloat16 w3[MLP_H];  // BF16 (the device copy's rounded values)
+  alignas(16) float b1[MLP_H];
+  alignas(16) float b2[MLP_H];
   float b3;
 };
 
@@ -70,13 +78,17 @@ struct ClosureCta {
   __nv_bfloat16 stage[8][32 * FSTAGE];
 };
 
+// Weights into a CTA's shared memory in 16-byte pieces (8 BF16: a W1 row is
+// 2 pieces, a W2 row 8; both padded strides are 16-byte multiples).
 __device__ __forceinline__ void closure_load_smem(ClosureSmem& sm, const ClosureParams* p) {
-  for (int i = threadIdx.x; i < MLP_H * MLP_IN; i += blockDim.x)
-    sm.w1[(i / MLP_IN) * W1S + i % MLP_IN] = p->w1[i];
-  for (int i = threadIdx.x; i < MLP_H * MLP_H; i += blockDim.x)
-    sm.w2[(i / MLP_H) * W2S + i % MLP_H] = p->w2[i];
+  const uint4* w1g = reinterpret_cast<const uint4*>(p->w1);
+  const uint4* w2g = reinterpret_cast<const uint4*>(p->w2);
+  for (int i = threadIdx.x; i < MLP_H * MLP_IN / 8; i += blockDim.x)
+    *reinterpret_cast<uint4*>(sm.w1 + (i >> 1) * W1S + (i & 1) * 8) = w1g[i];
+  for (int i = threadIdx.x; i < MLP_H * MLP_H / 8; i += blockDim.x)
+    *reinterpret_cast<uint4*>(sm.w2 + (i >> 3) * W2S + (i & 7) * 8) = w2g[i];
   for (int i = threadIdx.x; i < MLP_H; i += blockDim.x) {
-    sm.w3[i] = p->w3[i];
+    sm.w3[i] = __float2bfloat16_rn(p->w3[i]);  // exact: p->w3 holds BF16 values
     sm.b1[i] = p->b1[i];
     sm.b2[i] = p->b2[i];
   }
@@ -134,6 +146,26 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// max(lo, 0) and max(hi, 0) rounded to BF16 (nearest even), packed with lo in
+// the low half.
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// d = a * b + (c0, c1, c0, c1): the accumulator input is a per-column bias
+// (columns 2q and 2q + 1 of the 16 x 8 tile).
+__device__ __forceinline__ void mma_16816_bias(float d[4], const uint32_t a[4], uint32_t b0,
+                                               uint32_t b1, float c0, float c1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1),
+        "f"(c0), "f"(c1));
+}
+
 __device__ __forceinline__ void mma_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
@@ -142,79 +174,93 @@ __device__ __forceinline__ void mma_16816(float d[4], const uint32_t a[4], uint3
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Four 8 x 8 BF16 matrices from shared memory; lane l gives the address of
+// row l % 8 of matrix l / 8 and receives, of matrix i, row l / 4 and columns
+// 2 (l % 4), 2 (l % 4) + 1 in r[i].  On a weight matrix stored [unit][input]
+// that is the B fragment of m16n8k16 (units n = l / 4, inputs k = 2 (l % 4)).
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const __nv_bfloat16* row) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((uint32_t)__cvta_generic_to_shared(row)));
+}
+
 // Network output for the calling lane's voxel; every lane of the warp must
 // call it (warp-collective).  stage: this warp's 32 x FSTAGE BF16 scratch.
+// The two 16-voxel row tiles run one after the other, so only one tile's
+// activations are live at a time (the weight fragments are read twice).
 __device__ __forceinline__ float mlp_bf16_warp(const float x[MLP_IN], const ClosureSmem& P,
                                                __nv_bfloat16* stage) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int lr = lane & 7, lm = lane >> 3;  // ldmatrix: row within, and index of, its matrix
 #pragma unroll
   for (int k = 0; k < MLP_IN; k += 2)
     *reinterpret_cast<uint32_t*>(stage + lane * FSTAGE + k) = pack_bf16(x[k], x[k + 1]);
   __syncwarp();
-  uint32_t a2[2][4][4];
-#pragma unroll
+  // column 0 of row r of a tile sits in lane 4 (r % 8), register 0 (r < 8)
+  // or 2 (r >= 8); voxel (lane) L is row L % 16 of tile L / 16
+  const int src = (lane & 7) * 4, my_mt = lane >> 4, my_hi = (lane >> 3) & 1;
+  float out = 0.f;
+#pragma unroll 1
   for (int mt = 0; mt < 2; ++mt) {
+    // layer 1: A = the tile's 16 x 16 features, B = W1 (64 units)
+    uint32_t a1[4];
     const __nv_bfloat16* r0 = stage + (16 * mt + g) * FSTAGE;
     const __nv_bfloat16* r1 = stage + (16 * mt + g + 8) * FSTAGE;
-    uint32_t a[4];
-    a[0] = *reinterpret_cast<const uint32_t*>(r0 + 2 * q);
-    a[1] = *reinterpret_cast<const uint32_t*>(r1 + 2 * q);
-    a[2] = *reinterpret_cast<const uint32_t*>(r0 + 2 * q + 8);
-    a[3] = *reinterpret_cast<const uint32_t*>(r1 + 2 * q + 8);
+    a1[0] = *reinterpret_cast<const uint32_t*>(r0 + 2 * q);
+    a1[1] = *reinterpret_cast<const uint32_t*>(r1 + 2 * q);
+    a1[2] = *reinterpret_cast<const uint32_t*>(r0 + 2 * q + 8);
+    a1[3] = *reinterpret_cast<const uint32_t*>(r1 + 2 * q + 8);
+    // a2[ks]: layer-2 A fragments (hidden units 16 ks .. 16 ks + 15)
+    uint32_t a2[4][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int n = 8 * nt + g;
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(P.w1 + n * W1S + 2 * q);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(P.w1 + n * W1S + 2 * q + 8);
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_16816(d, a, b0, b1);
-      const int c0 = 8 * nt + 2 * q;
-      const float bb0 = P.b1[c0], bb1 = P.b1[c0 + 1];
-      a2[mt][nt >> 1][(nt & 1) * 2 + 0] = pack_bf16(fmaxf(d[0] + bb0, 0.f), fmaxf(d[1] + bb1, 0.f));
-      a2[mt][nt >> 1][(nt & 1) * 2 + 1] = pack_bf16(fmaxf(d[2] + bb0, 0.f), fmaxf(d[3] + bb1, 0.f));
+    for (int np = 0; np < 4; ++np) {  // unit tiles 2 np and 2 np + 1
+      uint32_t b[4];
+      // matrices: (tile 2np, inputs 0-7), (2np, 8-15), (2np+1, 0-7), (2np+1, 8-15)
+      ldmatrix_x4(b, P.w1 + (16 * np + 8 * (lm >> 1) + lr) * W1S + 8 * (lm & 1));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2 bb = *reinterpret_cast<const float2*>(P.b1 + 8 * (2 * np + h) + 2 * q);
+        float d[4];
+        mma_16816_bias(d, a1, b[2 * h], b[2 * h + 1], bb.x, bb.y);
+        a2[np][2 * h + 0] = pack_relu_bf16(d[0], d[1]);
+        a2[np][2 * h + 1] = pack_relu_bf16(d[2], d[3]);
+      }
     }
+    // layer 2 by pairs of unit tiles; each pair completes one k-step of the
+    // output layer, which runs right away (y = h2 . W3 + b3 in column 0)
+    float y[4] = {P.b3, P.b3, P.b3, P.b3};
+#pragma unroll 1
+    for (int np = 0; np < 4; ++np) {
+      uint32_t a3[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int nt = 2 * np + h;
+        const float2 bb = *reinterpret_cast<const float2*>(P.b2 + 8 * nt + 2 * q);
+        float acc[4];
+#pragma unroll
+        for (int kp = 0; kp < 2; ++kp) {  // input k-steps 2 kp and 2 kp + 1
+          uint32_t b[4];
+          // matrices: (k-step 2kp, half 0), (2kp, 1), (2kp+1, 0), (2kp+1, 1)
+          ldmatrix_x4(b, P.w2 + (8 * nt + lr) * W2S + 32 * kp + 8 * lm);
+          if (kp == 0) mma_16816_bias(acc, a2[0], b[0], b[1], bb.x, bb.y);
+          else mma_16816(acc, a2[2], b[0], b[1]);
+          mma_16816(acc, a2[2 * kp + 1], b[2], b[3]);
+        }
+        a3[2 * h + 0] = pack_relu_bf16(acc[0], acc[1]);
+        a3[2 * h + 1] = pack_relu_bf16(acc[2], acc[3]);
+      }
+      // output layer, k-step np: B column 0 = W3[16 np .. 16 np + 15], the
+      // other seven columns zero
+      const uint32_t w0 = g == 0 ? *reinterpret_cast<const uint32_t*>(P.w3 + 16 * np + 2 * q) : 0u;
+      const uint32_t w1 = g == 0 ? *reinterpret_cast<const uint32_t*>(P.w3 + 16 * np + 2 * q + 8) : 0u;
+      mma_16816(y, a3, w0, w1);
+    }
+    const float v0 = __shfl_sync(0xffffffffu, y[0], src);
+    const float v2 = __shfl_sync(0xffffffffu, y[2], src);
+    if (my_mt == mt) out = my_hi ? v2 : v0;
   }
   __syncwarp();
-  float y[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int n = 8 * nt + g;
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(P.w2 + n * W2S + 16 * ks + 2 * q);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(P.w2 + n * W2S + 16 * ks + 2 * q + 8);
-      mma_16816(acc[0], a2[0][ks], b0, b1);
-      mma_16816(acc[1], a2[1][ks], b0, b1);
-    }
-    const int c0 = 8 * nt + 2 * q;
-    const float bb0 = P.b2[c0], bb1 = P.b2[c0 + 1], w0 = P.w3[c0], w1 = P.w3[c0 + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      // layer-2 activations are rounded to BF16 like every layer input
-      const float h0 = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[mt][0] + bb0, 0.f)));
-      const float h1 = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[mt][1] + bb1, 0.f)));
-      const float h2 = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[mt][2] + bb0, 0.f)));
-      const float h3 = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[mt][3] + bb1, 0.f)));
-      y[mt][0] += h0 * w0 + h1 * w1;
-      y[mt][1] += h2 * w0 + h3 * w1;
-    }
-  }
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      y[mt][h] += __shfl_xor_sync(0xffffffffu, y[mt][h], 1);
-      y[mt][h] += __shfl_xor_sync(0xffffffffu, y[mt][h], 2);
-    }
-  const int r = lane & 15, src = (r & 7) * 4;
-  const float v00 = __shfl_sync(0xffffffffu, y[0][0], src);
-  const float v01 = __shfl_sync(0xffffffffu, y[0][1], src);
-  const float v10 = __shfl_sync(0xffffffffu, y[1][0], src);
-  const float v11 = __shfl_sync(0xffffffffu, y[1][1], src);
-  const int mtl = lane >> 4, hl = r >> 3;
-  const float out = mtl == 0 ? (hl ? v01 : v00) : (hl ? v11 : v10);
-  return out + P.b3;
+  return out;
 }
 
 }  // namespace LBM_LNS
