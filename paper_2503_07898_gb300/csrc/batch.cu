@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
     T* __restrict__ fout = (T*)C.buf[in ^ 1];
     float g[Q];
     bool act;
+    bool inb = true;  // a voxel of the case (dense: the last item's tail lies past it)
     int64_t obase;  // output index of population 0; population I adds I * ostride
     int ostride;
     if (C.kind == 0) {
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
       z += k;
       const int v = x + C.nx * (y + C.ny * z);
       uint32_t wm = 0u;
-      act = z < C.nz;
+      act = inb = z < C.nz;
       if (act && C.wmask) {
         wm = C.wmask[v];
         act = !(wm & (WM_SKIP | WM_REG));
@@ -105,6 +106,9 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
         } else {
           pull_all<S>(fin, a, x, y, z, v, wm, g);
         }
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state (solid voxel)
       }
     } else {
       const int b = (int)(t >> 1);
@@ -115,14 +119,20 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
       act = !(wm & WM_SKIP);
       obase = (int64_t)b * (Q * 512) + l;
       ostride = 512;
-      if (act) sparse_pull_voxel<S, 8>(fin, C.nbr + (int64_t)b * 27, wm, b, l, walls, g);
+      if (act) {
+        sparse_pull_voxel<S, 8>(fin, C.nbr + (int64_t)b * 27, wm, b, l, walls, g);
+      } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state (solid voxel)
+      }
     }
     float omega = C.omega;
     if constexpr (CLOSURE) {
       if (C.closure) {  // uniform per item: every lane of every warp takes part
-        if (!act) {
+        // a lane without a voxel (past the case's end) joins with the rest state
+        if (!inb) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state, finite features
+          for (int i = 0; i < Q; ++i) g[i] = 0.f;
         }
         ClosureCta* sm = reinterpret_cast<ClosureCta*>(batch_dyn_smem);
         float x[MLP_IN];
@@ -131,7 +141,11 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
         omega = 1.f / fmaxf(C.tau + dtau, TAU_MIN);
       }
     }
-    if (act) {
+    if (inb) {
+      // a voxel that is not updated (solid) carries the rest state (g = 0)
+      // through the collision, which keeps it, and stores it: batch cases
+      // have no other writer, and whole-sector stores spare the DRAM read
+      // that completes a partly written sector (ECC memory)
       collide<COLL>(g, omega);
       // one base pointer; the population stride is a constant for sparse
       // items (512) and a 32-bit value for dense ones
