@@ -373,7 +373,7 @@ __device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, uin
 constexpr uint64_t STAGED_DRAIN_NS = 1000000000ull;
 
 // One voxel (slot) of the group the mode selects.
-template <int S, int E, int COLL, int MODE>
+template <int S, int E, int COLL, int MODE, class IDX = int64_t>
 __device__ __forceinline__ void sparse_update(const SparseArgs& a, int64_t slot) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E;
@@ -394,7 +394,7 @@ __device__ __forceinline__ void sparse_update(const SparseArgs& a, int64_t slot)
   }
   const T* __restrict__ fin = (const T*)a.fin;
   float g[Q];
-  sparse_pull_voxel<S, E>(fin, a.nbr + b * 27, wm, b, l, walls, g);
+  sparse_pull_voxel<S, E, IDX>(fin, a.nbr + b * 27, wm, b, l, walls, g);
   if constexpr (LEAN) {
     collide<COLL>(g, a.omega);
   } else {
@@ -408,16 +408,17 @@ __device__ __forceinline__ void sparse_update(const SparseArgs& a, int64_t slot)
     }
   }
   T* __restrict__ fout = (T*)a.fout;
+  const IDX o = (IDX)b * (IDX)(Q * E3) + (IDX)l;
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
-    fout[(b * Q + I) * E3 + l] = Codec<S>::template store<I>(g[I]);
+    fout[o + (IDX)(I * E3)] = Codec<S>::template store<I>(g[I]);
   });
 }
 
 // BOUNDARY_BM with 8^3 blocks takes one block per CTA (two voxels per
 // thread): the launch over every block, most of which leave at once on
 // their boundary bit, then has half as many CTAs.
-template <int S, int E, int COLL, int MODE>
+template <int S, int E, int COLL, int MODE, class IDX = int64_t>
 __global__ void __launch_bounds__(SP_THREADS,
                                   (MODE == MODE_INTERIOR || MODE == MODE_INTERIOR_BM) ? (Q == 27 ? 3 : (S == S_F32 ? 4 : 5)) : 1)
     sparse_kernel(SparseArgs a) {
@@ -425,8 +426,8 @@ __global__ void __launch_bounds__(SP_THREADS,
   if constexpr (MODE == MODE_BOUNDARY_BM && E3 == 2 * SP_THREADS) {
     const int64_t b = blockIdx.x;
     if (!((a.bnd_bits[b >> 5] >> (b & 31)) & 1u)) return;  // uniform per CTA
-    sparse_update<S, E, COLL, MODE>(a, b * E3 + threadIdx.x);
-    sparse_update<S, E, COLL, MODE>(a, b * E3 + SP_THREADS + threadIdx.x);
+    sparse_update<S, E, COLL, MODE, IDX>(a, b * E3 + threadIdx.x);
+    sparse_update<S, E, COLL, MODE, IDX>(a, b * E3 + SP_THREADS + threadIdx.x);
   } else {
     int64_t slot;
     if constexpr (MODE == MODE_REG_LIST)
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(SP_THREADS,
     else
       slot = a.s0 + (int64_t)blockIdx.x * SP_THREADS + threadIdx.x;
     if (slot >= a.s1) return;
-    sparse_update<S, E, COLL, MODE>(a, slot);
+    sparse_update<S, E, COLL, MODE, IDX>(a, slot);
   }
 }
 
@@ -575,17 +576,26 @@ static void reg_list_t(Grid& g, Level& L, const void* fin, void* fout, float ome
   prof_end(g, s, pr);
 }
 
+// i32: the level's Q E^3 n_blocks population elements fit in 31 bits, so the
+// lean kernel indexes with 32-bit offsets (fewer integer instructions per
+// pull); the other modes keep 64-bit indexing.
 template <int S, int E, int COLL, int MODE>
-static void launch_range(Grid& g, SparseArgs a, cudaStream_t s, const char* name, int64_t units) {
+static void launch_range(Grid& g, SparseArgs a, cudaStream_t s, const char* name, int64_t units,
+                         bool i32 = false) {
   if (a.s1 <= a.s0) return;
   constexpr int64_t E3 = (int64_t)E * E * E;
   const unsigned nb = (MODE == MODE_BOUNDARY_BM && E3 == 2 * SP_THREADS)
                           ? (unsigned)((a.s1 - a.s0) / E3)  // one CTA per block
                           : (unsigned)((a.s1 - a.s0 + SP_THREADS - 1) / SP_THREADS);
   const int pr = prof_begin(g, s, name, units);
-  sparse_kernel<S, E, COLL, MODE><<<nb, SP_THREADS, 0, s>>>(a);
+  if (MODE == MODE_INTERIOR && i32)
+    sparse_kernel<S, E, COLL, MODE, int32_t><<<nb, SP_THREADS, 0, s>>>(a);
+  else
+    sparse_kernel<S, E, COLL, MODE><<<nb, SP_THREADS, 0, s>>>(a);
   prof_end(g, s, pr);
 }
+
+static bool fits_i32(const Level& L, int q) { return (int64_t)q * L.n_slots < ((int64_t)1 << 31); }
 
 template <int S, int E, int COLL>
 static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
@@ -637,7 +647,8 @@ static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
         }
       }
       if (!staged)
-        launch_range<S, E, COLL, MODE_INTERIOR>(g, a, s, "sparse_interior", L.n_updated - L.n_upd_b);
+        launch_range<S, E, COLL, MODE_INTERIOR>(g, a, s, "sparse_interior", L.n_updated - L.n_upd_b,
+                                                fits_i32(L, Q));
     }
     if (fork) {
       lbm_status st = group_join(g, s);
@@ -663,7 +674,7 @@ static void uniform_range_t(Grid& g, Level& L, int64_t b0, int64_t b1, const voi
   a.s0 = b0 * 512;
   a.s1 = b1 * 512;
   if (L.variant == VARIANT_STAGED) launch_staged<S, COLL>(g, a, s, name, units);
-  else launch_range<S, 8, COLL, MODE_INTERIOR>(g, a, s, name, units);
+  else launch_range<S, 8, COLL, MODE_INTERIOR>(g, a, s, name, units, fits_i32(L, Q));
 }
 
 lbm_status sparse_reg_blocks(Grid& g, Level& L, const void* fin, void* fout, float omega,

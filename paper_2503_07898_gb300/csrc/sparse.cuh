@@ -23,61 +23,66 @@ namespace LBM_LNS {
 // velocities, the one at the corner of three (six or seven in all) — are
 // looked up once, and the source coordinate wrapped into the source block
 // is one of three precomputed values per axis.  Each pull then costs a few
-// selects and one 32 x 32 -> 64-bit multiply-add.
-template <int S, int E, bool WALLS>
+// selects among the neighbours' element offsets (formed once per voxel), one
+// add and the load.  IDX is int32_t when the level's Q E^3 n_blocks elements
+// fit in 31 bits (the kernels choose), else int64_t.
+template <int S, int E, bool WALLS, class IDX = int64_t>
 __device__ __forceinline__ void sparse_pull_voxel_t(const typename Codec<S>::T* __restrict__ fin,
                                                     const int32_t* nbr27, uint32_t wm, int b,
                                                     int l, float g[Q]) {
   using T = typename Codec<S>::T;
   constexpr int E3 = E * E * E, M = E - 1;
+  constexpr IDX QE3 = (IDX)Q * E3;
   const int lx = l & M, ly = (l / E) & M, lz = l / (E * E);
   const int ex = lx == 0 ? -1 : (lx == M ? 1 : 0);
   const int ey = ly == 0 ? -1 : (ly == M ? 1 : 0);
   const int ez = lz == 0 ? -1 : (lz == M ? 1 : 0);
-  const int nX = __ldg(nbr27 + 13 + ex), nY = __ldg(nbr27 + 13 + 3 * ey);
-  const int nZ = __ldg(nbr27 + 13 + 9 * ez);
-  const int nXY = __ldg(nbr27 + 13 + ex + 3 * ey), nXZ = __ldg(nbr27 + 13 + ex + 9 * ez);
-  const int nYZ = __ldg(nbr27 + 13 + 3 * ey + 9 * ez);
-  const int nXYZ = Q == 27 ? __ldg(nbr27 + 13 + ex + 3 * ey + 9 * ez) : b;
+  // element offsets of the blocks a pull can enter (a missing neighbour
+  // gives a negative offset that only a bounced-back pull would name, and
+  // such a pull reads the voxel itself instead)
+  const IDX oS = (IDX)b * QE3;
+  const IDX oX = (IDX)__ldg(nbr27 + 13 + ex) * QE3, oY = (IDX)__ldg(nbr27 + 13 + 3 * ey) * QE3;
+  const IDX oZ = (IDX)__ldg(nbr27 + 13 + 9 * ez) * QE3;
+  const IDX oXY = (IDX)__ldg(nbr27 + 13 + ex + 3 * ey) * QE3;
+  const IDX oXZ = (IDX)__ldg(nbr27 + 13 + ex + 9 * ez) * QE3;
+  const IDX oYZ = (IDX)__ldg(nbr27 + 13 + 3 * ey + 9 * ez) * QE3;
+  const IDX oXYZ = Q == 27 ? (IDX)__ldg(nbr27 + 13 + ex + 3 * ey + 9 * ez) * QE3 : oS;
   // source coordinate inside its block for c = +1, -1 (pre-scaled by the
   // axis stride for y and z)
   const int xp = (lx - 1) & M, xn = (lx + 1) & M;
   const int yp = ((ly - 1) & M) * E, yn = ((ly + 1) & M) * E, y0 = ly * E;
   const int zp = ((lz - 1) & M) * E * E, zn = ((lz + 1) & M) * E * E, z0 = lz * E * E;
-  const T* __restrict__ self = fin + (int64_t)b * (Q * E3) + l;
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     constexpr int X = cx(I), Y = cy(I), Z = cz(I);
     const bool kx = X != 0 && ex == -X;  // the pull crosses the x face
     const bool ky = Y != 0 && ey == -Y;
     const bool kz = Z != 0 && ez == -Z;
-    int nb = b;
+    IDX o = oS;
     if constexpr (X != 0 && Y != 0 && Z != 0)
-      nb = kz ? (kx ? (ky ? nXYZ : nXZ) : (ky ? nYZ : nZ)) : (kx ? (ky ? nXY : nX) : (ky ? nY : b));
-    else if constexpr (X != 0 && Y != 0) nb = kx ? (ky ? nXY : nX) : (ky ? nY : b);
-    else if constexpr (X != 0 && Z != 0) nb = kx ? (kz ? nXZ : nX) : (kz ? nZ : b);
-    else if constexpr (Y != 0 && Z != 0) nb = ky ? (kz ? nYZ : nY) : (kz ? nZ : b);
-    else if constexpr (X != 0) nb = kx ? nX : b;
-    else if constexpr (Y != 0) nb = ky ? nY : b;
-    else if constexpr (Z != 0) nb = kz ? nZ : b;
+      o = kz ? (kx ? (ky ? oXYZ : oXZ) : (ky ? oYZ : oZ)) : (kx ? (ky ? oXY : oX) : (ky ? oY : oS));
+    else if constexpr (X != 0 && Y != 0) o = kx ? (ky ? oXY : oX) : (ky ? oY : oS);
+    else if constexpr (X != 0 && Z != 0) o = kx ? (kz ? oXZ : oX) : (kz ? oZ : oS);
+    else if constexpr (Y != 0 && Z != 0) o = ky ? (kz ? oYZ : oY) : (kz ? oZ : oS);
+    else if constexpr (X != 0) o = kx ? oX : oS;
+    else if constexpr (Y != 0) o = ky ? oY : oS;
+    else if constexpr (Z != 0) o = kz ? oZ : oS;
     const int ls = (X > 0 ? xp : (X < 0 ? xn : lx)) + (Y > 0 ? yp : (Y < 0 ? yn : y0)) +
                    (Z > 0 ? zp : (Z < 0 ? zn : z0));
-    if constexpr (!WALLS) {
-      g[I] = Codec<S>::template load<I>(fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)]);
-    } else {
-      const bool wall = (wm >> I) & 1u;
-      g[I] = Codec<S>::template load<I>(wall ? self[opp(I) * E3]
-                                             : fin[(int64_t)nb * (Q * E3) + (I * E3 + ls)]);
+    IDX src = o + (IDX)(I * E3 + ls);
+    if constexpr (WALLS) {
+      if ((wm >> I) & 1u) src = oS + (IDX)(opp(I) * E3 + l);
     }
+    g[I] = Codec<S>::template load<I>(fin[src]);
   });
 }
 
-template <int S, int E>
+template <int S, int E, class IDX = int64_t>
 __device__ __forceinline__ void sparse_pull_voxel(const typename Codec<S>::T* __restrict__ fin,
                                                   const int32_t* nbr27, uint32_t wm, int64_t b,
                                                   int l, bool walls, float g[Q]) {
-  if (walls) sparse_pull_voxel_t<S, E, true>(fin, nbr27, wm, (int)b, l, g);
-  else sparse_pull_voxel_t<S, E, false>(fin, nbr27, 0u, (int)b, l, g);
+  if (walls) sparse_pull_voxel_t<S, E, true, IDX>(fin, nbr27, wm, (int)b, l, g);
+  else sparse_pull_voxel_t<S, E, false, IDX>(fin, nbr27, 0u, (int)b, l, g);
 }
 
 }  // namespace LBM_LNS
