@@ -2,8 +2,9 @@
 //
 // Not in the paper (a serving-style use of the same update): a batch holds
 // dense and 8^3 block-sparse grids of different sizes, walls and relaxation
-// times.  Their voxels are cut into work items of 256 voxels (dense: 256
-// consecutive voxel ids; sparse: half a block) listed case after case; one
+// times.  Their voxels are cut into work items of 512 voxels (dense: 512
+// consecutive voxel ids; sparse: one 8^3 block), two per thread, listed case
+// after case; one
 // persistent kernel per step walks the list with a grid-stride loop, so a
 // step over the whole batch is a single launch whatever the number of cases.
 // A sequence of steps is captured once into a CUDA graph and replayed.  The
@@ -41,7 +42,9 @@ struct BatchCase {
   float inv_nx, inv_ny;  // dense: 1 / nx, 1 / ny (voxel decode)
 };
 
-constexpr int BT = 256;  // threads per CTA = voxels per work item
+constexpr int BT = 256;       // threads per CTA
+constexpr int VPT = 2;        // voxels per thread in a work item, taken one after the other
+constexpr int VPI = BT * VPT; // voxels per work item: 512 (dense: consecutive ids; sparse: a block)
 
 template <int S, int COLL, bool CLOSURE>
 __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_step_kernel(const BatchCase* __restrict__ cases,
@@ -61,105 +64,111 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
     const int in = parity ^ C.cur0;
     const T* __restrict__ fin = (const T*)C.buf[in];
     T* __restrict__ fout = (T*)C.buf[in ^ 1];
-    float g[Q];
-    bool act;
-    bool inb = true;  // a voxel of the case (dense: the last item's tail lies past it)
-    int64_t obase;  // output index of population 0; population I adds I * ostride
-    int ostride;
-    if (C.kind == 0) {
-      // case sizes are below 2^31 / 19 voxels (checked at creation): 32-bit
-      // voxel ids and offsets
-      // the item's first voxel, packed x | y << 11 | z << 22; this thread's
-      // voxel follows by carrying across rows and planes with a float
-      // reciprocal (exact: x and y stay below 2^12, so the product's error
-      // is far below the 0.5 / n distance to the next integer)
-      const uint32_t pk = (uint32_t)t;
-      int x = (int)(pk & 2047u) + (int)threadIdx.x, y = (int)((pk >> 11) & 2047u),
-          z = (int)(pk >> 22);
-      int k = (int)(((float)x + 0.5f) * C.inv_nx);
-      x -= k * C.nx;
-      y += k;
-      k = (int)(((float)y + 0.5f) * C.inv_ny);
-      y -= k * C.ny;
-      z += k;
-      const int v = x + C.nx * (y + C.ny * z);
-      uint32_t wm = 0u;
-      act = inb = z < C.nz;
-      if (act && C.wmask) {
-        wm = C.wmask[v];
-        act = !(wm & (WM_SKIP | WM_REG));
-      }
-      obase = v;
-      ostride = (int)C.N;
-      if (act) {
-        DenseArgs a{};
-        a.nx = C.nx;
-        a.ny = C.ny;
-        a.nz = C.nz;
-        a.N = C.N;
-        a.px = C.px;
-        a.py = C.py;
-        a.pz = C.pz;
-        if (lean_row(a, y, z)) {
-          if (wm) pull_row_interior<S, int, true>(fin, a, x, y, z, v, wm, g);
-          else pull_row_interior<S, int, false>(fin, a, x, y, z, v, 0u, g);
-        } else {
-          pull_all<S>(fin, a, x, y, z, v, wm, g);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state (solid voxel)
-      }
-    } else {
-      const int b = (int)(t >> 1);
-      const int l = (int)(t & 1) * BT + threadIdx.x;
-      const bool walls = C.blk_walls[b] != 0;
-      uint32_t wm = 0u;
-      if (walls) wm = C.wmask[(int64_t)b * 512 + l];
-      act = !(wm & WM_SKIP);
-      obase = (int64_t)b * (Q * 512) + l;
-      ostride = 512;
-      if (act) {
-        sparse_pull_voxel<S, 8>(fin, C.nbr + (int64_t)b * 27, wm, b, l, walls, g);
-      } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state (solid voxel)
-      }
-    }
-    float omega = C.omega;
-    if constexpr (CLOSURE) {
-      if (C.closure) {  // uniform per item: every lane of every warp takes part
-        // a lane without a voxel (past the case's end) joins with the rest state
-        if (!inb) {
-#pragma unroll
-          for (int i = 0; i < Q; ++i) g[i] = 0.f;
-        }
-        ClosureCta* sm = reinterpret_cast<ClosureCta*>(batch_dyn_smem);
-        float x[MLP_IN];
-        closure_features(g, C.tau, x);
-        const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
-        omega = 1.f / fmaxf(C.tau + dtau, TAU_MIN);
-      }
-    }
-    if (inb) {
-      // a voxel that is not updated (solid) carries the rest state (g = 0)
-      // through the collision, which keeps it, and stores it: batch cases
-      // have no other writer, and whole-sector stores spare the DRAM read
-      // that completes a partly written sector (ECC memory)
-      collide<COLL>(g, omega);
-      // one base pointer; the population stride is a constant for sparse
-      // items (512) and a 32-bit value for dense ones
-      T* __restrict__ o = fout + obase;
+    // the item's VPT voxels of this thread, one after the other: the item
+    // lookup and the case's descriptor serve them all
+#pragma unroll 1
+    for (int h = 0; h < VPT; ++h) {
+      float g[Q];
+      bool act;
+      bool inb = true;  // a voxel of the case (dense: the last item's tail lies past it)
+      int64_t obase;  // output index of population 0; population I adds I * ostride
+      int ostride;
       if (C.kind == 0) {
-        static_for<Q>([&](auto ic) {
-          constexpr int I = decltype(ic)::value;
-          o[I * ostride] = Codec<S>::template store<I>(g[I]);
-        });
+        // case sizes are below 2^31 / 19 voxels (checked at creation): 32-bit
+        // voxel ids and offsets
+        // the item's first voxel, packed x | y << 11 | z << 22; this thread's
+        // voxel follows by carrying across rows and planes with a float
+        // reciprocal (exact: x and y stay below 2^12, so the product's error
+        // is far below the 0.5 / n distance to the next integer)
+        const uint32_t pk = (uint32_t)t;
+        int x = (int)(pk & 2047u) + h * BT + (int)threadIdx.x, y = (int)((pk >> 11) & 2047u),
+            z = (int)(pk >> 22);
+        int k = (int)(((float)x + 0.5f) * C.inv_nx);
+        x -= k * C.nx;
+        y += k;
+        k = (int)(((float)y + 0.5f) * C.inv_ny);
+        y -= k * C.ny;
+        z += k;
+        const int v = x + C.nx * (y + C.ny * z);
+        uint32_t wm = 0u;
+        act = inb = z < C.nz;
+        if (act && C.wmask) {
+          wm = C.wmask[v];
+          act = !(wm & (WM_SKIP | WM_REG));
+        }
+        obase = v;
+        ostride = (int)C.N;
+        if (act) {
+          DenseArgs a{};
+          a.nx = C.nx;
+          a.ny = C.ny;
+          a.nz = C.nz;
+          a.N = C.N;
+          a.px = C.px;
+          a.py = C.py;
+          a.pz = C.pz;
+          if (lean_row(a, y, z)) {
+            if (wm) pull_row_interior<S, int, true>(fin, a, x, y, z, v, wm, g);
+            else pull_row_interior<S, int, false>(fin, a, x, y, z, v, 0u, g);
+          } else {
+            pull_all<S>(fin, a, x, y, z, v, wm, g);
+          }
+        } else {
+  #pragma unroll
+          for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state (solid voxel)
+        }
       } else {
-        static_for<Q>([&](auto ic) {
-          constexpr int I = decltype(ic)::value;
-          o[I * 512] = Codec<S>::template store<I>(g[I]);
-        });
+        const int b = (int)t;
+        const int l = h * BT + (int)threadIdx.x;
+        const bool walls = C.blk_walls[b] != 0;
+        uint32_t wm = 0u;
+        if (walls) wm = C.wmask[(int64_t)b * 512 + l];
+        act = !(wm & WM_SKIP);
+        obase = (int64_t)b * (Q * 512) + l;
+        ostride = 512;
+        if (act) {
+          // batch cases hold fewer than 2^31 / 19 slots: 32-bit offsets
+          sparse_pull_voxel<S, 8, int32_t>(fin, C.nbr + (int64_t)b * 27, wm, b, l, walls, g);
+        } else {
+  #pragma unroll
+          for (int i = 0; i < Q; ++i) g[i] = 0.f;  // rest state (solid voxel)
+        }
+      }
+      float omega = C.omega;
+      if constexpr (CLOSURE) {
+        if (C.closure) {  // uniform per item: every lane of every warp takes part
+          // a lane without a voxel (past the case's end) joins with the rest state
+          if (!inb) {
+  #pragma unroll
+            for (int i = 0; i < Q; ++i) g[i] = 0.f;
+          }
+          ClosureCta* sm = reinterpret_cast<ClosureCta*>(batch_dyn_smem);
+          float x[MLP_IN];
+          closure_features(g, C.tau, x);
+          const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
+          omega = 1.f / fmaxf(C.tau + dtau, TAU_MIN);
+        }
+      }
+      if (inb) {
+        // a voxel that is not updated (solid) carries the rest state (g = 0)
+        // through the collision, which keeps it, and stores it: batch cases
+        // have no other writer, and whole-sector stores spare the DRAM read
+        // that completes a partly written sector (ECC memory)
+        collide<COLL>(g, omega);
+        // one base pointer; the population stride is a constant for sparse
+        // items (512) and a 32-bit value for dense ones
+        T* __restrict__ o = fout + obase;
+        if (C.kind == 0) {
+          static_for<Q>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            o[I * ostride] = Codec<S>::template store<I>(g[I]);
+          });
+        } else {
+          static_for<Q>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            o[I * 512] = Codec<S>::template store<I>(g[I]);
+          });
+        }
       }
     }
   }
@@ -321,11 +330,11 @@ lbm_status lbm_batch_create(int n_cases, lbm_grid* const* cases, lbm_batch** out
     d.inv_nx = 1.f / (float)L.nx;
     d.inv_ny = 1.f / (float)L.ny;
     b->cases_h.push_back(d);
-    const int64_t items = g.kind == 0 ? (L.n_slots + BT - 1) / BT : L.n_blocks * 2;
+    const int64_t items = g.kind == 0 ? (L.n_slots + VPI - 1) / VPI : L.n_blocks;
     for (int64_t t = 0; t < items; ++t) {
       ic.push_back(c);
       if (g.kind == 0) {  // dense: first voxel of the item, packed
-        const int64_t v0 = t * BT;
+        const int64_t v0 = t * VPI;
         const int64_t x0 = v0 % L.nx, y0 = (v0 / L.nx) % L.ny, z0 = v0 / ((int64_t)L.nx * L.ny);
         il.push_back((int32_t)(uint32_t)(x0 | (y0 << 11) | (z0 << 22)));
       } else {
