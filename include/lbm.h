@@ -433,6 +433,18 @@ typedef struct {
 } lbm_kernel_stat;
 lbm_status lbm_profile(lbm_grid* g, int enable);
 lbm_status lbm_profile_read(lbm_grid* g, lbm_kernel_stat* out, int max, int* n_out);
+/* The same records one by one, in launch order: each launch's kernel name,
+ * start and end in ms after the first recorded launch's start (event times
+ * on the launch's own stream, so launches on the multi-resolution and
+ * boundary-group streams show their overlap) and units.  At most `max`
+ * entries are written; *n_out receives the number of launches recorded. */
+typedef struct {
+  char name[48];
+  double start_ms;
+  double end_ms;
+  int64_t units;
+} lbm_kernel_trace;
+lbm_status lbm_profile_trace(lbm_grid* g, lbm_kernel_trace* out, int max, int* n_out);
 
 /* Thread-local message of the last error on this thread ("" if none). */
 const char* lbm_last_error(void);

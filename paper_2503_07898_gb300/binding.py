@@ -52,6 +52,11 @@ class lbm_info(C.Structure):
                 ("steps_done", C.c_int64), ("lattice", C.c_int)]
 
 
+class lbm_kernel_trace(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("start_ms", C.c_double), ("end_ms", C.c_double),
+                ("units", C.c_int64)]
+
+
 class lbm_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double),
                 ("units", C.c_int64)]
@@ -111,6 +116,7 @@ def load():
         "lbm_batch_closure_load": [vp, vp, C.c_size_t, I],
         "lbm_profile": [vp, I],
         "lbm_profile_read": [vp, P(lbm_kernel_stat), I, P(I)],
+        "lbm_profile_trace": [vp, P(lbm_kernel_trace), I, P(I)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -541,3 +547,12 @@ def lbm_profile_read(grid):
     _check(load().lbm_profile_read(grid.ptr, stats, 32, C.byref(n)), "lbm_profile_read")
     return {stats[k].name.decode(): {"launches": stats[k].launches, "total_ms": stats[k].total_ms,
                                      "units": stats[k].units} for k in range(min(n.value, 32))}
+
+
+def lbm_profile_trace(grid, max_records=100000):
+    """Every recorded launch in order: (name, start_ms, end_ms, units)."""
+    buf = (lbm_kernel_trace * max_records)()
+    n = C.c_int()
+    _check(load().lbm_profile_trace(grid.ptr, buf, max_records, C.byref(n)), "lbm_profile_trace")
+    return [(buf[k].name.decode(), buf[k].start_ms, buf[k].end_ms, buf[k].units)
+            for k in range(min(n.value, max_records))]

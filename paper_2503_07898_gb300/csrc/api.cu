@@ -878,6 +878,28 @@ lbm_status lbm_profile_read(lbm_grid* h, lbm_kernel_stat* out, int max, int* n_o
   return LBM_OK;
 }
 
+lbm_status lbm_profile_trace(lbm_grid* h, lbm_kernel_trace* out, int max, int* n_out) {
+  if (!h || !n_out || (max > 0 && !out)) return fail(LBM_ERR_INVALID, "NULL argument");
+  Grid& g = h->g;
+  LBM_CUDA(cudaStreamSynchronize(g.stream));
+  const int n = (int)g.prof_recs.size();
+  *n_out = n;
+  if (n == 0) return LBM_OK;
+  const cudaEvent_t t0 = g.prof_recs[0].a;
+  for (int k = 0; k < n && k < max; ++k) {
+    const ProfRec& r = g.prof_recs[(size_t)k];
+    std::memset(&out[k], 0, sizeof(out[k]));
+    std::strncpy(out[k].name, g.prof_names[(size_t)r.kernel].c_str(), sizeof(out[k].name) - 1);
+    float a = 0.f, b = 0.f;
+    LBM_CUDA(cudaEventElapsedTime(&a, t0, r.a));
+    LBM_CUDA(cudaEventElapsedTime(&b, t0, r.b));
+    out[k].start_ms = a;
+    out[k].end_ms = b;
+    out[k].units = r.units;
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_conservation(lbm_grid* h, double out[4]) {
   if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
   Grid& g = h->g;
