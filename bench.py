@@ -46,8 +46,8 @@ METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated err
 # 4,070,400 updates per launch) scaled by units to one 256^3 launch
 # (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md; keyed by
 # kernel and storage (the FP16 capture: dense_interior_f16_cavity160_ncu.md).
-NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.351797e+09, "src_sha": "d62c038efe78398d"},
-               ("dense_interior", "f16"): {"bytes_per_launch": 1.118711e+09, "src_sha": "d62c038efe78398d"}}
+NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.342251e+09, "src_sha": "474bb1a56bd9c9a4"},
+               ("dense_interior", "f16"): {"bytes_per_launch": 1.106437e+09, "src_sha": "474bb1a56bd9c9a4"}}
 
 
 def src_hash():
