@@ -385,8 +385,8 @@ lbm_status lbm_closure_load(lbm_grid* g, const float* theta, size_t n);
 /* ------------------------------------------------------------- batching
  * Not in the paper (a serving-style use of the same update): many
  * independent dense and 8^3 block-sparse grids advance together, one
- * persistent kernel launch per step over a work list of 256-voxel items
- * (dense: consecutive voxel ids; sparse: half blocks), the steps of one
+ * persistent kernel launch per step over a work list of 512-voxel items
+ * (dense: consecutive voxel ids; sparse: whole blocks), the steps of one
  * lbm_batch_step call captured once into a CUDA graph and replayed.
  * Cases keep their own state, walls and tau; they must share storage and
  * collision, be D3Q19, have no regularized voxels and fewer than 2^31 / 19
