@@ -46,8 +46,8 @@ METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated err
 # 4,070,400 updates per launch) scaled by units to one 256^3 launch
 # (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md; keyed by
 # kernel and storage (the FP16 capture: dense_interior_f16_cavity160_ncu.md).
-NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.342251e+09, "src_sha": "474bb1a56bd9c9a4"},
-               ("dense_interior", "f16"): {"bytes_per_launch": 1.106437e+09, "src_sha": "474bb1a56bd9c9a4"}}
+NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.343073e+09, "src_sha": "d03b2cafedf1e1c0"},
+               ("dense_interior", "f16"): {"bytes_per_launch": 1.109004e+09, "src_sha": "d03b2cafedf1e1c0"}}
 
 
 def src_hash():
@@ -730,7 +730,7 @@ def run_ours(args, rank, world, local_rank):
             gv = lbm.lbm_grid_create_dense(dims, lbm.physics(tau, **kw), stream=stream)
             lbm.lbm_set_boundary(gv, 0, flags, None, np.array([0.05, 0, 0, 1.0], np.float32))
             lbm.lbm_init_equilibrium(gv, 0, None, None)
-            gv_variant, _ = lbm.lbm_autotune(gv, 20)
+            gv_variant, gv_ms = lbm.lbm_autotune(gv, 20)
             lbm.lbm_step(gv, 20, stream)
             torch.cuda.synchronize()
             a0 = torch.cuda.Event(enable_timing=True)
@@ -748,7 +748,10 @@ def run_ours(args, rank, world, local_rank):
                               "bytes_per_update": vbpu,
                               ("velocity_l2_vs_f32" if q == 19 else "velocity_l2_vs_d3q19_f32"):
                                   float(f"{l2:.3e}"),
-                              "l2_vs_f32_after_steps": 20 + kv}
+                              "l2_vs_f32_after_steps": 20 + kv,
+                              "kernel_variant": lbm.VARIANT_NAMES[gv_variant],
+                              "autotune_ms_per_step": {lbm.VARIANT_NAMES[k]: round(t, 5)
+                                                       for k, t in enumerate(gv_ms) if t > 0}}
             variants[name].update(acc.run(f"cavity48_q{q}", storage=kw["storage"],
                                           schedule=kw["schedule"], variant=gv_variant))
             lbm.lbm_grid_destroy(gv)

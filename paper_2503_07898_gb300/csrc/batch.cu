@@ -96,6 +96,10 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
           wm = C.wmask[v];
           act = !(wm & (WM_SKIP | WM_REG));
         }
+        // one pull form per warp: with a wall bit in any lane, the whole warp
+        // takes the wall-mask form (a lane without bits selects nothing), so
+        // a warp never runs both forms one after the other
+        const bool wmw = __any_sync(0xffffffffu, wm != 0u);
         obase = v;
         ostride = (int)C.N;
         if (act) {
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
           a.py = C.py;
           a.pz = C.pz;
           if (lean_row(a, y, z)) {
-            if (wm) pull_row_interior<S, int, true>(fin, a, x, y, z, v, wm, g);
+            if (wmw) pull_row_interior<S, int, true>(fin, a, x, y, z, v, wm, g);
             else pull_row_interior<S, int, false>(fin, a, x, y, z, v, 0u, g);
           } else {
             pull_all<S>(fin, a, x, y, z, v, wm, g);

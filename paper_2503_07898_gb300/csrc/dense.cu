@@ -24,8 +24,19 @@
 namespace lbm {
 namespace LBM_LNS {
 
+// Per-population base addresses of the interior kernel, passed as kernel
+// parameters: a pull source or a store target is then one multiply-add of a
+// 32-bit (or 64-bit) voxel offset onto a constant-bank base.  in[I] points
+// at population I of the input shifted by -c_x(I) elements, so that the
+// source of voxel v is in[I][v + row offset of (c_y, c_z)]; out[I] at
+// population I of the output.
+struct DensePops {
+  const void* in[Q];
+  void* out[Q];
+};
+
 template <int S, int COLL, class IDX>
-__global__ void __launch_bounds__(256, S == S_F32 ? 4 : 5) dense_interior(DenseArgs a) {
+__global__ void __launch_bounds__(256, S == S_F32 ? 4 : 5) dense_interior(DenseArgs a, DensePops p) {
   using T = typename Codec<S>::T;
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
@@ -39,20 +50,37 @@ __global__ void __launch_bounds__(256, S == S_F32 ? 4 : 5) dense_interior(DenseA
     wm = a.wmask[v];
     if (wm & (WM_SKIP | WM_REG)) return;
   }
-  // warp-uniform choice: a warp holds one (y, z) row
+  // warp-uniform choice: a warp holds one (y, z) row.  16-bit storage, whose
+  // kernel is bound by instruction issue, takes the select-free lean pull
+  // and the per-population bases; FP32, bound by DRAM, keeps one offset
+  // and selects per population (measured 0.2 % faster for D3Q19, 1 % for
+  // D3Q27)
   if (lean_row(a, y, z)) {
-    if (wm) pull_row_interior<S, IDX, true>((const T*)a.fin, a, x, y, z, (IDX)v, wm, g);
-    else pull_row_interior<S, IDX, false>((const T*)a.fin, a, x, y, z, (IDX)v, 0u, g);
+    if constexpr (S == S_F32) {
+      if (wm) pull_row_interior<S, IDX, true>((const T*)a.fin, a, x, y, z, (IDX)v, wm, g);
+      else pull_row_interior<S, IDX, false>((const T*)a.fin, a, x, y, z, (IDX)v, 0u, g);
+    } else {
+      pull_lean<S, IDX>(a, x, y, z, (IDX)v, wm, g, [&](auto ic, IDX o) {
+        return reinterpret_cast<const T*>(p.in[decltype(ic)::value])[o];
+      });
+    }
   } else {
     pull_all<S>((const T*)a.fin, a, x, y, z, v, wm, g);
   }
   collide<COLL>(g, a.omega);
-  T* __restrict__ fout = (T*)a.fout;
-  const IDX N = (IDX)a.N;
-  static_for<Q>([&](auto ic) {
-    constexpr int I = decltype(ic)::value;
-    fout[(IDX)I * N + (IDX)v] = Codec<S>::template store<I>(g[I]);
-  });
+  if constexpr (S == S_F32) {
+    T* __restrict__ fout = (T*)a.fout;
+    const IDX N = (IDX)a.N;
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      fout[(IDX)I * N + (IDX)v] = Codec<S>::template store<I>(g[I]);
+    });
+  } else {
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      reinterpret_cast<T*>(p.out[I])[(IDX)v] = Codec<S>::template store<I>(g[I]);
+    });
+  }
 }
 
 // ------------------------------------------------------------------------
@@ -294,10 +322,19 @@ static lbm_status dense_step_t(Grid& g, Level& L, cudaStream_t s) {
       prof_end(g, s, pr);
     } else if (zc > 0) {
       const int pr = prof_begin(g, s, "dense_interior", L.n_updated - L.n_reg);
-      if ((int64_t)Q * L.n_slots < (1LL << 31))
-        dense_interior<S, COLL, int32_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
+      using T = typename Codec<S>::T;
+      DensePops p;
+      for (int i = 0; i < Q; ++i) {
+        p.in[i] = (const T*)a.fin + ((int64_t)i * L.n_slots - cx(i));
+        p.out[i] = (T*)a.fout + (int64_t)i * L.n_slots;
+      }
+      // 32-bit offsets while they fit: FP32 indexes every population from
+      // the first (Q N elements); 16-bit offsets are per population and stay
+      // below N + nx ny
+      if ((S == S_F32 ? (int64_t)Q * L.n_slots : L.n_slots + (int64_t)L.nx * L.ny) < (1LL << 31))
+        dense_interior<S, COLL, int32_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a, p);
       else
-        dense_interior<S, COLL, int64_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a);
+        dense_interior<S, COLL, int64_t><<<dim3(gx, gy, zc), blk, 0, s>>>(a, p);
       prof_end(g, s, pr);
     }
     if (fork) {

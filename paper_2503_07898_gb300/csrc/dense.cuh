@@ -98,6 +98,67 @@ __device__ __forceinline__ void pull_row_interior(const typename Codec<S>::T* __
   });
 }
 
+// Lean pull of a voxel in a row with no non-periodic box side next to it in
+// y or z, without per-population selects.  at(IC<I>, o) returns element
+// o + c_x(I) of population I's source array, i.e. population I of voxel
+// o + c_x(I); the pull source of voxel v is at(IC<I>, v + row offset of
+// (c_y, c_z)), one offset per (c_y, c_z) class, wrapping across periodic
+// y / z sides.  Every population is first read as if the voxel were away
+// from the x ends and from walls; voxels at an x end, and voxels with
+// wall-mask bits, then re-read the affected populations in branches that
+// only their lanes take (bounce-back reads population opp(I) of the voxel
+// itself: at(IC<opp(I)>, v - c_x(I))).  The first read of such a
+// population stays inside the arrays: its element lies in [-1, N] of a
+// population I >= 1 (c_x = +1 at x = 0) or I <= Q - 2 (c_x = -1 at x =
+// nx - 1).  Offsets o stay within [-1, N + nx), so IDX is 32-bit while
+// N + nx ny < 2^31 whatever Q N is.
+template <int S, class IDX, class AT>
+__device__ __forceinline__ void pull_lean(const DenseArgs& a, int x, int y, int z, IDX v,
+                                          uint32_t wm, float g[Q], AT&& at) {
+  const IDX nx = (IDX)a.nx, plane = (IDX)a.nx * (IDX)a.ny;
+  const IDX yp = y == 0 ? (IDX)(a.ny - 1) * nx : -nx;
+  const IDX yn = y == a.ny - 1 ? -(IDX)(a.ny - 1) * nx : nx;
+  const IDX zp = z == 0 ? (IDX)(a.nz - 1) * plane : -plane;
+  const IDX zn = z == a.nz - 1 ? -(IDX)(a.nz - 1) * plane : plane;
+  auto src = [&](auto ic) -> IDX {
+    constexpr int I = decltype(ic)::value;
+    IDX o = v;
+    if constexpr (cy(I) > 0) o += yp;
+    else if constexpr (cy(I) < 0) o += yn;
+    if constexpr (cz(I) > 0) o += zp;
+    else if constexpr (cz(I) < 0) o += zn;
+    return o;
+  };
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    g[I] = Codec<S>::template load<I>(at(ic, src(ic)));
+  });
+  if (x == 0) {  // c_x = +1: the source lies past the row start
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      if constexpr (cx(I) > 0)
+        g[I] = Codec<S>::template load<I>(a.px ? at(ic, src(ic) + nx)
+                                               : at(IC<opp(I)>{}, v - (IDX)cx(I)));
+    });
+  }
+  if (x == a.nx - 1) {  // c_x = -1: the source lies past the row end
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      if constexpr (cx(I) < 0)
+        g[I] = Codec<S>::template load<I>(a.px ? at(ic, src(ic) - nx)
+                                               : at(IC<opp(I)>{}, v - (IDX)cx(I)));
+    });
+  }
+  if (wm) {  // sources on walls: halfway bounce-back
+    static_for<Q>([&](auto ic) {
+      constexpr int I = decltype(ic)::value;
+      if constexpr (I != 0) {
+        if ((wm >> I) & 1u) g[I] = Codec<S>::template load<I>(at(IC<opp(I)>{}, v - (IDX)cx(I)));
+      }
+    });
+  }
+}
+
 // A row of the lean pull: no non-periodic box side next to it in y or z.
 __device__ __forceinline__ bool lean_row(const DenseArgs& a, int y, int z) {
   return (a.py || (y > 0 && y < a.ny - 1)) && (a.pz || (z > 0 && z < a.nz - 1));

@@ -84,6 +84,61 @@ def test_sparse_periodic_obstacles_16bit(lbm, storage):
     assert err <= VEL_L2[storage]
 
 
+# ------------------------------------------------------------------ dense
+# The 16-bit dense interior kernel reads every population as if the voxel
+# were away from the x ends and from walls and re-reads the affected ones
+# for voxels at an x end or next to a wall; these cases take every such
+# branch: x ends that wrap and x ends that bounce back, a per-voxel wall
+# mask (obstacles, regularized inlet / outlet), y / z box sides of both kinds.
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_dense_channel_obstacles_16bit(lbm, storage):
+    """Obstacles, regularized inlet / outlet, bounce-back side walls (x, y,
+    z not periodic): the wall-mask path."""
+    dims_zyx = (14, 18, 41)
+    flags = wl.random_obstacles(dims_zyx, seed=24, solid_fraction=0.08)
+    flags[:, :, 0] = wl.flag(wl.VELOCITY, wl.NX_M)
+    flags[:, :, -1] = wl.flag(wl.PRESSURE, wl.NX_P)
+    bc = np.zeros((4,) + dims_zyx)
+    bc[0, :, :, 0] = 0.03
+    bc[3] = 1.0
+    bc[3, :, :, -1] = 0.995
+    rho, u = wl.random_fields(dims_zyx, seed=25, u_amp=0.02)
+    g = make_grid(lbm, "dense", flags, bc, 0.58, storage=storage)
+    lbm.lbm_init_equilibrium(g, 0, rho, u)
+    lbm.lbm_step(g, 100)
+    f = lbm.lbm_get_populations_f64(g, 0)
+    m = updated_mask(flags)
+    assert np.all(np.isfinite(f[:, m]))
+    _, u_gpu = olbm.state_moments(f)
+    _, u_ref = olbm.state_moments(run_oracle(flags, bc, rho, u, 0.58, 100))
+    err = rel_l2(u_gpu, u_ref, m)
+    print(f"dense channel obstacles {storage}: velocity L2 {err:.3e}")
+    assert err <= VEL_L2[storage]
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("periodic", [(1, 0, 1), (0, 1, 1)])
+def test_dense_obstacles_mixed_periodic_16bit(lbm, storage, periodic):
+    """Obstacles on a box periodic along some axes: x ends that wrap or
+    bounce back, with the wall mask, on a ragged 37 x 19 x 23 box."""
+    dims_zyx = (23, 19, 37)
+    flags = wl.random_obstacles(dims_zyx, seed=26, solid_fraction=0.06)
+    rho, u = wl.random_fields(dims_zyx, seed=27, u_amp=0.03)
+    g = make_grid(lbm, "dense", flags, None, 0.6, storage=storage, periodic=periodic)
+    lbm.lbm_init_equilibrium(g, 0, rho, u)
+    lbm.lbm_step(g, 100)
+    f = lbm.lbm_get_populations_f64(g, 0)
+    m = updated_mask(flags)
+    assert np.all(np.isfinite(f[:, m]))
+    _, u_gpu = olbm.state_moments(f)
+    _, u_ref = olbm.state_moments(run_oracle(flags, None, rho, u, 0.6, 100,
+                                             periodic=periodic))
+    err = rel_l2(u_gpu, u_ref, m)
+    print(f"dense obstacles periodic {periodic} {storage}: velocity L2 {err:.3e}")
+    assert err <= VEL_L2[storage]
+
+
 # ------------------------------------------------------- multi-resolution
 
 LMAP3 = np.array([2, 1, 0, 1], np.uint8).reshape(4, 1, 1)
