@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
         }
       }
       float omega = C.omega;
+      float m[4];            // moments of g, formed with the features
+      bool have_m = false;
       if constexpr (CLOSURE) {
         if (C.closure) {  // uniform per item: every lane of every warp takes part
           // a lane without a voxel (past the case's end) joins with the rest state
@@ -148,7 +150,8 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
           }
           ClosureCta* sm = reinterpret_cast<ClosureCta*>(batch_dyn_smem);
           float x[MLP_IN];
-          closure_features(g, C.tau, x);
+          closure_features(g, C.tau, x, m);
+          have_m = true;
           const float dtau = mlp_bf16_warp(x, sm->w, sm->stage[threadIdx.x >> 5]);
           omega = 1.f / fmaxf(C.tau + dtau, TAU_MIN);
         }
@@ -158,7 +161,8 @@ __global__ void __launch_bounds__(BT, (S == S_F32 || CLOSURE) ? 1 : 5) batch_ste
         // through the collision, which keeps it, and stores it: batch cases
         // have no other writer, and whole-sector stores spare the DRAM read
         // that completes a partly written sector (ECC memory)
-        collide<COLL>(g, omega);
+        if (have_m) collide_m<COLL>(g, omega, m[0], m[1], m[2], m[3]);
+        else collide<COLL>(g, omega);
         // one base pointer; the population stride is a constant for sparse
         // items (512) and a 32-bit value for dense ones
         T* __restrict__ o = fout + obase;

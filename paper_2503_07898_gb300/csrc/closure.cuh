@@ -95,32 +95,45 @@ __device__ __forceinline__ void closure_load_smem(ClosureSmem& sm, const Closure
   if (threadIdx.x == 0) sm.b3 = p->b3;
 }
 
-// Features of one voxel from its shifted pulled populations.
-__device__ __forceinline__ void closure_features(const float s[Q], float tau, float x[MLP_IN]) {
+// Features of one voxel from its shifted pulled populations.  The
+// non-equilibrium moments are those of d = s - (f^eq - w); the equilibrium's
+// own moments have closed forms (the lattice's fourth-order isotropy):
+// sum c_a c_b (f^eq - w) = (rho - 1)/3 delta_ab + rho u_a u_b and
+// sum c_a (|c|^2 - c_a^2) (f^eq - w) = 2/3 rho u_a (sum w c_x^2 c_y^2 = 1/9),
+// so they are subtracted from the moments of s instead of forming d per
+// population (equal in exact arithmetic; FP32 rounding differs).
+// m receives (rho - 1, j) as moments_s gives them, for the collision.
+__device__ __forceinline__ void closure_features(const float s[Q], float tau, float x[MLP_IN],
+                                                 float m[4]) {
   float drho, jx, jy, jz;
   moments_s(s, drho, jx, jy, jz);
+  m[0] = drho;
+  m[1] = jx;
+  m[2] = jy;
+  m[3] = jz;
   const float rho = 1.f + drho, inv = 1.f / rho;
   const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  float d[Q];
-  float e = 0.f;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const float E = eq_s(i, drho, rho, ux, uy, uz, usq15);
-    e += E;
-    d[i] = s[i] - E;
-  }
-  d[0] = s[0] - (drho - e);
   float pxx, pyy, pzz, pxy, pxz, pyz;
-  second_moment(d, pxx, pyy, pzz, pxy, pxz, pyz);
+  second_moment(s, pxx, pyy, pzz, pxy, pxz, pyz);
+  const float d3 = drho * (1.f / 3.f);
+  pxx -= d3 + jx * ux;
+  pyy -= d3 + jy * uy;
+  pzz -= d3 + jz * uz;
+  pxy -= jx * uy;
+  pxz -= jx * uz;
+  pyz -= jy * uz;
   float qx = 0.f, qy = 0.f, qz = 0.f;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int ax = cx(i), ay = cy(i), az = cz(i);
-    if (ax && (ay * ay + az * az)) qx += ax > 0 ? d[i] : -d[i];
-    if (ay && (ax * ax + az * az)) qy += ay > 0 ? d[i] : -d[i];
-    if (az && (ax * ax + ay * ay)) qz += az > 0 ? d[i] : -d[i];
+    if (ax && (ay * ay + az * az)) qx += ax > 0 ? s[i] : -s[i];
+    if (ay && (ax * ax + az * az)) qy += ay > 0 ? s[i] : -s[i];
+    if (az && (ax * ax + ay * ay)) qz += az > 0 ? s[i] : -s[i];
   }
+  constexpr float two3 = 2.f / 3.f;
+  qx -= two3 * jx;
+  qy -= two3 * jy;
+  qz -= two3 * jz;
   const float k = 3.f * inv;  // 1 / (rho c_s^2)
   x[0] = drho;
   x[1] = ux;
@@ -139,6 +152,11 @@ __device__ __forceinline__ void closure_features(const float s[Q], float tau, fl
   x[13] = qy * k;
   x[14] = qz * k;
   x[15] = tau;
+}
+
+__device__ __forceinline__ void closure_features(const float s[Q], float tau, float x[MLP_IN]) {
+  float m[4];
+  closure_features(s, tau, x, m);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

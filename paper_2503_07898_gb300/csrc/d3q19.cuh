@@ -205,10 +205,11 @@ enum Collision { C_BGK = 0, C_REG = 1 };
 // weights sum to 1 + 1.5e-8), and for REG its non-equilibrium part is minus
 // the sum of the others, so each update conserves mass up to unbiased
 // rounding.
+// collide_m takes the moments of s from the caller (moments_s of the same
+// values), collide forms them itself.
 template <int COLL>
-__device__ __forceinline__ void collide(float s[Q], float omega) {
-  float drho, jx, jy, jz;
-  moments_s(s, drho, jx, jy, jz);
+__device__ __forceinline__ void collide_m(float s[Q], float omega, float drho, float jx, float jy,
+                                          float jz) {
   const float rho = 1.f + drho;
   const float inv = 1.f / rho;
   const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
@@ -265,6 +266,13 @@ __device__ __forceinline__ void collide(float s[Q], float omega) {
     }
     s[0] = (drho - e) - k * sn;
   }
+}
+
+template <int COLL>
+__device__ __forceinline__ void collide(float s[Q], float omega) {
+  float drho, jx, jy, jz;
+  moments_s(s, drho, jx, jy, jz);
+  collide_m<COLL>(s, omega, drho, jx, jy, jz);
 }
 
 // Regularized velocity / pressure node (3Q live values: s, equilibrium,

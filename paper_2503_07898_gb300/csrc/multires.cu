@@ -617,10 +617,11 @@ __global__ void __launch_bounds__(256, Q == 27 ? 3 : 4) mr_stream_split(MrArgs a
 // collective: every lane takes part).  The populations wait in the thread's
 // column of `park` meanwhile (volatile: the copies must really leave the
 // registers, which the network needs).
+// m receives the moments of g (rho - 1, j) for the collision.
 __device__ __forceinline__ float closure_omega(float g[Q], float tau, ClosureCta* sm,
-                                               float (*park)[256]) {
+                                               float (*park)[256], float m[4]) {
   float x[MLP_IN];
-  closure_features(g, tau, x);
+  closure_features(g, tau, x, m);
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
     *(volatile float*)&park[I][threadIdx.x] = g[I];
@@ -637,7 +638,7 @@ __device__ __forceinline__ float closure_omega(float g[Q], float tau, ClosureCta
 // as in the sparse lean kernel, and the closure runs in the collision.  The
 // masked voxels (interface voxels, bit 31) take part in the network with the
 // rest state, so its warps stay full, and store nothing.
-template <int S, int COLL>
+template <int S, int COLL, class IDX>
 __global__ void __launch_bounds__(256, 3)
     mr_lean_closure(const void* fin, void* fout, const int32_t* __restrict__ nbr,
                     const uint32_t* __restrict__ wmask, const uint8_t* __restrict__ blk_walls,
@@ -656,14 +657,15 @@ __global__ void __launch_bounds__(256, 3)
   const bool act = !(wm & 0xC0000000u);
   float g[Q];
   if (act) {
-    sparse_pull_voxel<S, 8>((const T*)fin, nbr + b * 27, wm, b, l, walls, g);
+    sparse_pull_voxel<S, 8, IDX>((const T*)fin, nbr + b * 27, wm, b, l, walls, g);
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = 0.f;
   }
-  const float omega = closure_omega(g, tau, sm, park);
+  float m[4];
+  const float omega = closure_omega(g, tau, sm, park, m);
   if (!act) return;
-  collide<COLL>(g, omega);
+  collide_m<COLL>(g, omega, m[0], m[1], m[2], m[3]);
   T* __restrict__ out = (T*)fout;
   static_for<Q>([&](auto ic) {
     constexpr int I = decltype(ic)::value;
@@ -759,9 +761,12 @@ __global__ void __launch_bounds__(256, CLOSURE ? 3 : (Q == 27 ? 3 : 4))
     for (int i = 0; i < Q; ++i) g[i] = 0.f;
   }
   float omega = a.omega;
-  if constexpr (CLOSURE) omega = closure_omega(g, a.tau, reinterpret_cast<ClosureCta*>(mr_dyn_smem), mr_slow);
+  float m[4];
+  if constexpr (CLOSURE)
+    omega = closure_omega(g, a.tau, reinterpret_cast<ClosureCta*>(mr_dyn_smem), mr_slow, m);
   if (!act) return;
-  collide<COLL>(g, omega);
+  if constexpr (CLOSURE) collide_m<COLL>(g, omega, m[0], m[1], m[2], m[3]);
+  else collide<COLL>(g, omega);
   const int b = slot >> 9, l = slot & 511;
   T* __restrict__ out = (T*)a.out;
   static_for<Q>([&](auto ic) {
@@ -860,8 +865,14 @@ static lbm_status mr_advance(Grid& g, int l, int k, cudaStream_t s) {
     s = g.mr_aux[l];
     if (closure) {
       const int pr = prof_begin(g, s, kname(0, l), V.n_updated - V.n_iface);
-      mr_lean_closure<S, COLL><<<(unsigned)(2 * V.n_blocks), 256, csm, s>>>(
-          V.f[c], V.f[nx], V.nbr_d, V.wmask_d, V.blk_walls_d, (float)tau_l, a.cp);
+      // 32-bit element offsets in the pull while the level's Q 512 n_blocks
+      // elements fit in 31 bits
+      if ((int64_t)Q * 512 * V.n_blocks < (1LL << 31))
+        mr_lean_closure<S, COLL, int32_t><<<(unsigned)(2 * V.n_blocks), 256, csm, s>>>(
+            V.f[c], V.f[nx], V.nbr_d, V.wmask_d, V.blk_walls_d, (float)tau_l, a.cp);
+      else
+        mr_lean_closure<S, COLL, int64_t><<<(unsigned)(2 * V.n_blocks), 256, csm, s>>>(
+            V.f[c], V.f[nx], V.nbr_d, V.wmask_d, V.blk_walls_d, (float)tau_l, a.cp);
       prof_end(g, s, pr);
     } else {
       st = sparse_uniform_range(g, V, 0, V.n_blocks, V.f[c], V.f[nx], omega, s, kname(0, l),

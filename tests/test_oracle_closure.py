@@ -87,6 +87,34 @@ def test_features_of_known_populations():
     assert np.allclose(F[:, 12], qx, rtol=1e-10)
 
 
+def test_feature_moments_through_closed_equilibrium_moments():
+    """The closure kernels form the non-equilibrium moments of the features
+    from the moments of the shifted populations s = f - w minus the
+    equilibrium's closed-form moments: sum c_a c_b (f^eq - w) = (rho - 1)/3
+    delta_ab + rho u_a u_b and sum c_a (|c|^2 - c_a^2) (f^eq - w) = 2/3 rho
+    u_a.  On random populations that reading gives the oracle's features
+    (which subtract the equilibrium population by population)."""
+    rng = np.random.default_rng(61)
+    rho = 1.0 + 0.02 * rng.standard_normal(50)
+    u = 0.05 * rng.standard_normal((3, 50))
+    g = L.equilibrium(rho, u) + 1e-3 * rng.standard_normal((19, 50))
+    F = cl.features(g, 0.53)
+    s = g - L.W[:, None]
+    C = L.C.astype(float)
+    r = g.sum(0)
+    j = C.T @ g
+    uu = j / r
+    P = np.einsum("ia,ib,iv->abv", C, C, s) - (r - 1) / 3 * np.eye(3)[:, :, None] \
+        - r * uu[:, None, :] * uu[None, :, :]
+    k = 3 / r
+    want = np.stack([P[0, 0], P[1, 1], P[2, 2], P[0, 1], P[0, 2], P[1, 2]]) * k
+    assert np.allclose(F[:, 4:10].T, want, rtol=0, atol=1e-13)
+    for a in range(3):
+        b, c = [m for m in range(3) if m != a]
+        q = (C[:, a] * (C[:, b] ** 2 + C[:, c] ** 2)) @ s - 2 / 3 * j[a]
+        assert np.allclose(F[:, 12 + a], q * k, rtol=0, atol=1e-13)
+
+
 def _fine_feq(u, rho=None):
     shape = u.shape[1:]
     rho = np.ones(shape) if rho is None else rho
