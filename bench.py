@@ -46,8 +46,8 @@ METRIC = "D3Q19 GLUPS & % HBM roofline, FP32 vs FP16-store/learned at stated err
 # 4,070,400 updates per launch) scaled by units to one 256^3 launch
 # (16,711,680 updates), profiles/dense_interior_cavity160_ncu.md; keyed by
 # kernel and storage (the FP16 capture: dense_interior_f16_cavity160_ncu.md).
-NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.343073e+09, "src_sha": "d03b2cafedf1e1c0"},
-               ("dense_interior", "f16"): {"bytes_per_launch": 1.109004e+09, "src_sha": "d03b2cafedf1e1c0"}}
+NCU_TRAFFIC = {("dense_interior", "f32"): {"bytes_per_launch": 2.342294e+09, "src_sha": "27e849b9f3a71c23"},
+               ("dense_interior", "f16"): {"bytes_per_launch": 1.109482e+09, "src_sha": "27e849b9f3a71c23"}}
 
 
 def src_hash():
