@@ -530,7 +530,7 @@ def closure_quality(torch, lbm, wl, N=256, tau0=0.504, T=2048, snap=128, kmax=32
     kept so both levels weigh alike).  Evaluation, three more seeds: the
     3-level slab map (level 0 the central slab) started from the
     box-filtered field runs T / 4 coarsest steps with and without the network
-    on levels 1 and 2; the judge is the plain fine run of the same seed,
+    on levels 1 and 2; the reference is the plain fine run of the same seed,
     box-filtered to each level.  Reported per seed: velocity L2 over the
     voxels of levels 1 and 2 (volume-weighted) without the closure, with the
     network, and with constant corrections d_tau (the best constant is the

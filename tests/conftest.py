@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def lbm():
-    """The product binding; built on demand on a GPU machine."""
+    """The product binding; built on demand on a machine with a GPU."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
