@@ -448,6 +448,108 @@ __global__ void __launch_bounds__(SP_THREADS, sparse_min_ctas<S, MODE, IDX>())
   }
 }
 
+// Two-voxel form of the lean interior kernel for 16-bit storage (D3Q19, 8^3
+// blocks, 32-bit offsets).  A CTA updates one block; thread t takes the two
+// voxels 2t and 2t + 1, neighbours along x (lx = 2k, 2k + 1, k = t mod 4),
+// so a warp holds one z plane of the block:
+//  - the pulls with c_x = 0 of the two voxels are adjacent and aligned (the
+//    element offset of each term is even): one 32-bit load brings both;
+//  - of the pulls with c_x = +1 only the first voxel's can cross the -x face
+//    (k = 0), of those with c_x = -1 only the second voxel's the +x face
+//    (k = 3); the other voxel's source is in the block it would reach
+//    without the x move;
+//  - the 27 neighbour offsets are read once per CTA into shared memory, and
+//    the block choices by (c_y, c_z) are formed once per thread and shared
+//    by both voxels;
+//  - the results go out as one 32-bit store of both voxels per population
+//    (cvt.rn.{f16,bf16}x2.f32 packs them).
+// Blocks with a wall bit (a wall voxel in or next to the block, a missing
+// neighbour, masked voxels) take the one-voxel update for slots t and
+// t + 256, one after the other, in the same launch.  (Measured: running
+// them instead as a second launch of the one-voxel kernel over a block list,
+// with the wall-free blocks' list in this kernel, was 3-4 % slower on every
+// 16-bit workload.)
+template <int S> struct Pair16;
+template <> struct Pair16<S_F16> {
+  using T2 = __half2;
+  __device__ static __forceinline__ float lo(T2 v) { return __low2float(v); }
+  __device__ static __forceinline__ float hi(T2 v) { return __high2float(v); }
+  __device__ static __forceinline__ T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <> struct Pair16<S_BF16> {
+  using T2 = __nv_bfloat162;
+  __device__ static __forceinline__ float lo(T2 v) { return __low2float(v); }
+  __device__ static __forceinline__ float hi(T2 v) { return __high2float(v); }
+  __device__ static __forceinline__ T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+template <int S, int COLL>
+__global__ void __launch_bounds__(SP_THREADS, 4) sparse_pair16(SparseArgs a) {
+  static_assert(Q == 19 && S != S_F32, "two-voxel kernel: D3Q19, 16-bit storage");
+  using T = typename Codec<S>::T;
+  using P = Pair16<S>;
+  using T2 = typename P::T2;
+  constexpr int E3 = 512, QE3 = Q * E3;
+  __shared__ int32_t nb_off[27];
+  const int b = (int)(a.s0 / E3) + (int)blockIdx.x;
+  if (a.blk_walls[b]) {  // uniform per CTA
+    sparse_update<S, 8, COLL, MODE_INTERIOR, int32_t>(a, (int64_t)b * E3 + threadIdx.x);
+    sparse_update<S, 8, COLL, MODE_INTERIOR, int32_t>(a, (int64_t)b * E3 + SP_THREADS + threadIdx.x);
+    return;
+  }
+  if (threadIdx.x < 27) nb_off[threadIdx.x] = __ldg(a.nbr + (int64_t)b * 27 + threadIdx.x) * QE3;
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int k = t & 3, ly = (t >> 2) & 7, lz = t >> 5;
+  const int ey = ly == 0 ? -1 : (ly == 7 ? 1 : 0);
+  const int ez = lz == 0 ? -1 : (lz == 7 ? 1 : 0);
+  const bool xa = k == 0, xb = k == 3;  // first voxel at lx = 0, second at lx = 7
+  const int oS = b * QE3;
+  const int oY = nb_off[13 + 3 * ey], oZ = nb_off[13 + 9 * ez], oYZ = nb_off[13 + 3 * ey + 9 * ez];
+  // across the -x face (first voxel) and the +x face (second voxel)
+  const int oXm = nb_off[12], oXYm = nb_off[12 + 3 * ey], oXZm = nb_off[12 + 9 * ez];
+  const int oXp = nb_off[14], oXYp = nb_off[14 + 3 * ey], oXZp = nb_off[14 + 9 * ez];
+  // in-block source coordinate parts for c = +1, 0, -1 (pre-scaled)
+  const int yp = ((ly - 1) & 7) * 8, y0 = ly * 8, yn = ((ly + 1) & 7) * 8;
+  const int zp = ((lz - 1) & 7) * 64, z0 = lz * 64, zn = ((lz + 1) & 7) * 64;
+  const int lxa = 2 * k;
+  const T* __restrict__ fin = (const T*)a.fin;
+  float ga[Q], gb[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+    const bool ky = Y != 0 && ey == -Y, kz = Z != 0 && ez == -Z;
+    // block reached by the (c_y, c_z) move alone
+    const int oyz = (Y != 0 && Z != 0) ? (ky ? (kz ? oYZ : oY) : (kz ? oZ : oS))
+                                       : (Y != 0 ? (ky ? oY : oS) : (Z != 0 ? (kz ? oZ : oS) : oS));
+    const int lyz = (Y > 0 ? yp : (Y < 0 ? yn : y0)) + (Z > 0 ? zp : (Z < 0 ? zn : z0));
+    if constexpr (X == 0) {
+      const T2 w = reinterpret_cast<const T2*>(fin)[(oyz + I * E3 + lyz + lxa) >> 1];
+      ga[I] = P::lo(w);
+      gb[I] = P::hi(w);
+    } else if constexpr (X > 0) {
+      // first voxel: source lx - 1 (7 of the -x block when k = 0); second: lx - 1 = 2k
+      const int ox = Y != 0 ? (ky ? oXYm : oXm) : (Z != 0 ? (kz ? oXZm : oXm) : oXm);
+      const int oa = xa ? ox : oyz;
+      ga[I] = Codec<S>::template load<I>(fin[oa + I * E3 + lyz + ((lxa - 1) & 7)]);
+      gb[I] = Codec<S>::template load<I>(fin[oyz + I * E3 + lyz + lxa]);
+    } else {
+      // first voxel: source lx + 1 = 2k + 1; second: 2k + 2 (0 of the +x block when k = 3)
+      const int ox = Y != 0 ? (ky ? oXYp : oXp) : (Z != 0 ? (kz ? oXZp : oXp) : oXp);
+      const int ob = xb ? ox : oyz;
+      ga[I] = Codec<S>::template load<I>(fin[oyz + I * E3 + lyz + lxa + 1]);
+      gb[I] = Codec<S>::template load<I>(fin[ob + I * E3 + lyz + ((lxa + 2) & 7)]);
+    }
+  });
+  collide<COLL>(ga, a.omega);
+  collide<COLL>(gb, a.omega);
+  T2* __restrict__ out = reinterpret_cast<T2*>(a.fout) + (oS >> 1) + t;
+  static_for<Q>([&](auto ic) {
+    constexpr int I = decltype(ic)::value;
+    out[I * (E3 / 2)] = P::pack(ga[I], gb[I]);
+  });
+}
+
 // Pull of voxel l of block b with the block's populations staged in shared
 // memory (sb): in-block sources come from there, sources across the block's
 // faces from global memory; block selection and wall rule as in
@@ -597,14 +699,26 @@ static void launch_range(Grid& g, SparseArgs a, cudaStream_t s, const char* name
                           ? (unsigned)((a.s1 - a.s0) / E3)  // one CTA per block
                           : (unsigned)((a.s1 - a.s0 + SP_THREADS - 1) / SP_THREADS);
   const int pr = prof_begin(g, s, name, units);
-  if (MODE == MODE_INTERIOR && i32)
+  bool pair = false;
+  if constexpr (MODE == MODE_INTERIOR && E == 8 && S != S_F32 && Q == 19) {
+    // 16-bit storage: two voxels per thread, one CTA per block (the range
+    // is whole blocks)
+    if (i32) {
+      sparse_pair16<S, COLL><<<(unsigned)((a.s1 - a.s0) / E3), SP_THREADS, 0, s>>>(a);
+      pair = true;
+    }
+  }
+  if (pair) {
+  } else if (MODE == MODE_INTERIOR && i32) {
     sparse_kernel<S, E, COLL, MODE, int32_t><<<nb, SP_THREADS, 0, s>>>(a);
-  else
+  } else {
     sparse_kernel<S, E, COLL, MODE><<<nb, SP_THREADS, 0, s>>>(a);
+  }
   prof_end(g, s, pr);
 }
 
 static bool fits_i32(const Level& L, int q) { return (int64_t)q * L.n_slots < ((int64_t)1 << 31); }
+
 
 template <int S, int E, int COLL>
 static lbm_status sparse_step_t(Grid& g, Level& L, cudaStream_t s) {
