@@ -464,11 +464,17 @@ __global__ void __launch_bounds__(SP_THREADS, sparse_min_ctas<S, MODE, IDX>())
 //  - the results go out as one 32-bit store of both voxels per population
 //    (cvt.rn.{f16,bf16}x2.f32 packs them).
 // Blocks with a wall bit (a wall voxel in or next to the block, a missing
-// neighbour, masked voxels) take the one-voxel update for slots t and
-// t + 256, one after the other, in the same launch.  (Measured: running
-// them instead as a second launch of the one-voxel kernel over a block list,
-// with the wall-free blocks' list in this kernel, was 3-4 % slower on every
-// 16-bit workload.)
+// neighbour, masked voxels) read the wall masks of their voxels, and the
+// choice is made per warp, which holds one z plane of 64 voxels in either
+// form: a warp in which no voxel has a bit runs the two-voxel form, any
+// other warp the one-voxel update of the plane's voxels 64w + lane and
+// 64w + 32 + lane.  (Measured on GB300, FP16: the one-voxel update for
+// every warp of such blocks gave sphere channel 53.3, 384^3 cavity 59.3,
+// turbulence 55.1 GLUPS; a two-voxel wall form for the warps with bits
+// (bounce-back source selects, a warp vote per c_x = 0 pair load, unpaired
+// stores next to masked voxels) 51.6, 56.3, 57.8; running the wall blocks
+// as a second launch of the one-voxel kernel over a block list was 3-4 %
+// slower on every 16-bit workload.)
 template <int S> struct Pair16;
 template <> struct Pair16<S_F16> {
   using T2 = __half2;
@@ -492,14 +498,18 @@ __global__ void __launch_bounds__(SP_THREADS, 4) sparse_pair16(SparseArgs a) {
   constexpr int E3 = 512, QE3 = Q * E3;
   __shared__ int32_t nb_off[27];
   const int b = (int)(a.s0 / E3) + (int)blockIdx.x;
-  if (a.blk_walls[b]) {  // uniform per CTA
-    sparse_update<S, 8, COLL, MODE_INTERIOR, int32_t>(a, (int64_t)b * E3 + threadIdx.x);
-    sparse_update<S, 8, COLL, MODE_INTERIOR, int32_t>(a, (int64_t)b * E3 + SP_THREADS + threadIdx.x);
-    return;
-  }
-  if (threadIdx.x < 27) nb_off[threadIdx.x] = __ldg(a.nbr + (int64_t)b * 27 + threadIdx.x) * QE3;
-  __syncthreads();
   const int t = threadIdx.x;
+  if (t < 27) nb_off[t] = __ldg(a.nbr + (int64_t)b * 27 + t) * QE3;
+  __syncthreads();
+  if (a.blk_walls[b]) {  // uniform per CTA
+    const uint32_t* wm = a.wmask + (int64_t)b * E3 + 2 * t;
+    if (__any_sync(0xffffffffu, (wm[0] | wm[1]) != 0u)) {  // uniform per warp
+      const int64_t s = (int64_t)b * E3 + 2 * (t & ~31) + (t & 31);
+      sparse_update<S, 8, COLL, MODE_INTERIOR, int32_t>(a, s);
+      sparse_update<S, 8, COLL, MODE_INTERIOR, int32_t>(a, s + 32);
+      return;
+    }
+  }
   const int k = t & 3, ly = (t >> 2) & 7, lz = t >> 5;
   const int ey = ly == 0 ? -1 : (ly == 7 ? 1 : 0);
   const int ez = lz == 0 ? -1 : (lz == 7 ? 1 : 0);

@@ -139,22 +139,45 @@ def test_dense_obstacles_mixed_periodic_16bit(lbm, storage, periodic):
     assert err <= VEL_L2[storage]
 
 
+def channel_flags(dims_zyx, seed):
+    """A channel along x (circular cross-section, not-in-domain voxels
+    outside it, so whole blocks are missing and partly filled blocks hold
+    masked voxels) with random solids inside."""
+    nz, ny, nx = dims_zyx
+    z = np.arange(nz)[:, None, None]
+    y = np.arange(ny)[None, :, None]
+    inside = np.broadcast_to((y - ny / 2 + 0.5) ** 2 + (z - nz / 2 + 0.5) ** 2 < (0.45 * nz) ** 2,
+                             dims_zyx)
+    flags = wl.random_obstacles(dims_zyx, seed=seed, solid_fraction=0.05)
+    flags[~inside] = wl.OUTSIDE
+    return flags
+
+
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("collision", ["bgk", "reg"])
-@pytest.mark.parametrize("obstacle", [False, True])
-def test_sparse_16bit_equals_dense_16bit(lbm, storage, collision, obstacle):
-    """Periodic box, every block active: the block-sparse 16-bit step (two
-    voxels per thread in blocks without walls, one voxel per thread in blocks
-    next to the solid box) gives the dense 16-bit step's populations bit for
-    bit: both pull the same stored values and run the same collision."""
+@pytest.mark.parametrize("layout", ["periodic", "obstacle", "channel"])
+def test_sparse_16bit_equals_dense_16bit(lbm, storage, collision, layout):
+    """The block-sparse 16-bit step (two voxels per thread; in blocks with
+    walls, the warps whose z plane holds a wall bit update one voxel at a
+    time and the others keep the two-voxel form) gives the dense 16-bit
+    step's populations bit for bit: both pull the same stored values and run
+    the same collision.  Layouts: a periodic box with every block active,
+    the same with a solid box, and a channel periodic along x only (missing
+    blocks outside it, not-in-domain and solid voxels inside blocks,
+    bounce-back at the y / z box sides)."""
     dims_zyx = (24, 32, 48)
+    periodic = (1, 1, 1)
     flags = np.zeros(dims_zyx, np.uint8)
-    if obstacle:
+    if layout == "obstacle":
         flags[3:9, 10:15, 30:37] = wl.SOLID
+    elif layout == "channel":
+        dims_zyx = (32, 40, 48)
+        flags = channel_flags(dims_zyx, seed=29)
+        periodic = (1, 0, 0)
     rho, u = wl.random_fields(dims_zyx, seed=28, u_amp=0.03)
     out = []
     for kind in ("dense", "sparse"):
-        g = make_grid(lbm, kind, flags, None, 0.57, collision, storage, periodic=(1, 1, 1))
+        g = make_grid(lbm, kind, flags, None, 0.57, collision, storage, periodic=periodic)
         lbm.lbm_init_equilibrium(g, 0, rho, u)
         lbm.lbm_step(g, 40)
         out.append(lbm.lbm_get_populations_f64(g, 0))
