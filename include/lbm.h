@@ -56,7 +56,7 @@ typedef enum {
   LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed                      */
   LBM_ERR_TIMEOUT = 4,     /* a bounded device wait ran out                   */
   LBM_ERR_DIVERGED = 5,    /* non-finite mass / momentum                      */
-  LBM_ERR_UNSUPPORTED = 6, /* valid request this build does not implement     */
+  LBM_ERR_UNSUPPORTED = 6, /* valid request the library does not implement   */
   LBM_ERR_INTERNAL = 7     /* library invariant broken (device-side check)    */
 } lbm_status;
 
@@ -131,7 +131,8 @@ lbm_status lbm_grid_create_dense(const int dims[3], const lbm_physics* phys,
  * and the groups: a block is a boundary block iff it holds a regularized
  * voxel (Sec. 6.2).  Numbering: boundary blocks first, then non-boundary
  * blocks, each in ascending Morton order of the block coordinate (x lowest
- * bit).  Storage index ((block * 19) + pop) * E^3 + lx + E*(ly + E*lz).
+ * bit).  Storage index ((block * Q) + pop) * E^3 + lx + E*(ly + E*lz), Q = 19
+ * or 27 (phys->lattice).
  * block_edge must be 4 or 8; periodic axes need dims divisible by it. */
 lbm_status lbm_grid_create_sparse(const int dims[3], int block_edge,
                                   const uint8_t* flags, const lbm_physics* phys,

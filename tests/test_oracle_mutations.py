@@ -1,0 +1,193 @@
+"""The oracle's pins against planted mistakes (CPU).
+
+A pin is only worth something if a plausible mistake in the function it
+checks makes it fail.  Each case below copies the oracle into a scratch
+directory, plants one mistake in the copy (a textual edit of one line: a
+sign, a factor, an index, a direction, a dropped term), and runs the pin
+files that cover that function against the copy in a separate interpreter.
+The case passes when that run ends with failing tests (pytest exit code 1);
+an unmodified copy must pass the same files (exit code 0), which shows that
+the harness itself does not cause the failures.  Edits that cannot change
+any result are not listed: for instance, dropping the second hop of the
+coalescence trace in `layout.multires_interface` leaves the classification
+as it is, since that hop always lands in the coarse voxel G - c_i, which the
+first hop of another subcell of G reaches as well, and levels own whole
+coarse voxels.
+
+The product is not involved: only `oracle/`, the input generators of
+`paper_2503_07898_gb300/workloads.py` and the `-m "not gpu"` pin files are
+copied.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+PINS = "test_oracle_pins.py"
+Q27 = "test_oracle_d3q27.py"
+MR = "test_oracle_multires.py"
+CL = "test_oracle_closure.py"
+
+# (name, oracle file, original text, planted text, pin files run)
+MUTATIONS = [
+    # lattice: weights, equilibrium, regularized projection, velocity order
+    ("weights_axis_edge_swapped", "lattice.py",
+     "_W19 = [Fraction(1, 3)] + [Fraction(1, 18)] * 6 + [Fraction(1, 36)] * 12",
+     "_W19 = [Fraction(1, 3)] + [Fraction(1, 36)] * 6 + [Fraction(1, 18)] * 12", [PINS]),
+    ("equilibrium_quadratic_factor", "lattice.py",
+     "1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq", "1.0 + 3.0 * cu + 4.0 * cu * cu - 1.5 * usq",
+     [PINS]),
+    ("equilibrium_usq_sign", "lattice.py",
+     "1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq", "1.0 + 3.0 * cu + 4.5 * cu * cu + 1.5 * usq",
+     [PINS]),
+    ("regularized_projection_factor", "lattice.py",
+     "out[i] = 4.5 * self.W[i] * acc", "out[i] = 3.0 * self.W[i] * acc", [PINS]),
+    ("regularized_projection_trace_dropped", "lattice.py",
+     "(1.0 / 3.0 if a == b else 0.0)", "(0.0 if a == b else 0.0)", [PINS]),
+    ("velocity_order_not_paired", "lattice.py",
+     "(1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0),",
+     "(1, 1, 0), (1, -1, 0), (-1, -1, 0), (-1, 1, 0),", [PINS]),
+    # single-resolution step: streaming, walls, collision, regularized nodes
+    ("stream_direction_reversed", "lbm.py",
+     "src_val = _shift(f[i], cz, cy, cx)", "src_val = _shift(f[i], -cz, -cy, -cx)", [PINS]),
+    ("bounce_back_not_opposite", "lbm.py",
+     "g[i] = np.where(wall, f[lat.OPP[i]], src_val)", "g[i] = np.where(wall, f[i], src_val)",
+     [PINS]),
+    ("outside_voxels_not_walls", "lbm.py",
+     "wall = (src_type == SOLID) | (src_type == OUTSIDE)", "wall = (src_type == SOLID)", [PINS]),
+    ("box_side_one_end_only", "lbm.py",
+     "out = out | (s < 0) | (s >= n)", "out = out | (s < 0)", [PINS]),
+    ("bgk_rate_inverted", "lbm.py",
+     "f_star = g - (g - feq) / tau", "f_star = g - (g - feq) * tau", [PINS]),
+    ("reg_collision_factor", "lbm.py",
+     "f_star = feq + (1.0 - 1.0 / tau) * lat.regularized_neq(lat.second_moment(g - feq))",
+     "f_star = feq + (1.0 - 0.5 / tau) * lat.regularized_neq(lat.second_moment(g - feq))", [PINS]),
+    ("velocity_node_density_sign", "lbm.py",
+     "rho = s / (1.0 + un)", "rho = s / (1.0 - un)", [PINS]),
+    ("pressure_node_velocity_sign", "lbm.py",
+     "un = s / rho - 1.0", "un = 1.0 - s / rho", [PINS]),
+    ("known_sum_factor_dropped", "lbm.py",
+     "s = g_node[k0].sum(axis=0) + 2.0 * g_node[kp].sum(axis=0)",
+     "s = g_node[k0].sum(axis=0) + g_node[kp].sum(axis=0)", [PINS]),
+    ("unknown_neq_bounce_sign", "lbm.py",
+     "g[i] = feq[i] + (g[j] - feq[j])", "g[i] = feq[i] - (g[j] - feq[j])", [PINS]),
+    # D3Q27 corner weights
+    ("d3q27_corner_weight", "lattice.py",
+     "[Fraction(1, 54)] * 12 + [Fraction(1, 216)] * 8", "[Fraction(1, 54)] * 12 + [Fraction(1, 108)] * 8",
+     [Q27]),
+    # multi-resolution exchange
+    ("level_tau_scaling_inverted", "multires.py",
+     "return 0.5 + (tau0 - 0.5) / (2 ** level)", "return 0.5 + (tau0 - 0.5) * (2 ** level)", [MR]),
+    ("explosion_substeps_swapped", "multires.py",
+     "                if k == 1:\n", "                if k == 2:\n", [MR]),
+    ("coalescence_second_hop_dropped", "multires.py",
+     "coal = subcell_mean(shift(held, c))", "coal = subcell_mean(held)", [MR]),
+    ("coalescence_reads_start_state", "multires.py",
+     "held = np.where(own_f == lv - 1, f1_fine[i], v1)",
+     "held = np.where(own_f == lv - 1, f0_fine[i], v1)", [MR]),
+    ("volume_weight_wrong", "multires.py",
+     "out += (8.0 ** lv) * lbm.conservation(self.f[lv])",
+     "out += (4.0 ** lv) * lbm.conservation(self.f[lv])", [MR]),
+    # layout tables
+    ("morton_y_bit_misplaced", "layout.py",
+     "code |= ((by >> k) & 1) << (3 * k + 1)", "code |= ((by >> k) & 1) << (3 * k)", [PINS]),
+    ("boundary_blocks_last", "layout.py",
+     "keys = [(0 if isb else 1, morton_code(*c)) for c, isb in zip(active, boundary)]",
+     "keys = [(1 if isb else 0, morton_code(*c)) for c, isb in zip(active, boundary)]", [PINS]),
+    ("interface_explosion_source_reversed", "layout.py",
+     "dep |= at(o, C[i], 1) == lv + 1", "dep |= at(o, C[i], -1) == lv + 1", [MR]),
+    # learned closure: network, training, features, data path
+    ("relu_derivative_dropped", "closure.py",
+     "dz2 = dh2 * (z2 > 0)", "dz2 = dh2", [CL]),
+    ("adam_bias_correction_dropped", "closure.py",
+     "mhat = m / (1 - beta1 ** step)", "mhat = m", [CL]),
+    ("fold_bias_sign", "closure.py",
+     'p["b1"] = p["b1"] - p["W1"] @ (mu / sd)', 'p["b1"] = p["b1"] + p["W1"] @ (mu / sd)', [CL]),
+    ("splitmix_final_shift", "closure.py",
+     "return x ^ (x >> 31)", "return x ^ (x >> 30)", [CL]),
+    ("feature_scale", "closure.py",
+     "s = rho / 3.0", "s = rho / 2.0", [CL]),
+    ("eddy_central_difference_reversed", "closure.py",
+     "0.5 * (np.roll(ub[b], -1, axis=axis) - np.roll(ub[b], 1, axis=axis))",
+     "0.5 * (np.roll(ub[b], 1, axis=axis) - np.roll(ub[b], -1, axis=axis))", [CL]),
+    ("eddy_sign", "closure.py",
+     "nu_t = np.where(den > 0, -num / den, 0.0)", "nu_t = np.where(den > 0, num / den, 0.0)", [CL]),
+    ("eddy_factor_three_dropped", "closure.py",
+     "return np.clip(3.0 * nu_t,", "return np.clip(nu_t,", [CL]),
+    ("eddy_density_dropped", "closure.py",
+     "den = 2.0 * rb * den", "den = 2.0 * den", [CL]),
+    ("coarse_pull_shift_reversed", "closure.py",
+     "out[i] = np.roll(fb[i], shift=(cz, cy, cx), axis=(0, 1, 2))",
+     "out[i] = np.roll(fb[i], shift=(-cz, -cy, -cx), axis=(0, 1, 2))", [CL]),
+    ("box_filter_transposed", "closure.py",
+     "b = a.reshape(*lead, nz // r, r, ny // r, r, nx // r, r)",
+     "b = a.reshape(*lead, r, nz // r, r, ny // r, r, nx // r)", [CL]),
+]
+
+
+def _copy_tree(dst, oracle_file=None, old=None, new=None):
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    pkg = os.path.join(dst, "paper_2503_07898_gb300")
+    os.makedirs(pkg)
+    for f in ("__init__.py", "workloads.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2503_07898_gb300", f), pkg)
+    tdir = os.path.join(dst, "tests")
+    os.makedirs(tdir)
+    for f in ("conftest.py", PINS, Q27, MR, CL):
+        shutil.copy(os.path.join(ROOT, "tests", f), tdir)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), dst)
+    if oracle_file is not None:
+        path = os.path.join(dst, "oracle", oracle_file)
+        src = open(path).read()
+        assert src.count(old) == 1, f"planted edit must match exactly once in {oracle_file}: {old!r}"
+        open(path, "w").write(src.replace(old, new))
+
+
+def _run_pins(dst, files):
+    env = {k: v for k, v in os.environ.items() if k != "PYTHONPATH"}
+    env.update(PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1")
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
+    cmd += [os.path.join("tests", f) for f in files]
+    r = subprocess.run(cmd, cwd=dst, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+def _case(m):
+    name, ofile, old, new, files = m
+    with tempfile.TemporaryDirectory(prefix="oracle_mut_") as d:
+        _copy_tree(d, ofile, old, new)
+        return _run_pins(d, files)
+
+
+UNMODIFIED = ("unmodified", None, None, None, [PINS, Q27, MR, CL])
+
+
+@pytest.fixture(scope="module")
+def outcomes():
+    """Run the unmodified copy and every planted mistake once, in parallel
+    interpreters."""
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {m[0]: ex.submit(_case, m) for m in [UNMODIFIED] + MUTATIONS}
+        return {k: f.result() for k, f in futs.items()}
+
+
+def test_unmodified_copy_passes_the_pins(outcomes):
+    rc, out = outcomes["unmodified"]
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    rc, out = outcomes[name]
+    # 1: tests ran and some failed; anything else (collection error, crash)
+    # would not show that a pin caught the mistake
+    assert rc == 1, f"{name}: pytest exit code {rc}\n{out}"

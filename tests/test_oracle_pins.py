@@ -75,6 +75,26 @@ def test_regularized_projection_reproduces_second_moment():
     assert np.allclose(L.C.T.astype(float) @ fneq, 0.0, atol=1e-14)
 
 
+def test_reg_collision_equals_bgk_on_a_regularized_input():
+    """Populations f^eq(rho, u) + f^{neq,reg}(Pi) have no non-equilibrium
+    part outside the second-order Hermite space the regularized collision
+    keeps, so REG and BGK give the same post-collision state, the closed form
+    f^eq + (1 - 1/tau) f^{neq,reg}(Pi) (Latt and Chopard, Sec. 6.2)."""
+    rng = np.random.default_rng(13)
+    shape = (5, 6)
+    rho = 1.0 + 0.02 * rng.standard_normal(shape)
+    u = 0.03 * rng.standard_normal((3,) + shape)
+    a = 1e-3 * rng.standard_normal((3, 3) + shape)
+    pi = a + a.transpose(1, 0, 2, 3)
+    g = L.equilibrium(rho, u) + L.regularized_neq(pi)
+    for tau in (0.52, 0.6, 1.3):
+        fb, _, _ = lbm.collide(g, tau, "bgk")
+        fr, _, _ = lbm.collide(g, tau, "reg")
+        want = L.equilibrium(rho, u) + (1.0 - 1.0 / tau) * L.regularized_neq(pi)
+        assert np.allclose(fr, fb, rtol=0, atol=1e-15)
+        assert np.allclose(fr, want, rtol=0, atol=1e-15)
+
+
 # ------------------------------------------------------------ conservation
 
 @pytest.mark.parametrize("collision", ["bgk", "reg"])
@@ -132,6 +152,27 @@ def test_closed_box_conserves_mass():
     m0 = lbm.conservation(f, flags)[0]
     f = lbm.run(f, flags, 0.58, 60)
     assert abs(lbm.conservation(f, flags)[0] - m0) / m0 < 1e-13
+
+
+def test_not_in_domain_voxels_bounce_back_like_solids():
+    """Voxels outside the domain (type 7) are walls (halfway bounce-back,
+    Sec. 6.2): a fluid region enclosed by a shell of them on a periodic box
+    conserves its mass exactly, and steps exactly as the same region
+    enclosed by solid voxels."""
+    shape = (8, 9, 10)
+    rho, u = wl.random_fields(shape, seed=12)
+    shell = np.ones(shape, bool)
+    shell[1:-1, 1:-1, 1:-1] = False
+    res = []
+    for kind in (wl.OUTSIDE, wl.SOLID):
+        flags = np.zeros(shape, np.uint8)
+        flags[shell] = kind
+        f = lbm.init_equilibrium(rho, u, flags)
+        m0 = lbm.conservation(f, flags)[0]
+        f = lbm.run(f, flags, 0.6, 40, periodic=(True, True, True))
+        assert abs(lbm.conservation(f, flags)[0] - m0) / m0 < 1e-13
+        res.append(f)
+    assert np.array_equal(res[0], res[1])
 
 
 def test_closed_box_mirror_symmetry():
