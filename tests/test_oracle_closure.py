@@ -312,6 +312,26 @@ def test_eddy_target_recovers_a_planted_eddy_viscosity(a, b, nu0):
     assert np.allclose(t, 3 * nu0, rtol=1e-9, atol=1e-12), (t.min(), t.max())
 
 
+def test_eddy_target_ignores_an_isotropic_sub_filter_stress():
+    """The fit uses the deviator of the sub-filter stress.  Inside every 2^3
+    box the fine velocity carries +-eps along each axis with the signs set by
+    the subcell's x, y and z parity, so the eight subcells take all eight
+    sign patterns: the sub-filter stress is rho eps^2 I (equal variances, no
+    covariance).  Under the diverging filtered velocity u_x = A sin(2 pi X /
+    n) (S_xx != 0) the target is 0 everywhere; keeping the trace would give
+    3 nu_t = -3 sum_N rho eps^2 S_xx / (2 rho sum_N S_xx^2), about -5e-3."""
+    n, r, A, eps, rho0 = 8, 2, 0.01, 0.004, 1.1
+    N = n * r
+    X = np.indices((n, n, n))[2]
+    up = lambda c: c.repeat(r, 0).repeat(r, 1).repeat(r, 2)
+    fine = np.indices((N, N, N))                   # fine (z, y, x)
+    u = np.stack([eps * np.where(fine[2 - a] % 2 == 0, 1.0, -1.0) for a in range(3)])
+    u[0] += up(A * np.sin(2 * np.pi * X / n))
+    f = L.equilibrium(np.full((N, N, N), rho0), u)
+    t = cl.eddy_target(f, r, 0.51)
+    assert np.allclose(t, 0.0, rtol=0, atol=1e-12), (t.min(), t.max())
+
+
 def test_eddy_target_sums_over_the_3x3x3_neighbourhood():
     """Sub-filter stress in one coarse voxel X0 only: the target is nonzero
     exactly on the 27 voxels whose neighbourhood holds X0, with the value

@@ -128,6 +128,56 @@ MUTATIONS = [
     ("box_filter_transposed", "closure.py",
      "b = a.reshape(*lead, nz // r, r, ny // r, r, nx // r, r)",
      "b = a.reshape(*lead, r, nz // r, r, ny // r, r, nx // r)", [CL]),
+    ("features_third_order_weight_sign", "closure.py",
+     "w = Cf[:, a] * (Cf[:, b] ** 2 + Cf[:, c] ** 2)", "w = Cf[:, a] * (Cf[:, b] ** 2 - Cf[:, c] ** 2)",
+     [CL]),
+    ("features_norm_cross_factor", "closure.py",
+     "pzz ** 2 + 2 * (pxy ** 2 + pxz ** 2 + pyz ** 2)", "pzz ** 2 + (pxy ** 2 + pxz ** 2 + pyz ** 2)",
+     [CL]),
+    ("features_trace_sign", "closure.py", "tr = pxx + pyy + pzz", "tr = pxx + pyy - pzz", [CL]),
+    ("forward_bias_dropped", "closure.py",
+     'z1 = X @ p["W1"].T + p["b1"]', 'z1 = X @ p["W1"].T', [CL]),
+    ("gradient_w1_sign", "closure.py", 'g["W1"] = dz1.T @ X', 'g["W1"] = -dz1.T @ X', [CL]),
+    ("adam_second_moment_not_squared", "closure.py",
+     "v = beta2 * v + (1 - beta2) * grad * grad", "v = beta2 * v + (1 - beta2) * abs(grad)", [CL]),
+    ("sgs_stress_density_dropped", "closure.py",
+     "- rb * ub[a] * ub[b]", "- ub[a] * ub[b]", [CL]),
+    ("strain_not_symmetrised", "closure.py",
+     "S = 0.5 * (grad + grad.transpose(1, 0, *range(2, grad.ndim)))", "S = grad", [CL]),
+    ("stress_deviator_dropped", "closure.py",
+     "dev = tsgs[a, b] - (tr if a == b else 0.0)", "dev = tsgs[a, b]", [CL]),
+    ("neighbourhood_sum_self_only", "closure.py",
+     "    for dz in (-1, 0, 1):\n        for dy in (-1, 0, 1):\n            for dx in (-1, 0, 1):\n"
+     "                out = out + np.roll(a",
+     "    for dz in (0,):\n        for dy in (-1, 0, 1):\n            for dx in (-1, 0, 1):\n"
+     "                out = out + np.roll(a", [CL]),
+    ("closure_tau_not_clamped", "closure.py",
+     "tau_eff[fluid] = np.maximum(tau + d_tau, TAU_MIN)", "tau_eff[fluid] = tau + d_tau", [CL]),
+    ("minibatch_counter_offset", "closure.py",
+     "c0 = (step - 1) * batch", "c0 = step * batch", [CL]),
+    ("standardisation_constant_rule_dropped", "closure.py",
+     "sd = np.where((sd > 1e-6 * np.abs(mu)) & (sd > 1e-30), sd, 1.0)",
+     "sd = np.where(sd > 1e-30, sd, 1.0)", [CL]),
+    ("block_activity_counts_solids", "layout.py",
+     "UPDATED_TYPES = (0, 2, 3)", "UPDATED_TYPES = (0, 1, 2, 3)", [PINS]),
+    ("block_neighbours_not_wrapped", "layout.py",
+     "q[a] %= dims_b[a]", "q[a] = -1", [PINS]),
+    ("bitmask_bit_order_reversed", "layout.py",
+     "words[b // 32] |= np.uint32(1 << (b % 32))", "words[b // 32] |= np.uint32(1 << (31 - b % 32))",
+     [PINS]),
+    ("regularized_node_relaxation_factor", "lbm.py",
+     "f_star = feq + (1.0 - 1.0 / tau) * fneq", "f_star = feq + (1.0 - 0.5 / tau) * fneq", [PINS]),
+    ("taylor_green_viscosity_closed_form", "lbm.py",
+     "nu = (tau - 0.5) / 3.0", "nu = (tau - 0.5) / 6.0", [PINS]),
+    ("subcell_mean_pairs_wrong", "multires.py",
+     "a = 0.5 * (a[..., 0::2] + a[..., 1::2])", "a = 0.5 * (a[..., 0::2] + a[..., 0::2])", [MR]),
+    ("explosion_second_substep_one_hop", "multires.py",
+     "ex = np.where(shift(own, c, 2) == lv, shift(f0_self[i], c, 2),",
+     "ex = np.where(shift(own, c, 2) == lv, shift(f0_self[i], c, 1),", [MR]),
+    ("closure_on_finest_level", "multires.py",
+     "if self.theta is not None and lv > 0:", "if self.theta is not None and lv >= 0:", [MR]),
+    ("explosion_opposite_population", "multires.py",
+     "c_up = upsample(self.f[lv + 1][i])", "c_up = upsample(self.f[lv + 1][self.lat.OPP[i]])", [MR]),
 ]
 
 

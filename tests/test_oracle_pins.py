@@ -337,6 +337,34 @@ def test_block_tables_hand_example():
     assert nbr[0, k(0, 0, 0)] == 0
 
 
+def test_block_tables_periodic_wrap_hand_example():
+    """3 x 3 x 2 blocks, periodic along x and z, walls at the y sides:
+    across a periodic side the neighbour is the block on the far side
+    (with two blocks along z, -z and +z name the same block), across a
+    walled side there is none, and the table is an involution."""
+    flags = np.zeros((16, 24, 24), np.uint8)
+    t = layout.block_tables(flags, 8, periodic=(True, False, True))
+    ids = {tuple(int(v) for v in c): b for b, c in enumerate(t["coords"])}
+    nbr = t["nbr"]
+    k = lambda dx, dy, dz: (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+    b0 = ids[(0, 0, 0)]
+    assert nbr[b0, k(-1, 0, 0)] == ids[(2, 0, 0)]
+    assert nbr[b0, k(1, 0, 0)] == ids[(1, 0, 0)]
+    assert nbr[b0, k(0, 0, -1)] == ids[(0, 0, 1)] == nbr[b0, k(0, 0, 1)]
+    assert nbr[b0, k(-1, 0, -1)] == ids[(2, 0, 1)]
+    assert nbr[b0, k(0, -1, 0)] == -1 and nbr[b0, k(-1, -1, 1)] == -1
+    assert nbr[b0, k(1, 1, 1)] == ids[(1, 1, 1)]
+    b1 = ids[(2, 2, 1)]
+    assert nbr[b1, k(1, 0, 1)] == ids[(0, 2, 0)]
+    assert nbr[b1, k(0, 1, 0)] == -1 and nbr[b1, k(0, -1, 0)] == ids[(2, 1, 1)]
+    # the 6 blocks on each walled side miss the 9 neighbours across it
+    assert len(ids) == 18 and int((nbr < 0).sum()) == 2 * 6 * 9
+    for b in range(len(ids)):
+        for kk in range(27):
+            if nbr[b, kk] >= 0:
+                assert nbr[nbr[b, kk], 26 - kk] == b
+
+
 def test_block_tables_bitmask_grouping_hand_example():
     """Bitmask grouping of the example above: every block in Morton order,
     (1,1,0) marked by bit 3, its two regularized voxels indexed 0 and 1 in
