@@ -178,6 +178,17 @@ MUTATIONS = [
      "if self.theta is not None and lv > 0:", "if self.theta is not None and lv >= 0:", [MR]),
     ("explosion_opposite_population", "multires.py",
      "c_up = upsample(self.f[lv + 1][i])", "c_up = upsample(self.f[lv + 1][self.lat.OPP[i]])", [MR]),
+    ("d3q27_corner_order_not_paired", "lattice.py",
+     "(1, -1, 1), (-1, 1, -1), (-1, 1, 1), (1, -1, -1),",
+     "(1, -1, 1), (-1, 1, 1), (-1, 1, -1), (1, -1, -1),", [Q27]),
+    ("d3q27_edge_weight", "lattice.py",
+     "[Fraction(2, 27)] * 6 + [Fraction(1, 54)] * 12", "[Fraction(2, 27)] * 6 + [Fraction(1, 27)] * 12",
+     [Q27]),
+    ("flag_normal_bits_shifted", "lbm.py",
+     "return (flags >> 3) & 7", "return (flags >> 4) & 7", [PINS]),
+    ("box_sides_axes_swapped", "lbm.py",
+     "for coord, n, ci, per in ((x, nx, c[0], periodic[0]), (y, ny, c[1], periodic[1]),",
+     "for coord, n, ci, per in ((x, nx, c[0], periodic[2]), (y, ny, c[1], periodic[1]),", [PINS]),
 ]
 
 
