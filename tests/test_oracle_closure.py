@@ -332,6 +332,16 @@ def test_eddy_target_ignores_an_isotropic_sub_filter_stress():
     assert np.allclose(t, 0.0, rtol=0, atol=1e-12), (t.min(), t.max())
 
 
+@pytest.mark.parametrize("nu0,want", [(0.3, 0.5), (-0.1, -(0.51 - 0.5) + 1e-3)])
+def test_eddy_target_is_clamped(nu0, want):
+    """A planted eddy viscosity whose 3 nu0 lies outside the admissible range
+    gives the bound: at most 1/2, at least -(tau_c - 1/2) + 1e-3 (so that the
+    coarse level keeps tau > 1/2)."""
+    f, _ = _shear_state(0, 1, nu0)
+    t = cl.eddy_target(f, 2, 0.51)
+    assert np.allclose(t, want, rtol=0, atol=1e-15)
+
+
 def test_eddy_target_sums_over_the_3x3x3_neighbourhood():
     """Sub-filter stress in one coarse voxel X0 only: the target is nonzero
     exactly on the 27 voxels whose neighbourhood holds X0, with the value

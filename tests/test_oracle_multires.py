@@ -240,6 +240,22 @@ def test_closed_box_conserves_volume_weighted_mass():
     assert abs(g.conservation()[0] / m0 - 1) < 1e-12
 
 
+def test_closed_box_with_an_obstacle_conserves_volume_weighted_mass():
+    """Solid voxels on level 0 are walls: they bounce back and hold no
+    populations, so the volume-weighted mass of the two-level closed box
+    stays exact."""
+    lmap = wl.multires_cavity_map(48, 2, (1,))
+    flags0 = np.zeros((48, 48, 48), np.uint8)
+    flags0[3:9, 20:26, 5:11] = wl.SOLID            # inside level 0's shell
+    g = mr.MultiRes(lmap, 2, 16, 0.6, periodic=(False,) * 3, flags0=flags0)
+    init_random(g, 63)
+    assert np.all(g.f[0][:, flags0 == wl.SOLID] == 0)
+    m0 = g.conservation()[0]
+    g.run(3)
+    assert np.all(g.f[0][:, flags0 == wl.SOLID] == 0)
+    assert abs(g.conservation()[0] / m0 - 1) < 1e-12
+
+
 def test_cavity_near_walls_equals_single_resolution():
     """Finest-level voxels beyond the light cone of the level jump (lid,
     walls and the edges between them) evolve exactly as in a plain fine

@@ -189,6 +189,56 @@ MUTATIONS = [
     ("box_sides_axes_swapped", "lbm.py",
      "for coord, n, ci, per in ((x, nx, c[0], periodic[0]), (y, ny, c[1], periodic[1]),",
      "for coord, n, ci, per in ((x, nx, c[0], periodic[2]), (y, ny, c[1], periodic[1]),", [PINS]),
+    ("moments_velocity_not_divided", "lattice.py", "return rho, j / rho", "return rho, j", [PINS]),
+    ("second_moment_index", "lattice.py",
+     "out[a, b] = np.tensordot(Cf[:, a] * Cf[:, b], f, axes=(0, 0))",
+     "out[a, b] = np.tensordot(Cf[:, a] * Cf[:, a], f, axes=(0, 0))", [PINS]),
+    ("known_set_reversed", "lbm.py",
+     "kp = np.flatnonzero(cn > 0)", "kp = np.flatnonzero(cn < 0)", [PINS]),
+    ("boundary_stress_not_neq", "lbm.py",
+     "pi_neq = lat.second_moment(g - feq)", "pi_neq = lat.second_moment(g)", [PINS]),
+    ("regularized_voxels_not_stored", "lbm.py",
+     "updated = (types == FLUID) | reg", "updated = (types == FLUID)", [PINS]),
+    ("guo_half_force_shift", "lbm.py",
+     "j = j + 0.5 * np.asarray(force", "j = j + 1.0 * np.asarray(force", [PINS]),
+    ("guo_source_prefactor", "lbm.py",
+     "f_star[i] = f_star[i] + (1.0 - 0.5 / tau) * lat.W[i] * src",
+     "f_star[i] = f_star[i] + (1.0 - 1.0 / tau) * lat.W[i] * src", [PINS]),
+    ("init_skips_velocity_nodes", "lbm.py",
+     "f = L.equilibrium(rho, u, q)\n    if flags is not None:\n        t = flag_type(flags)\n"
+     "        upd = (t == FLUID) | (t == VELOCITY) | (t == PRESSURE)",
+     "f = L.equilibrium(rho, u, q)\n    if flags is not None:\n        t = flag_type(flags)\n"
+     "        upd = (t == FLUID) | (t == PRESSURE)", [PINS]),
+    ("finer_neighbour_level", "multires.py",
+     "finer |= nb == lv - 1", "finer |= nb == lv + 1", [MR]),
+    ("level_tau_off_by_one", "multires.py",
+     "tau = tau_of_level(self.tau0, lv)", "tau = tau_of_level(self.tau0, lv + 1)", [MR]),
+    ("finest_solids_updated", "multires.py",
+     "            mine = mine & self.updated0\n        self.f[lv] = np.where",
+     "            mine = mine\n        self.f[lv] = np.where", [MR]),
+    ("coalescence_first_hop_state", "multires.py",
+     "v1 = np.where(shift(own_f, c) == lv - 1, shift(f0_fine[i], c), shift(s_up, c))",
+     "v1 = np.where(shift(own_f, c) == lv - 1, shift(f1_fine[i], c), shift(s_up, c))", [MR]),
+    ("loss_gradient_factor", "closure.py", "dy = 2.0 * r / n", "dy = r / n", [CL]),
+    ("bias_gradient_mean", "closure.py",
+     'g["b2"] = dz2.sum(axis=0)', 'g["b2"] = dz2.mean(axis=0)', [CL]),
+    ("relu_as_abs", "closure.py", "h2 = np.maximum(z2, 0.0)", "h2 = np.abs(z2)", [CL]),
+    ("fold_output_scale", "closure.py",
+     'p["W3"] = p["W3"] * y_sd', 'p["W3"] = p["W3"] / y_sd', [CL]),
+    ("standardisation_sample_deviation", "closure.py",
+     "mu, sd = X.mean(axis=0), X.std(axis=0)", "mu, sd = X.mean(axis=0), X.std(axis=0, ddof=1)", [CL]),
+    ("filtered_velocity_undivided", "closure.py", "ub = jb / rb", "ub = jb", [CL]),
+    ("gradient_axis_mapping", "closure.py", "axis = 2 - a ", "axis = a ", [CL]),
+    ("target_upper_clamp", "closure.py",
+     "np.clip(3.0 * nu_t, -(tau_coarse - 0.5) + 1e-3, 0.5)",
+     "np.clip(3.0 * nu_t, -(tau_coarse - 0.5) + 1e-3, 0.25)", [CL]),
+    ("tau_feature_shifted", "closure.py",
+     "tau_f = np.full(rho.shape, float(tau))", "tau_f = np.full(rho.shape, float(tau) - 0.5)", [CL]),
+    ("pressure_blocks_not_boundary", "layout.py",
+     "REGULARIZED_TYPES = (2, 3)", "REGULARIZED_TYPES = (2,)", [PINS]),
+    ("coarse_neighbour_axes_swapped", "layout.py",
+     "xc[b, k] = bmaps[lv + 1][(q[0] // 2, q[1] // 2, q[2] // 2)]",
+     "xc[b, k] = bmaps[lv + 1].get((q[1] // 2, q[0] // 2, q[2] // 2), -2)", [PINS]),
 ]
 
 

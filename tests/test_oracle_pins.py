@@ -95,6 +95,25 @@ def test_reg_collision_equals_bgk_on_a_regularized_input():
         assert np.allclose(fr, want, rtol=0, atol=1e-15)
 
 
+def test_initial_state_fills_every_updated_voxel():
+    """The initial state is f^eq(rho, u) on fluid voxels and on both kinds of
+    regularized node, 0 on solid and not-in-domain voxels; its mass is the
+    sum of rho over those updated voxels."""
+    shape = (4, 5, 6)
+    rho, u = wl.random_fields(shape, seed=15)
+    flags = np.zeros(shape, np.uint8)
+    flags[1, 2, 3] = wl.SOLID
+    flags[:, :, 0] = wl.flag(wl.VELOCITY, wl.NX_M)
+    flags[:, :, 5] = wl.flag(wl.PRESSURE, wl.NX_P)
+    flags[0, 0, 0] = wl.OUTSIDE
+    kept = np.ones(shape, bool)
+    kept[1, 2, 3] = kept[0, 0, 0] = False
+    f = lbm.init_equilibrium(rho, u, flags)
+    assert np.array_equal(f[:, kept], L.equilibrium(rho, u)[:, kept])
+    assert np.all(f[:, ~kept] == 0)
+    assert abs(lbm.conservation(f)[0] - rho[kept].sum()) < 1e-12
+
+
 # ------------------------------------------------------------ conservation
 
 @pytest.mark.parametrize("collision", ["bgk", "reg"])
@@ -441,6 +460,27 @@ def test_multires_tables_hand_example():
     # level-0 block (0,0,0): -x neighbour region is level 1 (periodic wrap), +x is level 0
     assert t[0]["xnbr_coarse"][0, k(-1, 0, 0)] == 0 and t[0]["nbr"][0, k(1, 0, 0)] == 1
     assert t[0]["xnbr_coarse"][1, k(1, 0, 0)] == 0
+
+
+def test_multires_tables_coarse_neighbours_asymmetric_example():
+    """Level 0 owns the map cell (x 0, y 0), level 1 the cells (1, 0),
+    (0, 1) and (1, 1) of a 32 x 32 x 16 finest box (cells of 16 voxels).
+    The level-1 blocks, all G_c, are numbered in Morton order: (1,0,0) = 0,
+    (0,1,0) = 1, (1,1,0) = 2.  A level-0 block's coarse neighbour across
+    +x, +y or the (+x, +y) edge is the level-1 block covering that region."""
+    lmap = np.array([[[0, 1], [1, 1]]], np.uint8)
+    t = layout.multires_tables(lmap, 2, 16)
+    assert [tuple(int(v) for v in c) for c in t[1]["coords"]] == [(1, 0, 0), (0, 1, 0), (1, 1, 0)]
+    ids = {tuple(int(v) for v in c): b for b, c in enumerate(t[0]["coords"])}
+    xc = t[0]["xnbr_coarse"]
+    k = lambda dx, dy, dz: (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+    assert xc[ids[(1, 0, 0)], k(1, 0, 0)] == 0
+    assert xc[ids[(0, 1, 0)], k(0, 1, 0)] == 1
+    assert xc[ids[(1, 1, 1)], k(1, 1, 0)] == 2
+    assert xc[ids[(0, 0, 0)], k(-1, 0, 0)] == 0      # x wraps to the level-1 cell (1, 0)
+    assert xc[ids[(0, 0, 0)], k(0, -1, 0)] == 1      # y wraps to the level-1 cell (0, 1)
+    assert xc[ids[(1, 0, 0)], k(-1, 0, 0)] == -1     # (0,0,0) is level 0
+    assert t[0]["nbr"][ids[(1, 0, 0)], k(-1, 0, 0)] == ids[(0, 0, 0)]
 
 
 def test_multires_tables_interior_blocks_are_gi():
