@@ -405,6 +405,29 @@ def test_train_one_step_is_adam_on_the_standardised_minibatch():
     assert np.allclose(got, want, rtol=1e-12, atol=1e-15)
 
 
+def test_train_steps_with_a_constant_gradient_move_by_lr_each():
+    """Adam's bias-corrected moments of a constant gradient g are g and g^2
+    at every step k (m_k = (1 - b1^k) g, v_k = (1 - b2^k) g^2), so each step
+    moves a weight by lr g / (|g| + eps).  A one-sample training set makes
+    every minibatch the same, and a learning rate of 1e-7 keeps the gradient
+    constant over three steps; the weights then move by 3 lr g / (|g| + eps)
+    (a step counter stuck at 1 would move them by 3.9 lr)."""
+    rng = np.random.default_rng(44)
+    X = rng.standard_normal((1, 16))
+    t = np.array([0.7])
+    th0 = random_theta(45)
+    lr, K = 1e-7, 3
+    got, _ = cl.train(X, t, th0, K, 8, lr, 3)
+    # one sample: every column is constant (scale 1) and the standardised
+    # problem has input 0 and target 0
+    _, g = cl.loss_and_grad(th0, np.zeros((8, 16)), np.zeros(8))
+    want = th0 - K * lr * g / (np.abs(g) + 1e-8)
+    want = cl.fold_normalisation(want, X[0], np.ones(16), 0.7, 1.0)
+    moved = np.abs(g) > 1e-4
+    assert moved.sum() > 100
+    assert np.allclose(got[moved], want[moved], rtol=0, atol=1e-4 * K * lr)
+
+
 def test_train_lowers_the_loss():
     rng = np.random.default_rng(42)
     X = rng.standard_normal((2000, 16))

@@ -239,6 +239,40 @@ MUTATIONS = [
     ("coarse_neighbour_axes_swapped", "layout.py",
      "xc[b, k] = bmaps[lv + 1][(q[0] // 2, q[1] // 2, q[2] // 2)]",
      "xc[b, k] = bmaps[lv + 1].get((q[1] // 2, q[0] // 2, q[2] // 2), -2)", [PINS]),
+    ("features_velocity_times_density", "closure.py",
+     "u = np.stack([np.tensordot(Cf[:, a], g, axes=(0, 0)) for a in range(3)]) / rho",
+     "u = np.stack([np.tensordot(Cf[:, a], g, axes=(0, 0)) for a in range(3)]) * rho", [CL]),
+    ("features_shear_components_swapped", "closure.py",
+     "pxy, pxz, pyz = P[0, 1] / s, P[0, 2] / s, P[1, 2] / s",
+     "pxy, pxz, pyz = P[0, 2] / s, P[0, 1] / s, P[1, 2] / s", [CL]),
+    ("features_third_order_scale", "closure.py",
+     "q.append(np.tensordot(w, d, axes=(0, 0)) / s)", "q.append(np.tensordot(w, d, axes=(0, 0)))", [CL]),
+    ("closure_step_features_of_the_old_state", "closure.py",
+     "d_tau, _ = forward(theta, features(g[:, fluid], tau))",
+     "d_tau, _ = forward(theta, features(f[:, fluid], tau))", [CL]),
+    ("backprop_through_wrong_layer", "closure.py",
+     'dh1 = dz2 @ p["W2"]', 'dh1 = dz2 @ p["W2"].T', [CL]),
+    ("adam_step_counter_frozen", "closure.py",
+     "theta, m, v = adam(theta, g, m, v, k, lr=lr)", "theta, m, v = adam(theta, g, m, v, 1, lr=lr)", [CL]),
+    ("fold_output_offset_sign", "closure.py",
+     'p["b3"] = p["b3"] * y_sd + y_mean', 'p["b3"] = p["b3"] * y_sd - y_mean', [CL]),
+    ("loss_summed", "closure.py", "loss = float(np.mean(r * r))", "loss = float(np.sum(r * r))", [CL]),
+    ("velocity_node_value_components", "lbm.py",
+     "u = bc_node[0:3].copy()", "u = bc_node[1:4].copy()", [PINS]),
+    ("taylor_green_closed_form_rate", "lbm.py",
+     "return float(np.exp(-4.0 * nu * k * k * t))", "return float(np.exp(-2.0 * nu * k * k * t))", [PINS]),
+    ("poiseuille_closed_form_factor", "lbm.py",
+     "return g / (2.0 * nu) * (y + 0.5) * (h - 0.5 - y)", "return g / nu * (y + 0.5) * (h - 0.5 - y)",
+     [PINS]),
+    ("explosion_first_substep_two_hops", "multires.py",
+     "                    ex = shift(c_up, c)\n", "                    ex = shift(c_up, c, 2)\n", [MR]),
+    ("multires_closure_not_clamped", "multires.py",
+     "tau[mine] = np.maximum(tau[mine] + d_tau, cl.TAU_MIN)", "tau[mine] = tau[mine] + d_tau", [MR]),
+    ("partial_blocks_dropped", "layout.py",
+     "nbz, nby, nbx = -(-nz // B), -(-ny // B), -(-nx // B)", "nbz, nby, nbx = nz // B, ny // B, nx // B",
+     [PINS]),
+    ("interface_blocks_not_first", "layout.py",
+     "rows.sort(key=lambda r: r[0])", "rows.sort(key=lambda r: r[0][1])", [PINS]),
 ]
 
 

@@ -406,6 +406,17 @@ def test_block_tables_periodic_wrap_hand_example():
                 assert nbr[nbr[b, kk], 26 - kk] == b
 
 
+def test_block_tables_ragged_box_keeps_partial_blocks():
+    """A 12 x 9 x 10 all-fluid box is cut into 2 x 2 x 2 blocks of 8^3 (the
+    partial ones padded with not-in-domain voxels), every one active, in
+    Morton order."""
+    flags = np.zeros((10, 9, 12), np.uint8)
+    t = layout.block_tables(flags, 8)
+    assert [tuple(int(v) for v in c) for c in t["coords"]] == \
+        [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+    assert t["dims_blocks"] == (2, 2, 2) and t["n_boundary"] == 0
+
+
 def test_block_tables_bitmask_grouping_hand_example():
     """Bitmask grouping of the example above: every block in Morton order,
     (1,1,0) marked by bit 3, its two regularized voxels indexed 0 and 1 in
