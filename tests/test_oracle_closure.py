@@ -45,6 +45,32 @@ def test_hand_built_network():
     assert np.allclose(y, np.maximum(X, 0).sum(axis=1) + 0.25, atol=1e-14)
 
 
+def test_flat_parameter_layout():
+    """The flat parameter vector is, in order, W1 (64 x 16, row j = unit j),
+    b1 (64), W2 (64 x 64, row j = unit j), b2 (64), W3 (64), b3 (1): the
+    layout the library's kernels read.  Built here by offset, without pack:
+    unit 5 of layer 1 reads feature 2, unit 7 of layer 2 reads unit 5 with
+    bias 0.01, the other layer-2 units have negative biases, and the output
+    is 2 h2_7 + 0.1 = 2 max(x_2, 0) + 0.12."""
+    H, F = 64, 16
+    o_W1, o_b1 = 0, H * F
+    o_W2 = o_b1 + H
+    o_b2 = o_W2 + H * H
+    o_W3 = o_b2 + H
+    o_b3 = o_W3 + H
+    assert o_b3 + 1 == cl.N_PARAMS
+    theta = np.zeros(cl.N_PARAMS)
+    theta[o_W1 + 5 * F + 2] = 1.0
+    theta[o_W2 + 7 * H + 5] = 1.0
+    theta[o_b2:o_b2 + H] = -0.01 * np.arange(1, H + 1)
+    theta[o_b2 + 7] = 0.01
+    theta[o_W3 + 7] = 2.0
+    theta[o_b3] = 0.1
+    X = np.random.default_rng(46).standard_normal((11, F))
+    y, _ = cl.forward(theta, X)
+    assert np.allclose(y, 2 * np.maximum(X[:, 2], 0) + 0.12, rtol=0, atol=1e-15)
+
+
 def test_adam_first_step_moves_each_parameter_by_lr():
     theta = random_theta(4)
     grad = np.random.default_rng(5).standard_normal(cl.N_PARAMS)

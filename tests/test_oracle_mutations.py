@@ -273,6 +273,18 @@ MUTATIONS = [
      [PINS]),
     ("interface_blocks_not_first", "layout.py",
      "rows.sort(key=lambda r: r[0])", "rows.sort(key=lambda r: r[0][1])", [PINS]),
+    ("conservation_momentum_axis", "lbm.py",
+     "j = [float(np.tensordot(Cf[:, a], f, axes=(0, 0)).sum()) for a in range(3)]",
+     "j = [float(np.tensordot(Cf[:, 0], f, axes=(0, 0)).sum()) for a in range(3)]", [PINS]),
+    ("minibatch_modulus", "closure.py",
+     "return np.array([splitmix64(seed + c0 + b) % n for b in range(batch)]",
+     "return np.array([splitmix64(seed + c0 + b) % (n - 1) for b in range(batch)]", [CL]),
+    ("morton_z_bit_misplaced", "layout.py",
+     "code |= ((bz >> k) & 1) << (3 * k + 2)", "code |= ((bz >> k) & 1) << (3 * k + 1)", [PINS]),
+    ("bc_index_rank_not_advanced", "layout.py",
+     "                        rank += 1\n", "                        rank += 0\n", [PINS]),
+    ("parameter_layout_b2_w3_swapped", "closure.py",
+     '("b2", (HIDDEN,)), ("W3", (HIDDEN,))', '("W3", (HIDDEN,)), ("b2", (HIDDEN,))', [CL]),
 ]
 
 
