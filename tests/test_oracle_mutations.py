@@ -285,6 +285,18 @@ MUTATIONS = [
      "                        rank += 1\n", "                        rank += 0\n", [PINS]),
     ("parameter_layout_b2_w3_swapped", "closure.py",
      '("b2", (HIDDEN,)), ("W3", (HIDDEN,))', '("W3", (HIDDEN,)), ("b2", (HIDDEN,))', [CL]),
+    ("multires_shift_axes_swapped", "multires.py",
+     "return np.roll(a, shift=(k * int(c[2]), k * int(c[1]), k * int(c[0])), axis=(-3, -2, -1))",
+     "return np.roll(a, shift=(k * int(c[0]), k * int(c[1]), k * int(c[2])), axis=(-3, -2, -1))", [MR]),
+    ("single_resolution_shift_axes_swapped", "lbm.py",
+     "return np.roll(a, shift=(cz, cy, cx), axis=(0, 1, 2))",
+     "return np.roll(a, shift=(cx, cy, cz), axis=(0, 1, 2))", [PINS]),
+    ("level_owner_lookup_axes_swapped", "layout.py",
+     "owner = own[lv][q[2] * B, q[1] * B, q[0] * B]", "owner = own[lv][q[0] * B, q[1] * B, q[2] * B]",
+     [PINS, MR]),
+    ("fine_octant_bits_swapped", "layout.py",
+     "f = (2 * q[0] + (j & 1), 2 * q[1] + ((j >> 1) & 1), 2 * q[2] + (j >> 2))",
+     "f = (2 * q[0] + (j >> 2), 2 * q[1] + ((j >> 1) & 1), 2 * q[2] + (j & 1))", [PINS, MR]),
 ]
 
 
